@@ -1,0 +1,165 @@
+"""Pins of the oracle's discrete operator, time stepper and time step (CPU only)."""
+import numpy as np
+import pytest
+
+from oracle.constants import trace_constant
+from oracle.dg import LSRK_A, LSRK_B, LSRK_C, DGOracle, standing_mode
+from paper_1507_02557_b300.inputs import layered_mesh, random_state, small_hybrid_mesh
+
+
+@pytest.fixture(scope="module")
+def mesh():
+    return small_hybrid_mesh()
+
+
+@pytest.fixture(scope="module")
+def mesh_c():
+    """Small hybrid mesh with a wave-speed jump between layers (c = 1, 1.5 by parity)."""
+    return layered_mesh(3, 3, 5, "HWHTK", seed=3, c_of_layer=lambda k: 1.0 if k % 2 == 0 else 1.5)
+
+
+def energy_rate(dg, q):
+    return float(np.sum(q * dg.mass_apply(dg.rhs(q)) * dg.material_weights()))
+
+
+@pytest.mark.parametrize("N", [1, 2, 3])
+@pytest.mark.parametrize("which", ["mesh", "mesh_c"])
+def test_energy_identity(N, which, request):
+    """Eq. (sym): U^T A U = 0 for central flux and = -1/2 sum int (tau_p[p]^2 + tau_u[u_n]^2) for upwind."""
+    m = request.getfixturevalue(which)
+    for ts in (0.0, 1.0):
+        dg = DGOracle(m, N, tau_scale=ts)
+        q = random_state(dg.ndof, 7)
+        rate = energy_rate(dg, q)
+        diss = dg.jump_dissipation(q)
+        scale = float(np.sum(q * dg.mass_apply(q)))
+        assert abs(rate - diss) < 1e-12 * scale, (ts, rate, diss)
+        if ts == 0.0:
+            assert abs(rate) < 1e-12 * scale
+        else:
+            assert diss < 0
+
+
+@pytest.mark.parametrize("N", [1, 3])
+def test_pyramid_strong_and_skew_forms_agree(mesh, N):
+    """Sec. 2.2: with GL quadrature on the quadrilateral face the strong and skew-symmetric
+    pyramid forms are equivalent.  The cofactors J dr/dx are bilinear in (a,b) for a
+    vertex-mapped pyramid, so collocating them at the semi-nodal points keeps it exact."""
+    a = DGOracle(mesh, N, pyr_form="skew")
+    b = DGOracle(mesh, N, pyr_form="strong")
+    q = random_state(a.ndof, 3)
+    ra, rb = a.split(a.rhs(q))[2], b.split(b.rhs(q))[2]
+    assert np.abs(ra - rb).max() < 1e-12 * np.abs(ra).max()
+
+
+def test_lsrk_order_conditions():
+    """LSRK(5,4) applied to y' = z y gives R(z) with Taylor coefficients 1, 1, 1/2, 1/6, 1/24."""
+    poly = np.polynomial.polynomial
+    y = np.array([1.0])
+    res = np.array([0.0])
+    for a, b in zip(LSRK_A, LSRK_B):
+        res = poly.polyadd(a * res, poly.polymul([0.0, 1.0], y))
+        y = poly.polyadd(y, b * res)
+    assert np.allclose(y[:5], [1, 1, 1 / 2, 1 / 6, 1 / 24], atol=1e-10)
+    # stage times: y' = t^m integrates exactly for m <= 3
+    for m in range(4):
+        yy, rr = 0.0, 0.0
+        for a, b, c in zip(LSRK_A, LSRK_B, LSRK_C):
+            rr = a * rr + c ** m
+            yy += b * rr
+        assert abs(yy - 1.0 / (m + 1)) < 1e-10   # published rationals hold to ~1e-12
+
+
+def test_faces_conform_and_walls_on_cube(mesh):
+    dg = DGOracle(mesh, 3)
+    sides = dg.geo.sides
+    nb = 0
+    for s in sides:
+        xv = mesh.xyz[mesh.conn[s.t][s.e]]
+        x, F = dg.els[s.t].vmap(xv, s.rst)
+        assert np.all(np.linalg.det(F) > 0)
+        if s.nbr >= 0:
+            o = sides[s.nbr]
+            xo, _ = dg.els[o.t].vmap(mesh.xyz[mesh.conn[o.t][o.e]], o.rst)
+            assert np.abs(x - xo).max() < 1e-13
+            assert np.abs(s.n + o.n).max() < 1e-12
+            assert np.abs(s.Js - o.Js).max() < 1e-13
+        else:
+            nb += 1
+            assert np.all(np.min(np.abs(np.abs(x) - 1.0), axis=1) < 1e-13)
+    # 4x4x5 cells: 2*16 + 4*20 wall quads/triangle pairs
+    assert nb > 0
+
+
+@pytest.mark.parametrize("N", [1, 3])
+def test_linear_fields_are_reproduced(N):
+    """Continuous linear fields: zero jumps, and -div u, -grad p exact at interior elements.
+
+    Affine mesh (amp = 0), so that the LSC wedge space contains the linear fields.
+    """
+    m = layered_mesh(3, 3, 5, "HWHTK", seed=0, amp=0.0)
+    dg = DGOracle(m, N)
+    f = lambda x, t: np.stack([1 + 2 * x[:, 0] - x[:, 1] + 0.5 * x[:, 2],
+                               0.3 * x[:, 0], -0.7 * x[:, 1] + 0.1, 0.2 * x[:, 2] + 0.4 * x[:, 0]])
+    q = dg.project(f)
+    r = dg.rhs(q)
+    exact = lambda x, t: np.stack([np.full(len(x), -(0.3 - 0.7 + 0.2)),
+                                   np.full(len(x), -2.0), np.full(len(x), 1.0), np.full(len(x), -0.5)])
+    want = dg.project(exact)
+    inner = np.ones((4, dg.ndof), bool)
+    rv = dg.split(inner)
+    for s in dg.geo.sides:
+        if s.nbr < 0:
+            rv[s.t][:, s.e] = False
+    assert np.abs(r - want)[inner].max() < 1e-10
+
+
+def assemble(dg):
+    n = 4 * dg.ndof
+    A = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        A[:, j] = dg.rhs(e.reshape(4, -1)).ravel()
+    return A
+
+
+@pytest.mark.parametrize("N", [1, 2])
+def test_spectral_radius_below_trace_bound(N):
+    """Eq. (bnd_re), (dtK): rho(M^{-1}A) <= max_K C^K C_T(N) C_J^K, and LSRK(5,4) is stable at
+    the paper's dt (C = 0.5) for every eigenvalue of the assembled operator."""
+    m = layered_mesh(2, 2, 5, "HWHTK", seed=1)
+    dg = DGOracle(m, N)
+    lam = np.linalg.eigvals(assemble(dg))
+    CT = [trace_constant(t, N) for t in range(4)]
+    bound = 1.0 / dg.global_dt(CT, cfl=1.0)
+    rho = np.abs(lam).max()
+    assert rho <= bound
+    assert np.max(lam.real) < 1e-9
+    dt = dg.global_dt(CT, cfl=0.5)
+    z = lam * dt
+    R = np.ones_like(z)
+    res = np.zeros_like(z)
+    y = np.ones_like(z)
+    for a, b in zip(LSRK_A, LSRK_B):
+        res = a * res + z * y
+        y = y + b * res
+    assert np.abs(y).max() <= 1.0 + 1e-12
+
+
+def test_convergence_to_standing_mode():
+    """GL formulation on refined hybrid meshes: L2 error rate >= N + 1/2 (Sec. 4.1-4.2)."""
+    N = 1
+    errs = []
+    for mlev in (1, 2):
+        L = "H" * mlev + "W" * mlev + "H" * mlev + "T" + "K" * mlev
+        m = layered_mesh(2 * mlev, 2 * mlev, len(L), L, seed=0)
+        dg = DGOracle(m, N)
+        CT = [trace_constant(t, N) for t in range(4)]
+        T = 0.1
+        nst = int(np.ceil(T / dg.global_dt(CT)))
+        q = dg.project(standing_mode, 0.0)
+        for _ in range(nst):
+            q = dg.lsrk_step(q, T / nst)
+        errs.append(dg.l2_error(q, standing_mode, T))
+    assert np.log2(errs[0] / errs[1]) > N + 0.5
