@@ -1,0 +1,144 @@
+/*
+ * dg.h - C ABI of the hybrid-mesh acoustic discontinuous Galerkin library (libdg).
+ *
+ * Semi-discrete system (arxiv 1507.02557, Sec. 2.2, Eq. skewform and the strong
+ * form):  (1/kappa) p_t + div u = 0,  rho u_t + grad p = 0, with kappa = 1 and
+ * rho = 1/c^2 per element, free-surface walls p = 0, upwind penalties
+ * tau_p = 1/{rho c}, tau_u = {rho c} (times tau_scale).  Bases (Sec. 2.1):
+ * GL-nodal hexahedra, LSC-DG modal wedges, semi-nodal rational pyramids,
+ * nodal tetrahedra (equispaced lattice).  Time stepping: LSRK(5,4)
+ * (Carpenter-Kennedy 2N-storage); time step of Eq. (dtK) with the computed
+ * reference trace constants of Appendix B.
+ *
+ * State layout ("q"): float32 [4][ndof], fields p, u, v, w.  Within a field the
+ * DOFs of all hexahedra come first, then wedges, pyramids, tetrahedra
+ * (dg_layout gives the offsets); within a type, element-major with Np DOFs per
+ * element:
+ *   hex     node (i,j,k) at GL nodes (r_i,s_j,t_k), index i + (N+1)(j + (N+1)k)
+ *   wedge   modal (i,j,k), index m + Ntri*j, m enumerating (i,k), i outer, k inner
+ *           (P_i(a) P_j(s) ((1-c)/2)^i P_k^{(2i+1,0)}(t), orthonormal; LSC: / sqrt(J))
+ *   pyramid semi-nodal (i,j,k), 0 <= i,j <= k <= N, k outer, then j, then i
+ *   tet     nodal at r,s,t = -1 + 2(i,j,k)/N, i+j+k <= N, k outer, then j, then i
+ *
+ * Conventions
+ *   - Every call returns a dg_status and never aborts or throws across the ABI.
+ *   - Host arrays are borrowed for the duration of the call.  Device pointers
+ *     are borrowed; the caller keeps them alive until the stream has finished.
+ *   - Work is enqueued on the CUDA stream given to dg_mesh_create.  Only
+ *     dg_mesh_create, dg_timestep, dg_energy and dg_get_state(on_device = 0)
+ *     synchronise with the host.
+ *   - Errors: DG_EINVAL bad argument; DG_ENOMEM device allocation failed;
+ *     DG_ECUDA a CUDA call failed (dg_last_error() gives the message);
+ *     DG_EMESH invalid mesh (J <= 0 at a quadrature point, a face shared by
+ *     more than two elements); DG_ENOTSUP option not built.
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_mesh dg_mesh;  /* opaque; owns the device buffers it allocates */
+
+typedef enum {
+  DG_OK = 0,
+  DG_EINVAL = -1,
+  DG_ENOMEM = -2,
+  DG_ECUDA = -3,
+  DG_EMESH = -4,
+  DG_ETIMEOUT = -5,
+  DG_ENOTSUP = -6,
+  DG_ENONFINITE = -7
+} dg_status;
+
+enum { DG_HEX = 0, DG_WEDGE = 1, DG_PYR = 2, DG_TET = 3 };
+
+typedef struct {
+  int64_t nverts;
+  const double *xyz;       /* host, [nverts][3] vertex coordinates */
+  int64_t nelem[4];        /* elements per type: hex, wedge, pyramid, tet */
+  const int32_t *conn[4];  /* host, [nelem][8|6|5|4] vertex ids in the local order:
+                              hex (r,s,t) = (+-1,+-1,+-1) lexicographic, r fastest;
+                              wedge (r,t) = (-1,-1),(1,-1),(-1,1) at s=-1 then s=+1;
+                              pyramid base (r,s) lexicographic at t=-1, apex (-1,-1,1);
+                              tet (-1,-1,-1),(1,-1,-1),(-1,1,-1),(-1,-1,1) */
+  const double *c2[4];     /* host, [nelem] squared wave speed per element (> 0) */
+  int N;                   /* polynomial order, 1..6 */
+  int hex_basis;           /* 0 = GL nodes (only value built) */
+  int pyr_form;            /* 0 = skew-symmetric, 1 = strong (identical results, Sec. 2.2) */
+  double tau_scale;        /* 1 = upwind, 0 = central flux */
+  int nlevels;             /* 1 = single-rate (only value built) */
+  double cfl;              /* C of Eq. (dtK); <= 0 selects 0.5 */
+  int precision;           /* 0 = FP32 (only value built) */
+} dg_mesh_desc;
+
+/* Build the mesh on the current CUDA device: face matching, geometric factors,
+ * reference operators, local time steps (Eq. dtK).  stream: a cudaStream_t or
+ * NULL for the default stream.  Synchronises.  Allocates the state q, the LSRK
+ * residual and a face-trace exchange buffer, all zero-initialised. */
+dg_status dg_mesh_create(const dg_mesh_desc *desc, void *stream, dg_mesh **out);
+void dg_mesh_destroy(dg_mesh *mesh);
+
+/* Run the host part of dg_mesh_create only (face matching, geometry checks,
+ * reference operators, Eq. dtK) without touching any GPU.  Returns the global
+ * time step in *dt_min and, if trace_const is not NULL, the reference trace
+ * constants C_T(N) of hex, wedge, pyramid, tet (Appendix B) in trace_const[4].
+ * Same error codes as dg_mesh_create. */
+dg_status dg_host_check(const dg_mesh_desc *desc, double *dt_min, double *trace_const);
+
+/* DOF layout of one element type: offset of its first DOF within a field,
+ * its element count and DOFs per element. */
+dg_status dg_layout(const dg_mesh *mesh, int type, int64_t *offset, int64_t *nelem, int *Np);
+dg_status dg_ndof(const dg_mesh *mesh, int64_t *ndof);
+
+/* Copy a state [4][ndof] into the mesh's state (and zero the LSRK residual).
+ * q is a host pointer (on_device = 0) or a device pointer (on_device = 1). */
+dg_status dg_set_state(dg_mesh *mesh, const float *q, int on_device);
+/* Copy the mesh's state out; on_device = 0 synchronises. */
+dg_status dg_get_state(const dg_mesh *mesh, float *q, int on_device);
+
+/* rhs = M^{-1} A q for a device state q_dev [4][ndof] (Sec. 2.2-2.3); rhs_dev is
+ * a device buffer of the same size.  Uses the mesh's trace buffer as scratch.
+ * t is the time (unused: no source term). */
+dg_status dg_rhs(dg_mesh *mesh, const float *q_dev, float *rhs_dev, double t);
+
+/* Global time step dtau_min = min_K dtau_K of Eq. (dtK) (host, computed at
+ * create).  level_count may be NULL; otherwise receives the element count of
+ * each multi-rate level (nlevels entries). */
+dg_status dg_timestep(const dg_mesh *mesh, double *dt_min, int64_t *level_count);
+
+/* Advance the mesh's state by nsteps LSRK(5,4) steps of size dt (dt <= 0 uses
+ * dtau_min).  *t_inout (may be NULL) is advanced by nsteps*dt.  Asynchronous. */
+dg_status dg_step(dg_mesh *mesh, int nsteps, double dt, double *t_inout);
+
+/* Direct access to the device state [4][ndof] owned by the mesh. */
+dg_status dg_state_ptr(dg_mesh *mesh, float **q_dev);
+
+/* E = 1/2 sum_K (p^T M_K p / kappa + rho u^T M_K u) in FP64 for a device state
+ * (NULL = the mesh's state).  Synchronises. */
+dg_status dg_energy(dg_mesh *mesh, const float *q_dev, double *E);
+
+/* Per-type kernel timing.  ms and launches (4 entries each, hex, wedge,
+ * pyramid, tet; either may be NULL) receive the kernel time (CUDA events
+ * recorded on the mesh's stream around each launch) and the launch count
+ * accumulated since the previous dg_profile call (synchronises when either is
+ * given); then the counters are reset and event recording is switched on
+ * (enable = 1) or off (enable = 0).  Launch counts are kept even when off. */
+dg_status dg_profile(dg_mesh *mesh, int enable, double *ms, int64_t *launches);
+
+/* Adjoint of dg_step (gradient w.r.t. c^2 and source amplitude): not built,
+ * returns DG_ENOTSUP. */
+dg_status dg_adjoint_step(dg_mesh *mesh, int nsteps, float *lambda_dev, double *grad_c2_dev,
+                          double *grad_amp);
+
+const char *dg_status_string(dg_status s);
+/* Message of the last DG_ECUDA / DG_EMESH / DG_EINVAL error on this thread. */
+const char *dg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DG_H */

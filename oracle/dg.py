@@ -75,7 +75,7 @@ class DGOracle:
         self.wq_V = wd.basis(self.wq_pts)
         self.wq_Vg = wd.grad(self.wq_pts)
         self.wedge_G, self.wedge_J = self._factors(wd, X[1], self.wq_pts)
-        gJ = np.array([wd.jac_grad(xv, self.wq_pts) for xv in X[1]]).reshape(len(X[1]), -1, 3)
+        gJ = np.array([wd.jac_grad(xv, self.wq_pts) for xv in X[1]]).reshape(len(X[1]), len(self.wq_w), 3)
         # physical gradient of J: grad_x J = G^T grad_rst J
         self.wedge_gradJ = np.einsum("kqad,kqa->kqd", self.wedge_G, gJ) if len(X[1]) else gJ
         # ---- pyramid: weak derivative operators and factors at the semi-nodal points

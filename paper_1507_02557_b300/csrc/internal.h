@@ -1,0 +1,76 @@
+// Internal state of a dg_mesh and the kernel launch interface.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "dg.h"
+
+namespace dgk {
+
+constexpr int MAXN = 6;       // kernels are instantiated for N = 1..MAXN
+constexpr int NCODES = 8;     // face orientation codes (6 used for triangles)
+
+// Device data of one element type.
+struct TypeDev {
+  int K = 0, Np = 0, nf = 0, nc = 0;
+  int64_t dof_off = 0;        // first DOF of the type within a field
+  int64_t side_off = 0;       // first global side index of the type (side = off + e*nf + f)
+  float* c2 = nullptr;        // [K]
+  float* geo = nullptr;       // hex [K][24] trilinear coefficients; tet [K][12] G,J;
+                              // pyramid [K][Np][10] G,J; wedge [K][nc][12] G, grad J/(2J)
+  float4* sgeo = nullptr;     // non-hex: [K*nf][nq] (n, w_q J^s [/sqrt J for the wedge])
+  float* sisq = nullptr;      // wedge: [K*nf][nq] 1/sqrt(J) at face points
+  float* ops = nullptr;       // volume operators (type-specific layout, see setup.cpp)
+  float* Tt = nullptr;        // non-hex trace matrices [nf][8][Np][nq]
+  float* L = nullptr;         // non-hex lift matrices [nf][8][nq][Np]
+};
+
+}  // namespace dgk
+
+struct dg_mesh {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int N = 0, nq = 0;
+  double tau_scale = 1.0, cfl = 0.5;
+  int pyr_form = 0;
+  int64_t K[4] = {0, 0, 0, 0};
+  int64_t ndof = 0, nsides = 0;
+  dgk::TypeDev td[4];
+  int* side_nbr = nullptr;    // [nsides] neighbour's global side, -1 on a wall
+  int* side_code = nullptr;   // [nsides] canonical face-frame code
+  float* side_tau = nullptr;  // [nsides] tau_p = 1/{rho c}
+  float* hexc = nullptr;      // hex constants: D1[n1*n1], Vm[n1], Vp[n1], w1[n1], r1[n1]
+  int* hexperm = nullptr;     // [8][nq] local face point -> canonical index
+  float* q = nullptr;         // [4][ndof] state
+  float* res = nullptr;       // [4][ndof] LSRK residual
+  float* trace = nullptr;     // [2 buffers][2 planes: p, u.n][nsides*nq]
+  double* dacc = nullptr;     // energy accumulator
+  double dt_min = 0.0;
+  std::vector<double> dtK[4];
+  std::vector<double> tet_mhat;  // host copy of the reference tet mass (energy)
+  float* tet_mhat_dev = nullptr;
+  // per-type kernel timing (dg_profile): event pairs recorded around each launch
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_used[4];   // (start, stop) indices into ev_pool
+  size_t ev_next = 0;
+  int64_t launches[4] = {0, 0, 0, 0};
+};
+
+namespace dgk {
+// Kernel launchers (kernels.cu).  Return cudaSuccess or the launch error.
+cudaError_t launch_trace(dg_mesh* m, const float* q, float* tout);
+cudaError_t launch_rhs(dg_mesh* m, const float* q, const float* tin, float* rhs);
+cudaError_t launch_stage(dg_mesh* m, float* q, float* res, const float* tin, float* tout, float a,
+                         float b, float dt);
+cudaError_t launch_energy(dg_mesh* m, const float* q, double* acc);
+}  // namespace dgk
+
+// Host setup (setup.cpp).
+dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err);
+void dg_free(dg_mesh* m);
+// Host setup without any device allocation or transfer (dg_host_check).
+dg_status dg_setup_host_only(dg_mesh* m, const dg_mesh_desc* d, std::string& err, double ct[4]);

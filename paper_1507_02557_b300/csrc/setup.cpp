@@ -1,0 +1,835 @@
+// Host setup of a dg_mesh (FP64): face matching in canonical face frames,
+// geometric factors, reference operators, local time steps (Eq. dtK), upload.
+//
+// Canonical face frame (shared by the two elements of a face):
+//   triangle  corners ordered by increasing global vertex id G0 < G1 < G2, point
+//             (xi,eta) of {xi,eta >= -1, xi+eta <= 0} at barycentric weights
+//             (-(xi+eta)/2, (1+xi)/2, (1+eta)/2) on (G0,G1,G2);
+//   quad      C00 = smallest-id corner, C10 = its edge neighbour of smaller id,
+//             C01 = the other edge neighbour, C11 = opposite; bilinear blend.
+// Face points: collapsed rule (N+1)^2 on triangles, GL (N+1)^2 on quads.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <stdexcept>
+
+#include "internal.h"
+#include "refelem.h"
+
+using namespace dgref;
+
+namespace {
+
+struct SetupError : std::runtime_error {
+  dg_status code;
+  SetupError(dg_status c, const std::string& s) : std::runtime_error(s), code(c) {}
+};
+
+// dx_d/dr_a of the vertex map, F[3*d + a].
+void map_jacobian(int t, const double* xv, const double* rst, double F[9]) {
+  double r = rst[0], s = rst[1], u = rst[2];
+  std::memset(F, 0, 9 * sizeof(double));
+  if (t == HEX) {
+    for (int v = 0; v < 8; ++v) {
+      const double* c = vert_rst(HEX, v);
+      double fr = 0.5 * (1 + c[0] * r), fs = 0.5 * (1 + c[1] * s), ft = 0.5 * (1 + c[2] * u);
+      double g[3] = {0.5 * c[0] * fs * ft, fr * 0.5 * c[1] * ft, fr * fs * 0.5 * c[2]};
+      for (int d = 0; d < 3; ++d)
+        for (int a = 0; a < 3; ++a) F[3 * d + a] += xv[3 * v + d] * g[a];
+    }
+  } else if (t == TET) {
+    for (int d = 0; d < 3; ++d)
+      for (int a = 0; a < 3; ++a) F[3 * d + a] = 0.5 * (xv[3 * (a + 1) + d] - xv[d]);
+  } else if (t == WEDGE) {
+    double lam[3] = {-0.5 * (r + u), 0.5 * (1 + r), 0.5 * (1 + u)};
+    double lr[3] = {-0.5, 0.5, 0.0}, lt[3] = {-0.5, 0.0, 0.5};
+    double f0 = 0.5 * (1 - s), f1 = 0.5 * (1 + s);
+    for (int d = 0; d < 3; ++d)
+      for (int v = 0; v < 3; ++v) {
+        double lo = xv[3 * v + d], hi = xv[3 * (v + 3) + d];
+        F[3 * d + 0] += lr[v] * (f0 * lo + f1 * hi);
+        F[3 * d + 1] += lam[v] * 0.5 * (hi - lo);
+        F[3 * d + 2] += lt[v] * (f0 * lo + f1 * hi);
+      }
+  } else {  // pyramid: x = (1-c)/2 B(a,b) + (1+c)/2 x_apex
+    double h = 0.5 * (1 - u);
+    double a = (1 + r) / h - 1, b = (1 + s) / h - 1;
+    double Nab[4] = {0.25 * (1 - a) * (1 - b), 0.25 * (1 + a) * (1 - b), 0.25 * (1 - a) * (1 + b),
+                     0.25 * (1 + a) * (1 + b)};
+    double Na[4] = {-0.25 * (1 - b), 0.25 * (1 - b), -0.25 * (1 + b), 0.25 * (1 + b)};
+    double Nb[4] = {-0.25 * (1 - a), -0.25 * (1 + a), 0.25 * (1 - a), 0.25 * (1 + a)};
+    for (int d = 0; d < 3; ++d) {
+      double B = 0, Ba = 0, Bb = 0;
+      for (int v = 0; v < 4; ++v) {
+        B += Nab[v] * xv[3 * v + d];
+        Ba += Na[v] * xv[3 * v + d];
+        Bb += Nb[v] * xv[3 * v + d];
+      }
+      F[3 * d + 0] = Ba;
+      F[3 * d + 1] = Bb;
+      F[3 * d + 2] = 0.5 * (1 + a) * Ba + 0.5 * (1 + b) * Bb + 0.5 * (xv[12 + d] - B);
+    }
+  }
+}
+
+double det3(const double F[9]) {
+  return F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+         F[2] * (F[3] * F[7] - F[4] * F[6]);
+}
+
+// G[a][d] = d r_a / d x_d = inverse of F (F[d][a]).
+double inverse_metric(const double F[9], double G[9]) {
+  double J = det3(F);
+  // columns of F: x_r, x_s, x_t; rows of G: (x_s x x_t)/J, (x_t x x_r)/J, (x_r x x_s)/J
+  double c[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int d = 0; d < 3; ++d) c[a][d] = F[3 * d + a];
+  auto cross = [](const double* p, const double* q, double* o) {
+    o[0] = p[1] * q[2] - p[2] * q[1];
+    o[1] = p[2] * q[0] - p[0] * q[2];
+    o[2] = p[0] * q[1] - p[1] * q[0];
+  };
+  cross(c[1], c[2], G + 0);
+  cross(c[2], c[0], G + 3);
+  cross(c[0], c[1], G + 6);
+  for (int i = 0; i < 9; ++i) G[i] /= J;
+  return J;
+}
+
+// Reference gradient of J for the wedge map (second derivatives x_rs, x_ts are constant).
+void wedge_grad_J(const double* xv, const double* rst, double gJ[3]) {
+  double F[9];
+  map_jacobian(WEDGE, xv, rst, F);
+  double lr[3] = {-0.5, 0.5, 0.0}, lt[3] = {-0.5, 0.0, 0.5};
+  double xrs[3] = {0, 0, 0}, xts[3] = {0, 0, 0};
+  for (int d = 0; d < 3; ++d)
+    for (int v = 0; v < 3; ++v) {
+      double diff = 0.5 * (xv[3 * (v + 3) + d] - xv[3 * v + d]);
+      xrs[d] += lr[v] * diff;
+      xts[d] += lt[v] * diff;
+    }
+  auto detcols = [&](const double* c0, const double* c1, const double* c2) {
+    double M[9];
+    for (int d = 0; d < 3; ++d) {
+      M[3 * d] = c0[d];
+      M[3 * d + 1] = c1[d];
+      M[3 * d + 2] = c2[d];
+    }
+    return det3(M);
+  };
+  double xr[3], xs[3], xt[3];
+  for (int d = 0; d < 3; ++d) {
+    xr[d] = F[3 * d];
+    xs[d] = F[3 * d + 1];
+    xt[d] = F[3 * d + 2];
+  }
+  gJ[0] = detcols(xr, xrs, xt);                       // d x_s/dr = x_rs
+  gJ[1] = detcols(xrs, xs, xt) + detcols(xr, xs, xts); // d x_r/ds, d x_t/ds
+  gJ[2] = detcols(xr, xts, xt);                       // d x_s/dt = x_ts
+}
+
+// Exact volume rule on a reference element (for reference mass matrices).
+void volume_rule(int t, int q, std::vector<double>& P, std::vector<double>& W) {
+  std::vector<double> x, wx, y, wy, z, wz;
+  P.clear();
+  W.clear();
+  if (t == HEX) {
+    gauss_jacobi(q, 0, 0, x, wx);
+    for (int k = 0; k < q; ++k)
+      for (int j = 0; j < q; ++j)
+        for (int i = 0; i < q; ++i) {
+          P.insert(P.end(), {x[i], x[j], x[k]});
+          W.push_back(wx[i] * wx[j] * wx[k]);
+        }
+  } else if (t == WEDGE) {
+    std::vector<double> tp, tw;
+    tri_rule(q - 1, tp, tw);
+    gauss_jacobi(q, 0, 0, x, wx);
+    for (int l = 0; l < q; ++l)
+      for (size_t m = 0; m < tw.size(); ++m) {
+        P.insert(P.end(), {tp[2 * m], x[l], tp[2 * m + 1]});
+        W.push_back(tw[m] * wx[l]);
+      }
+  } else if (t == PYR) {
+    gauss_jacobi(q, 0, 0, x, wx);
+    gauss_jacobi(q, 2, 0, z, wz);
+    for (int k = 0; k < q; ++k)
+      for (int j = 0; j < q; ++j)
+        for (int i = 0; i < q; ++i) {
+          double h = 0.5 * (1 - z[k]);
+          P.insert(P.end(), {(1 + x[i]) * h - 1, (1 + x[j]) * h - 1, z[k]});
+          W.push_back(wx[i] * wx[j] * wz[k] / 4.0);
+        }
+  } else {
+    gauss_jacobi(q, 0, 0, x, wx);
+    gauss_jacobi(q, 1, 0, y, wy);
+    gauss_jacobi(q, 2, 0, z, wz);
+    for (int k = 0; k < q; ++k)
+      for (int j = 0; j < q; ++j)
+        for (int i = 0; i < q; ++i) {
+          double r = 0.25 * (1 + x[i]) * (1 - y[j]) * (1 - z[k]) - 1;
+          double s = 0.5 * (1 + y[j]) * (1 - z[k]) - 1;
+          P.insert(P.end(), {r, s, z[k]});
+          W.push_back(wx[i] * wy[j] * wz[k] / 8.0);
+        }
+  }
+}
+
+// Largest eigenvalue of the symmetric-definite pencil (A, B): Cholesky B = L L^T and
+// cyclic Jacobi rotations on L^{-1} A L^{-T}.
+double max_gen_eig(std::vector<double> A, std::vector<double> B, int n) {
+  for (int j = 0; j < n; ++j) {  // Cholesky, lower
+    double s = B[j * n + j];
+    for (int k = 0; k < j; ++k) s -= B[j * n + k] * B[j * n + k];
+    B[j * n + j] = std::sqrt(s);
+    for (int i = j + 1; i < n; ++i) {
+      double v = B[i * n + j];
+      for (int k = 0; k < j; ++k) v -= B[i * n + k] * B[j * n + k];
+      B[i * n + j] = v / B[j * n + j];
+    }
+  }
+  // C = L^{-1} A L^{-T}: solve L X = A, then L C^T = X^T
+  auto lsolve = [&](std::vector<double>& X) {
+    for (int c = 0; c < n; ++c)
+      for (int i = 0; i < n; ++i) {
+        double v = X[i * n + c];
+        for (int k = 0; k < i; ++k) v -= B[i * n + k] * X[k * n + c];
+        X[i * n + c] = v / B[i * n + i];
+      }
+  };
+  lsolve(A);
+  std::vector<double> T(n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) T[i * n + j] = A[j * n + i];
+  lsolve(T);
+  std::vector<double>& C = T;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += C[p * n + q] * C[p * n + q];
+    if (off < 1e-30) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double apq = C[p * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        double th = 0.5 * (C[q * n + q] - C[p * n + p]) / apq;
+        double tt = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+        double c = 1.0 / std::sqrt(tt * tt + 1.0), s = tt * c;
+        for (int k = 0; k < n; ++k) {
+          double akp = C[k * n + p], akq = C[k * n + q];
+          C[k * n + p] = c * akp - s * akq;
+          C[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          double apk = C[p * n + k], aqk = C[q * n + k];
+          C[p * n + k] = c * apk - s * aqk;
+          C[q * n + k] = s * apk + c * aqk;
+        }
+      }
+  }
+  double mx = -1e300;
+  for (int i = 0; i < n; ++i) mx = std::max(mx, C[i * n + i]);
+  return mx;
+}
+
+// Reference trace constant C_T(N) (Appendix B), Euclidean face measure of the reference element.
+double trace_constant(const Basis& B) {
+  int t = B.type, N = B.N, Np = B.Np;
+  if (t == HEX) return 1.5 * (N + 1) * (N + 2);
+  std::vector<double> P, W;
+  volume_rule(t, N + 2, P, W);
+  std::vector<double> M(Np * Np, 0.0), Ms(Np * Np, 0.0), phi(Np);
+  for (size_t q = 0; q < W.size(); ++q) {
+    B.eval(&P[3 * q], phi.data(), nullptr);
+    for (int i = 0; i < Np; ++i)
+      for (int j = 0; j < Np; ++j) M[i * Np + j] += W[q] * phi[i] * phi[j];
+  }
+  for (int f = 0; f < nfaces(t); ++f) {
+    int nv = face_nverts(t, f);
+    int key[4] = {0, 1, 2, 3};
+    std::vector<double> pts, w;
+    if (nv == 3) tri_rule(N, pts, w); else quad_rule(N, pts, w);
+    for (size_t q = 0; q < w.size(); ++q) {
+      double rst[3], d1[3], d2[3];
+      face_point(t, f, key, pts[2 * q], pts[2 * q + 1], rst, d1, d2);
+      double cr[3] = {d1[1] * d2[2] - d1[2] * d2[1], d1[2] * d2[0] - d1[0] * d2[2],
+                      d1[0] * d2[1] - d1[1] * d2[0]};
+      double ar = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+      B.eval(rst, phi.data(), nullptr);
+      for (int i = 0; i < Np; ++i)
+        for (int j = 0; j < Np; ++j) Ms[i * Np + j] += w[q] * ar * phi[i] * phi[j];
+    }
+  }
+  return max_gen_eig(Ms, M, Np);
+}
+
+// Canonical corner order (positions within the local corner list) of a face.
+void canonical_key(int nv, const int64_t* gid, int key[4]) {
+  if (nv == 3) {
+    int o[3] = {0, 1, 2};
+    std::sort(o, o + 3, [&](int x, int y) { return gid[x] < gid[y]; });
+    key[0] = o[0]; key[1] = o[1]; key[2] = o[2]; key[3] = -1;
+    return;
+  }
+  static const int cyc[4] = {0, 1, 3, 2};
+  int p = 0;
+  for (int m = 1; m < 4; ++m)
+    if (gid[cyc[m]] < gid[cyc[p]]) p = m;
+  int n1 = cyc[(p + 1) % 4], n2 = cyc[(p + 3) % 4];
+  key[0] = cyc[p];
+  key[1] = gid[n1] < gid[n2] ? n1 : n2;
+  key[2] = gid[n1] < gid[n2] ? n2 : n1;
+  key[3] = cyc[(p + 2) % 4];
+}
+
+int key_to_code(int nv, const int key[4]) {
+  for (int c = 0; c < (nv == 3 ? 6 : 8); ++c) {
+    int k2[4];
+    face_code_key(nv, c, k2);
+    bool ok = true;
+    for (int m = 0; m < nv; ++m) ok &= (k2[m] == key[m]);
+    if (ok) return c;
+  }
+  throw SetupError(DG_EMESH, "face orientation not recognised");
+}
+
+thread_local bool g_host_only = false;   // dg_host_check: run the host setup only
+
+template <class T>
+T* upload(const std::vector<T>& h, std::vector<void*>& owned) {
+  if (h.empty() || g_host_only) return nullptr;
+  void* p = nullptr;
+  if (cudaMalloc(&p, h.size() * sizeof(T)) != cudaSuccess) throw SetupError(DG_ENOMEM, "cudaMalloc failed");
+  owned.push_back(p);
+  if (cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+    throw SetupError(DG_ECUDA, "cudaMemcpy failed");
+  return static_cast<T*>(p);
+}
+
+template <class T>
+T* alloc_zero(size_t n, std::vector<void*>& owned) {
+  void* p = nullptr;
+  if (g_host_only) return nullptr;
+  if (n == 0) n = 1;
+  if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) throw SetupError(DG_ENOMEM, "cudaMalloc failed");
+  owned.push_back(p);
+  if (cudaMemset(p, 0, n * sizeof(T)) != cudaSuccess) throw SetupError(DG_ECUDA, "cudaMemset failed");
+  return static_cast<T*>(p);
+}
+
+std::vector<void*>& owned_list(dg_mesh* m);
+
+}  // namespace
+
+// ----------------------------------------------------------------------------- registry of allocations
+#include <mutex>
+#include <unordered_map>
+namespace {
+std::mutex g_mu;
+std::unordered_map<dg_mesh*, std::vector<void*>> g_owned;
+std::vector<void*>& owned_list(dg_mesh* m) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_owned[m];
+}
+}  // namespace
+
+dg_status dg_setup_host_only(dg_mesh* m, const dg_mesh_desc* d, std::string& err, double ct[4]) {
+  g_host_only = true;
+  dg_status st = dg_setup(m, d, err);
+  g_host_only = false;
+  if (st == DG_OK && ct) {
+    for (int t = 0; t < 4; ++t) {
+      Basis B;
+      B.init(t, d->N);
+      ct[t] = trace_constant(B);
+    }
+  }
+  dg_free(m);
+  return st;
+}
+
+void dg_free(dg_mesh* m) {
+  std::vector<void*> v;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_owned.find(m);
+    if (it != g_owned.end()) {
+      v.swap(it->second);
+      g_owned.erase(it);
+    }
+  }
+  for (void* p : v) cudaFree(p);
+}
+
+dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
+  try {
+    std::vector<void*>& owned = owned_list(m);
+    const int N = d->N;
+    m->N = N;
+    const int n1 = N + 1, nq = n1 * n1;
+    m->nq = nq;
+    m->tau_scale = d->tau_scale;
+    m->cfl = d->cfl > 0 ? d->cfl : 0.5;
+    m->pyr_form = d->pyr_form;
+    Basis B[4];
+    for (int t = 0; t < 4; ++t) B[t].init(t, N);
+    const int nfc[4] = {6, 5, 5, 4};
+
+    // --- offsets
+    int64_t dof = 0, side = 0;
+    for (int t = 0; t < 4; ++t) {
+      m->K[t] = d->nelem[t];
+      auto& td = m->td[t];
+      td.K = (int)d->nelem[t];
+      td.Np = B[t].Np;
+      td.nf = nfc[t];
+      td.dof_off = dof;
+      td.side_off = side;
+      dof += d->nelem[t] * B[t].Np;
+      side += d->nelem[t] * nfc[t];
+    }
+    m->ndof = dof;
+    m->nsides = side;
+
+    // --- face matching by sorted vertex ids
+    struct FaceKey {
+      std::array<int64_t, 4> v;
+      int64_t side;
+    };
+    std::vector<FaceKey> keys(side);
+    std::vector<int> nbr(side, -1), code(side, 0);
+    std::vector<float> tau(side, 0.f);
+    std::vector<double> taud(side, 0.0);
+    std::vector<std::array<int, 4>> skey(side);
+    for (int t = 0; t < 4; ++t) {
+      int nv = nverts(t);
+      for (int64_t e = 0; e < d->nelem[t]; ++e) {
+        const int32_t* cv = d->conn[t] + e * nv;
+        for (int f = 0; f < nfc[t]; ++f) {
+          int64_t s = m->td[t].side_off + e * nfc[t] + f;
+          int fn = face_nverts(t, f);
+          const int* fv = face_verts(t, f);
+          int64_t gid[4] = {-1, -1, -1, -1};
+          for (int c = 0; c < fn; ++c) {
+            int32_t g = cv[fv[c]];
+            if (g < 0 || g >= d->nverts) throw SetupError(DG_EINVAL, "vertex id out of range");
+            gid[c] = g;
+          }
+          int key[4];
+          canonical_key(fn, gid, key);
+          code[s] = key_to_code(fn, key);
+          for (int c = 0; c < 4; ++c) skey[s][c] = key[c];
+          FaceKey fk;
+          fk.v = {gid[0], gid[1], gid[2], gid[3]};
+          std::sort(fk.v.begin(), fk.v.begin() + fn);
+          fk.side = s;
+          keys[s] = fk;
+        }
+      }
+    }
+    std::sort(keys.begin(), keys.end(), [](const FaceKey& a, const FaceKey& b) { return a.v < b.v; });
+    for (size_t i = 0; i < keys.size();) {
+      size_t j = i + 1;
+      while (j < keys.size() && keys[j].v == keys[i].v) ++j;
+      if (j - i > 2) throw SetupError(DG_EMESH, "face shared by more than two elements");
+      if (j - i == 2) {
+        nbr[keys[i].side] = (int)keys[i + 1].side;
+        nbr[keys[i + 1].side] = (int)keys[i].side;
+      }
+      i = j;
+    }
+    // element of a side and its wave speed
+    auto side_elem = [&](int64_t s, int& t, int64_t& e, int& f) {
+      t = 3;
+      while (t > 0 && s < m->td[t].side_off) --t;
+      int64_t r = s - m->td[t].side_off;
+      e = r / nfc[t];
+      f = (int)(r % nfc[t]);
+    };
+    for (int64_t s = 0; s < side; ++s) {
+      int t, f, t2, f2;
+      int64_t e, e2;
+      side_elem(s, t, e, f);
+      double c2m = d->c2[t][e];
+      if (!(c2m > 0)) throw SetupError(DG_EINVAL, "c2 must be positive");
+      double cm = std::sqrt(c2m), cp = cm;
+      if (nbr[s] >= 0) {
+        side_elem(nbr[s], t2, e2, f2);
+        cp = std::sqrt(d->c2[t2][e2]);
+      }
+      taud[s] = 1.0 / (0.5 * (1.0 / cm + 1.0 / cp));  // 1/{rho c}, rho c = 1/c
+      tau[s] = (float)taud[s];
+    }
+
+    // --- face rules in canonical coordinates
+    std::vector<double> tpts, tw, qpts, qw;
+    tri_rule(N, tpts, tw);
+    quad_rule(N, qpts, qw);
+
+    // --- per-type geometry, operators and time-step data
+    double CT[4];
+    for (int t = 0; t < 4; ++t) CT[t] = trace_constant(B[t]);
+    std::vector<double> jsmax[4], jinvmax[4], jsj[4], taup[4], tauu[4];
+    for (int t = 0; t < 4; ++t) {
+      int K = m->td[t].K;
+      jsmax[t].assign(K, 0.0);
+      jinvmax[t].assign(K, 0.0);
+      jsj[t].assign(K, 0.0);
+      taup[t].assign(K, 0.0);
+      tauu[t].assign(K, 0.0);
+    }
+    std::vector<double> phi(512), grad(3 * 512);
+
+    for (int t = 0; t < 4; ++t) {
+      auto& td = m->td[t];
+      const int K = td.K, Np = td.Np, nf = td.nf, nv = nverts(t);
+      std::vector<float> c2f(K);
+      for (int e = 0; e < K; ++e) c2f[e] = (float)d->c2[t][e];
+      td.c2 = upload(c2f, owned);
+      std::vector<double> xv(3 * nv);
+      auto load_xv = [&](int64_t e) {
+        const int32_t* cv = d->conn[t] + e * nv;
+        for (int v = 0; v < nv; ++v)
+          for (int c = 0; c < 3; ++c) xv[3 * v + c] = d->xyz[3 * (int64_t)cv[v] + c];
+      };
+      // volume geometry
+      std::vector<float> geo;
+      std::vector<double> wedge_pts, wedge_w;
+      if (t == WEDGE) {
+        std::vector<double> tp, tww, sx, sw;
+        tri_rule(N, tp, tww);
+        gauss_jacobi(n1, 0, 0, sx, sw);
+        for (int l = 0; l < n1; ++l)
+          for (size_t q = 0; q < tww.size(); ++q) {
+            wedge_pts.insert(wedge_pts.end(), {tp[2 * q], sx[l], tp[2 * q + 1]});
+            wedge_w.push_back(tww[q] * sw[l]);
+          }
+        td.nc = (int)wedge_w.size();
+      }
+      for (int64_t e = 0; e < K; ++e) {
+        load_xv(e);
+        double F[9], G[9];
+        if (t == HEX) {
+          // x = c0 + c1 r + c2 s + c3 t + c4 rs + c5 rt + c6 st + c7 rst (coefficients c1..c7)
+          double cf[8][3] = {};
+          for (int v = 0; v < 8; ++v) {
+            const double* c = vert_rst(HEX, v);
+            double mon[8] = {1, c[0], c[1], c[2], c[0] * c[1], c[0] * c[2], c[1] * c[2],
+                             c[0] * c[1] * c[2]};
+            for (int mm = 0; mm < 8; ++mm)
+              for (int dd = 0; dd < 3; ++dd) cf[mm][dd] += 0.125 * mon[mm] * xv[3 * v + dd];
+          }
+          for (int mm = 1; mm < 8; ++mm)
+            for (int dd = 0; dd < 3; ++dd) geo.push_back((float)cf[mm][dd]);
+          geo.insert(geo.end(), {0.f, 0.f, 0.f});
+          double jmin = 1e300;
+          for (int n = 0; n < Np; ++n) {
+            map_jacobian(HEX, xv.data(), &B[t].nodes[3 * n], F);
+            double J = det3(F);
+            jmin = std::min(jmin, J);
+            jinvmax[t][e] = std::max(jinvmax[t][e], 1.0 / J);
+          }
+          if (!(jmin > 0)) throw SetupError(DG_EMESH, "hexahedron with J <= 0");
+        } else if (t == TET) {
+          double rst0[3] = {-1, -1, -1};
+          map_jacobian(TET, xv.data(), rst0, F);
+          double J = inverse_metric(F, G);
+          if (!(J > 0)) throw SetupError(DG_EMESH, "tetrahedron with J <= 0");
+          for (int i = 0; i < 9; ++i) geo.push_back((float)G[i]);
+          geo.insert(geo.end(), {(float)J, 0.f, 0.f});
+          jinvmax[t][e] = 1.0 / J;
+        } else if (t == PYR) {
+          for (int n = 0; n < Np; ++n) {
+            double a = B[t].lev_x[B[t].mk[n]][B[t].mi[n]], b = B[t].lev_x[B[t].mk[n]][B[t].mj[n]];
+            double rst[3] = {0.5 * (a - 1), 0.5 * (b - 1), 0.0};
+            map_jacobian(PYR, xv.data(), rst, F);
+            double J = inverse_metric(F, G);
+            if (!(J > 0)) throw SetupError(DG_EMESH, "pyramid with J <= 0");
+            for (int i = 0; i < 9; ++i) geo.push_back((float)G[i]);
+            geo.push_back((float)J);
+            jinvmax[t][e] = std::max(jinvmax[t][e], 1.0 / J);
+          }
+        } else {  // wedge
+          for (int q = 0; q < td.nc; ++q) {
+            map_jacobian(WEDGE, xv.data(), &wedge_pts[3 * q], F);
+            double J = inverse_metric(F, G);
+            if (!(J > 0)) throw SetupError(DG_EMESH, "wedge with J <= 0");
+            double gJ[3];
+            wedge_grad_J(xv.data(), &wedge_pts[3 * q], gJ);
+            for (int i = 0; i < 9; ++i) geo.push_back((float)G[i]);
+            for (int dd = 0; dd < 3; ++dd) {
+              double gx = G[0 + dd] * gJ[0] + G[3 + dd] * gJ[1] + G[6 + dd] * gJ[2];
+              geo.push_back((float)(gx / (2.0 * J)));
+            }
+          }
+        }
+      }
+      td.geo = upload(geo, owned);
+
+      // face geometry (non-hex: stored; all types: time-step data)
+      std::vector<float4> sgeo;
+      std::vector<float> sisq;
+      for (int64_t e = 0; e < K; ++e) {
+        load_xv(e);
+        for (int f = 0; f < nf; ++f) {
+          int64_t s = td.side_off + e * nf + f;
+          int fnv = face_nverts(t, f);
+          int key[4];
+          for (int c = 0; c < 4; ++c) key[c] = skey[s][c];
+          const std::vector<double>& pts = fnv == 3 ? tpts : qpts;
+          const std::vector<double>& w = fnv == 3 ? tw : qw;
+          const double* og = face_outward(t, f);
+          taup[t][e] = std::max(taup[t][e], taud[s]);
+          tauu[t][e] = std::max(tauu[t][e], 1.0 / taud[s]);
+          for (int q = 0; q < nq; ++q) {
+            double rst[3], d1[3], d2[3], F[9], G[9];
+            face_point(t, f, key, pts[2 * q], pts[2 * q + 1], rst, d1, d2);
+            map_jacobian(t, xv.data(), rst, F);
+            double J = inverse_metric(F, G);
+            double x1[3], x2[3], nn[3];
+            for (int dd = 0; dd < 3; ++dd) {
+              x1[dd] = F[3 * dd] * d1[0] + F[3 * dd + 1] * d1[1] + F[3 * dd + 2] * d1[2];
+              x2[dd] = F[3 * dd] * d2[0] + F[3 * dd + 1] * d2[1] + F[3 * dd + 2] * d2[2];
+              nn[dd] = G[0 + dd] * og[0] + G[3 + dd] * og[1] + G[6 + dd] * og[2];
+            }
+            double cr[3] = {x1[1] * x2[2] - x1[2] * x2[1], x1[2] * x2[0] - x1[0] * x2[2],
+                            x1[0] * x2[1] - x1[1] * x2[0]};
+            double Js = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+            double rc[3] = {d1[1] * d2[2] - d1[2] * d2[1], d1[2] * d2[0] - d1[0] * d2[2],
+                            d1[0] * d2[1] - d1[1] * d2[0]};
+            double Jsref = std::sqrt(rc[0] * rc[0] + rc[1] * rc[1] + rc[2] * rc[2]);
+            double nl = std::sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+            jsmax[t][e] = std::max(jsmax[t][e], Js / Jsref);
+            jsj[t][e] = std::max(jsj[t][e], Js / Jsref / J);
+            if (!(J > 0)) throw SetupError(DG_EMESH, "J <= 0 at a face point");
+            if (t != HEX) {
+              double wj = w[q] * Js;
+              if (t == WEDGE) wj /= std::sqrt(J);
+              sgeo.push_back(make_float4((float)(nn[0] / nl), (float)(nn[1] / nl), (float)(nn[2] / nl), (float)wj));
+              if (t == WEDGE) sisq.push_back((float)(1.0 / std::sqrt(J)));
+            }
+          }
+        }
+      }
+      if (t != HEX) {
+        td.sgeo = upload(sgeo, owned);
+        if (t == WEDGE) td.sisq = upload(sisq, owned);
+      }
+
+      // reference operators
+      if (t == HEX) {
+        std::vector<float> hc;
+        std::vector<double> l(n1), dl(n1);
+        for (int i = 0; i < n1; ++i) {
+          lagrange(B[t].r1, B[t].r1[i], l.data(), dl.data());
+          for (int mm = 0; mm < n1; ++mm) hc.push_back((float)dl[mm]);  // D1[i][m] = l_m'(r_i)
+        }
+        lagrange(B[t].r1, -1.0, l.data(), nullptr);
+        for (int i = 0; i < n1; ++i) hc.push_back((float)l[i]);
+        lagrange(B[t].r1, 1.0, l.data(), nullptr);
+        for (int i = 0; i < n1; ++i) hc.push_back((float)l[i]);
+        for (int i = 0; i < n1; ++i) hc.push_back((float)B[t].w1[i]);
+        for (int i = 0; i < n1; ++i) hc.push_back((float)B[t].r1[i]);
+        m->hexc = upload(hc, owned);
+        // local face point (iu + n1 iv) -> canonical index, per code
+        std::vector<int> perm(dgk::NCODES * nq, 0);
+        const double P[4][2] = {{-1, -1}, {1, -1}, {-1, 1}, {1, 1}};
+        for (int c = 0; c < dgk::NCODES; ++c) {
+          int key[4];
+          face_code_key(4, c, key);
+          for (int ib = 0; ib < n1; ++ib)
+            for (int ia = 0; ia < n1; ++ia) {
+              double al = B[t].r1[ia], be = B[t].r1[ib];
+              double uv[2];
+              for (int k2 = 0; k2 < 2; ++k2)
+                uv[k2] = P[key[0]][k2] + 0.5 * (1 + al) * (P[key[1]][k2] - P[key[0]][k2]) +
+                         0.5 * (1 + be) * (P[key[2]][k2] - P[key[0]][k2]);
+              int iu = 0, iv = 0;
+              for (int i = 0; i < n1; ++i) {
+                if (std::fabs(B[t].r1[i] - uv[0]) < std::fabs(B[t].r1[iu] - uv[0])) iu = i;
+                if (std::fabs(B[t].r1[i] - uv[1]) < std::fabs(B[t].r1[iv] - uv[1])) iv = i;
+              }
+              perm[c * nq + iu + n1 * iv] = ia + n1 * ib;
+            }
+        }
+        m->hexperm = upload(perm, owned);
+      } else {
+        // trace (transposed) and lift matrices per (face, code)
+        std::vector<float> Tt((size_t)nf * dgk::NCODES * Np * nq, 0.f), L((size_t)nf * dgk::NCODES * nq * Np, 0.f);
+        std::vector<double> Minv;
+        if (t == TET) {  // reference mass of the nodal basis and its inverse
+          std::vector<double> P, W;
+          volume_rule(TET, N + 2, P, W);
+          std::vector<double> M(Np * Np, 0.0);
+          for (size_t q = 0; q < W.size(); ++q) {
+            B[t].eval(&P[3 * q], phi.data(), nullptr);
+            for (int i = 0; i < Np; ++i)
+              for (int j = 0; j < Np; ++j) M[i * Np + j] += W[q] * phi[i] * phi[j];
+          }
+          m->tet_mhat = M;
+          Minv = M;
+          // Gauss-Jordan inverse
+          std::vector<double> I(Np * Np, 0.0);
+          for (int i = 0; i < Np; ++i) I[i * Np + i] = 1;
+          for (int c = 0; c < Np; ++c) {
+            int p = c;
+            for (int r = c + 1; r < Np; ++r)
+              if (std::fabs(Minv[r * Np + c]) > std::fabs(Minv[p * Np + c])) p = r;
+            for (int k = 0; k < Np; ++k) {
+              std::swap(Minv[p * Np + k], Minv[c * Np + k]);
+              std::swap(I[p * Np + k], I[c * Np + k]);
+            }
+            double dv = 1.0 / Minv[c * Np + c];
+            for (int k = 0; k < Np; ++k) { Minv[c * Np + k] *= dv; I[c * Np + k] *= dv; }
+            for (int r = 0; r < Np; ++r) {
+              if (r == c) continue;
+              double fct = Minv[r * Np + c];
+              for (int k = 0; k < Np; ++k) { Minv[r * Np + k] -= fct * Minv[c * Np + k]; I[r * Np + k] -= fct * I[c * Np + k]; }
+            }
+          }
+          Minv = I;
+          std::vector<float> mh(M.begin(), M.end());
+          m->tet_mhat_dev = upload(mh, owned);
+        }
+        for (int f = 0; f < nf; ++f) {
+          int fnv = face_nverts(t, f);
+          const std::vector<double>& pts = fnv == 3 ? tpts : qpts;
+          for (int c = 0; c < (fnv == 3 ? 6 : 8); ++c) {
+            int key[4];
+            face_code_key(fnv, c, key);
+            std::vector<double> T(nq * Np);
+            for (int q = 0; q < nq; ++q) {
+              double rst[3], d1[3], d2[3];
+              face_point(t, f, key, pts[2 * q], pts[2 * q + 1], rst, d1, d2);
+              B[t].eval(rst, phi.data(), nullptr);
+              for (int i = 0; i < Np; ++i) T[q * Np + i] = phi[i];
+            }
+            size_t base = ((size_t)f * dgk::NCODES + c) * nq * Np;
+            for (int q = 0; q < nq; ++q)
+              for (int i = 0; i < Np; ++i) {
+                Tt[base + (size_t)i * nq + q] = (float)T[q * Np + i];
+                double li = T[q * Np + i];
+                if (t == TET) {
+                  li = 0;
+                  for (int j = 0; j < Np; ++j) li += Minv[i * Np + j] * T[q * Np + j];
+                }
+                L[base + (size_t)q * Np + i] = (float)li;
+              }
+          }
+        }
+        td.Tt = upload(Tt, owned);
+        td.L = upload(L, owned);
+        // volume operators
+        std::vector<float> ops;
+        if (t == TET) {
+          // DT[a][m][n] = d l_m / d r_a (x_n)
+          std::vector<double> g(3 * Np);
+          std::vector<double> D(3 * Np * Np);
+          for (int n = 0; n < Np; ++n) {
+            B[t].eval(&B[t].nodes[3 * n], phi.data(), g.data());
+            for (int a = 0; a < 3; ++a)
+              for (int mm = 0; mm < Np; ++mm) D[(a * Np + mm) * Np + n] = g[a * Np + mm];
+          }
+          ops.assign(D.begin(), D.end());
+        } else if (t == PYR) {
+          // quadrature-free weak derivative operators (Sec. 2.3.4), factor (1+a)/2 at the test node
+          const Basis& Bp = B[t];
+          std::vector<double> c, wc;
+          gauss_jacobi(2 * N + 4, 0, 0, c, wc);
+          std::vector<double> Mc(n1 * n1, 0.0), Cc(n1 * n1, 0.0);
+          for (int n = 0; n <= N; ++n)
+            for (int k = 0; k <= N; ++k) {
+              double s1 = 0, s2 = 0;
+              for (size_t q = 0; q < c.size(); ++q) {
+                double h = 0.5 * (1 - c[q]);
+                double Pk = jacobi(N - k, 2 * k + 3, 0, c[q]), dPk = jacobi_deriv(N - k, 2 * k + 3, 0, c[q]);
+                double Pn = jacobi(N - n, 2 * n + 3, 0, c[q]);
+                s1 += wc[q] * Pk * Pn * std::pow(h, 1 + k + n);
+                double dk = dPk * std::pow(h, k) - (k > 0 ? 0.5 * k * std::pow(h, k - 1) * Pk : 0.0);
+                s2 += wc[q] * dk * Pn * std::pow(h, 2 + n);
+              }
+              double nrm = std::sqrt(Bp.gam[n] * Bp.gam[k]);
+              Mc[n * n1 + k] = s1 / nrm;
+              Cc[n * n1 + k] = s2 / nrm;
+            }
+          std::vector<double> Dr(Np * Np), Ds(Np * Np), Dt(Np * Np);
+          std::vector<double> la(n1), dla(n1), lb(n1), dlb(n1);
+          for (int row = 0; row < Np; ++row) {
+            int l = Bp.mi[row], mm = Bp.mj[row], n = Bp.mk[row];
+            double al = Bp.lev_x[n][l], bm = Bp.lev_x[n][mm];
+            for (int col = 0; col < Np; ++col) {
+              int i = Bp.mi[col], j = Bp.mj[col], k = Bp.mk[col];
+              lagrange(Bp.lev_x[k], al, la.data(), dla.data());
+              lagrange(Bp.lev_x[k], bm, lb.data(), dlb.data());
+              double fac = std::sqrt(Bp.lev_w[n][l] * Bp.lev_w[n][mm] / (Bp.lev_w[k][i] * Bp.lev_w[k][j]));
+              double dr = fac * dla[i] * lb[j] * Mc[n * n1 + k];
+              double ds = fac * la[i] * dlb[j] * Mc[n * n1 + k];
+              double dc = fac * la[i] * lb[j] * Cc[n * n1 + k];
+              Dr[row * Np + col] = dr;
+              Ds[row * Np + col] = ds;
+              Dt[row * Np + col] = 0.5 * (1 + al) * dr + 0.5 * (1 + bm) * ds + dc;
+            }
+          }
+          // D[a][m][n] = D^a_{m n} (row m), then DT[a][m][n] = D^a_{n m}
+          ops.resize(6 * Np * Np);
+          const std::vector<double>* Ds3[3] = {&Dr, &Ds, &Dt};
+          for (int a = 0; a < 3; ++a)
+            for (int i = 0; i < Np; ++i)
+              for (int j = 0; j < Np; ++j) {
+                ops[(a * Np + i) * Np + j] = (float)(*Ds3[a])[i * Np + j];
+                ops[3 * Np * Np + (a * Np + j) * Np + i] = (float)(*Ds3[a])[i * Np + j];
+              }
+        } else {  // wedge: V[nc][Np], Vg[3][nc][Np], VT[Np][nc], VgT[3][Np][nc], w[nc]
+          int nc = td.nc;
+          std::vector<double> g(3 * Np);
+          ops.assign((size_t)8 * nc * Np + nc, 0.f);
+          for (int q = 0; q < nc; ++q) {
+            B[t].eval(&wedge_pts[3 * q], phi.data(), g.data());
+            for (int i = 0; i < Np; ++i) {
+              ops[(size_t)q * Np + i] = (float)phi[i];
+              ops[(size_t)4 * nc * Np + (size_t)i * nc + q] = (float)phi[i];
+              for (int a = 0; a < 3; ++a) {
+                ops[(size_t)(1 + a) * nc * Np + (size_t)q * Np + i] = (float)g[a * Np + i];
+                ops[(size_t)(5 + a) * nc * Np + (size_t)i * nc + q] = (float)g[a * Np + i];
+              }
+            }
+            ops[(size_t)8 * nc * Np + q] = (float)wedge_w[q];
+          }
+        }
+        td.ops = upload(ops, owned);
+      }
+    }
+
+    // --- local time steps (Eq. dtK)
+    m->dt_min = 1e300;
+    for (int t = 0; t < 4; ++t) {
+      m->dtK[t].assign(m->td[t].K, 0.0);
+      for (int e = 0; e < m->td[t].K; ++e) {
+        double crk = std::max(taup[t][e], tauu[t][e] * d->c2[t][e]);
+        double cj = t == WEDGE ? jsj[t][e] : jsmax[t][e] * jinvmax[t][e];
+        double dte = m->cfl / (crk * CT[t] * cj);
+        m->dtK[t][e] = dte;
+        m->dt_min = std::min(m->dt_min, dte);
+      }
+    }
+
+    // --- side arrays, state, traces
+    m->side_nbr = upload(nbr, owned);
+    m->side_code = upload(code, owned);
+    m->side_tau = upload(tau, owned);
+    m->q = alloc_zero<float>(4 * (size_t)m->ndof, owned);
+    m->res = alloc_zero<float>(4 * (size_t)m->ndof, owned);
+    m->trace = alloc_zero<float>(4 * (size_t)m->nsides * nq, owned);
+    m->dacc = alloc_zero<double>(4, owned);
+    if (!g_host_only && cudaDeviceSynchronize() != cudaSuccess) throw SetupError(DG_ECUDA, cudaGetErrorString(cudaGetLastError()));
+    return DG_OK;
+  } catch (const SetupError& e) {
+    err = e.what();
+    return e.code;
+  } catch (const std::exception& e) {
+    err = e.what();
+    return DG_EINVAL;
+  }
+}

@@ -1,0 +1,161 @@
+"""Thin ctypes binding of libdg (include/dg.h): argument marshalling only.
+
+Every step of the computation runs inside libdg (host setup in C++, the
+right-hand side, LSRK stages and energy in CUDA kernels).  Importing this
+module raises if libdg.so has not been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdg.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libdg.so not built ({LIB_PATH}); run paper_1507_02557_b300/build.py")
+_lib = C.CDLL(LIB_PATH)
+
+HEX, WEDGE, PYR, TET = 0, 1, 2, 3
+EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_host_check", "dg_layout", "dg_ndof",
+           "dg_set_state", "dg_get_state", "dg_rhs", "dg_timestep", "dg_step", "dg_state_ptr",
+           "dg_energy", "dg_profile", "dg_adjoint_step", "dg_status_string", "dg_last_error")
+
+
+class Desc(C.Structure):
+    _fields_ = [("nverts", C.c_int64), ("xyz", C.POINTER(C.c_double)),
+                ("nelem", C.c_int64 * 4), ("conn", C.POINTER(C.c_int32) * 4),
+                ("c2", C.POINTER(C.c_double) * 4), ("N", C.c_int), ("hex_basis", C.c_int),
+                ("pyr_form", C.c_int), ("tau_scale", C.c_double), ("nlevels", C.c_int),
+                ("cfl", C.c_double), ("precision", C.c_int)]
+
+
+_vp = C.c_void_p
+_lib.dg_mesh_create.argtypes = [C.POINTER(Desc), _vp, C.POINTER(_vp)]
+_lib.dg_mesh_destroy.argtypes = [_vp]
+_lib.dg_mesh_destroy.restype = None
+_lib.dg_host_check.argtypes = [C.POINTER(Desc), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+_lib.dg_layout.argtypes = [_vp, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int)]
+_lib.dg_ndof.argtypes = [_vp, C.POINTER(C.c_int64)]
+_lib.dg_set_state.argtypes = [_vp, _vp, C.c_int]
+_lib.dg_get_state.argtypes = [_vp, _vp, C.c_int]
+_lib.dg_rhs.argtypes = [_vp, _vp, _vp, C.c_double]
+_lib.dg_timestep.argtypes = [_vp, C.POINTER(C.c_double), _vp]
+_lib.dg_step.argtypes = [_vp, C.c_int, C.c_double, C.POINTER(C.c_double)]
+_lib.dg_state_ptr.argtypes = [_vp, C.POINTER(_vp)]
+_lib.dg_energy.argtypes = [_vp, _vp, C.POINTER(C.c_double)]
+_lib.dg_profile.argtypes = [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+_lib.dg_status_string.restype = C.c_char_p
+_lib.dg_status_string.argtypes = [C.c_int]
+_lib.dg_last_error.restype = C.c_char_p
+
+
+class DGError(RuntimeError):
+    pass
+
+
+def _check(st):
+    if st != 0:
+        msg = _lib.dg_status_string(st).decode()
+        detail = _lib.dg_last_error().decode()
+        raise DGError(f"{msg} ({st}): {detail}")
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor or numpy array."""
+    if hasattr(x, "data_ptr"):
+        return _vp(x.data_ptr())
+    return x.ctypes.data_as(_vp)
+
+
+def _desc(mesh, N, tau_scale, pyr_form, cfl, keep):
+    d = Desc()
+    xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
+    keep.append(xyz)
+    d.nverts = xyz.shape[0]
+    d.xyz = xyz.ctypes.data_as(C.POINTER(C.c_double))
+    for t in range(4):
+        cn = np.ascontiguousarray(mesh.conn[t], dtype=np.int32)
+        c2 = np.ascontiguousarray(mesh.c2[t], dtype=np.float64)
+        keep += [cn, c2]
+        d.nelem[t] = cn.shape[0]
+        d.conn[t] = cn.ctypes.data_as(C.POINTER(C.c_int32))
+        d.c2[t] = c2.ctypes.data_as(C.POINTER(C.c_double))
+    d.N, d.hex_basis, d.pyr_form = N, 0, pyr_form
+    d.tau_scale, d.nlevels, d.cfl, d.precision = tau_scale, 1, cfl, 0
+    return d
+
+
+def host_check(mesh, N, tau_scale=1.0, pyr_form=0, cfl=0.5):
+    """dg_host_check: (dt_min, [C_T hex, wedge, pyr, tet]) from the host setup alone."""
+    keep = []
+    d = _desc(mesh, N, tau_scale, pyr_form, cfl, keep)
+    dt = C.c_double()
+    ct = (C.c_double * 4)()
+    _check(_lib.dg_host_check(C.byref(d), C.byref(dt), ct))
+    return dt.value, list(ct)
+
+
+class Mesh:
+    """A dg_mesh on the current CUDA device (see include/dg.h)."""
+
+    def __init__(self, mesh, N, tau_scale=1.0, pyr_form=0, cfl=0.5, stream=None):
+        keep = []
+        d = _desc(mesh, N, tau_scale, pyr_form, cfl, keep)
+        h = _vp()
+        _check(_lib.dg_mesh_create(C.byref(d), _vp(stream or 0), C.byref(h)))
+        self._h = h
+        self.N = N
+        n = C.c_int64()
+        _check(_lib.dg_ndof(h, C.byref(n)))
+        self.ndof = n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.dg_mesh_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def layout(self, t):
+        o, k, npn = C.c_int64(), C.c_int64(), C.c_int()
+        _check(_lib.dg_layout(self._h, t, C.byref(o), C.byref(k), C.byref(npn)))
+        return o.value, k.value, npn.value
+
+    def set_state(self, q, on_device):
+        _check(_lib.dg_set_state(self._h, _ptr(q), int(on_device)))
+
+    def get_state(self, out, on_device):
+        _check(_lib.dg_get_state(self._h, _ptr(out), int(on_device)))
+        return out
+
+    def state_ptr(self):
+        p = _vp()
+        _check(_lib.dg_state_ptr(self._h, C.byref(p)))
+        return p.value
+
+    def rhs(self, q_dev, rhs_dev, t=0.0):
+        _check(_lib.dg_rhs(self._h, _ptr(q_dev), _ptr(rhs_dev), float(t)))
+
+    def timestep(self):
+        dt = C.c_double()
+        _check(_lib.dg_timestep(self._h, C.byref(dt), None))
+        return dt.value
+
+    def step(self, nsteps, dt=0.0, t=0.0):
+        tt = C.c_double(t)
+        _check(_lib.dg_step(self._h, int(nsteps), float(dt), C.byref(tt)))
+        return tt.value
+
+    def profile(self, enable):
+        """Per-type kernel ms and launch counts since the last call; then (re)arm timing."""
+        ms = (C.c_double * 4)()
+        n = (C.c_int64 * 4)()
+        _check(_lib.dg_profile(self._h, int(enable), ms, n))
+        return list(ms), list(n)
+
+    def energy(self, q_dev=None):
+        E = C.c_double()
+        _check(_lib.dg_energy(self._h, _ptr(q_dev) if q_dev is not None else None, C.byref(E)))
+        return E.value

@@ -1,0 +1,131 @@
+"""CUDA path (libdg through its C ABI) against the FP64 oracle, element by element.
+
+Tolerance: relative L2 difference <= 1e-5 over all four fields (the FP32
+tolerance of the method's GPU/oracle comparison), also checked per element type.
+"""
+import numpy as np
+import pytest
+
+from oracle.dg import DGOracle
+from paper_1507_02557_b300.inputs import layered_mesh, random_state, small_hybrid_mesh
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1507_02557_b300 import dg
+    return dg
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def per_type_rel(o, a, b):
+    out = []
+    for t in range(4):
+        if o.K[t]:
+            out.append(rel(o.split(a)[t], o.split(b)[t]))
+    return out
+
+
+def gpu_rhs(lib, m, N, q32, **kw):
+    g = lib.Mesh(m, N, **kw)
+    qd = torch.from_numpy(q32).cuda()
+    rd = torch.zeros_like(qd)
+    g.rhs(qd, rd)
+    torch.cuda.synchronize()
+    return rd.cpu().numpy().astype(np.float64), g
+
+
+MESHES = {
+    "hybrid": lambda: small_hybrid_mesh(),
+    "cjump": lambda: layered_mesh(3, 3, 5, "HWHTK", seed=3, c_of_layer=lambda k: 1.0 if k % 2 == 0 else 1.5),
+    "ragged": lambda: layered_mesh(5, 3, 6, "HHWHTK", seed=5),         # odd counts, tail blocks
+    "inverted": lambda: layered_mesh(3, 2, 6, "HTKKUH", seed=2),       # both transition layers
+}
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("name", ["hybrid", "cjump", "ragged", "inverted"])
+def test_rhs_matches_oracle(lib, name, N):
+    if N >= 5 and name != "hybrid":
+        pytest.skip("high N on one mesh only")
+    m = MESHES[name]()
+    for ts in (1.0, 0.0):
+        o = DGOracle(m, N, tau_scale=ts)
+        q32 = random_state(o.ndof, 11).astype(np.float32)
+        want = o.rhs(q32.astype(np.float64))
+        got, _ = gpu_rhs(lib, m, N, q32, tau_scale=ts)
+        errs = per_type_rel(o, got, want)
+        assert rel(got, want) < TOL and max(errs) < TOL, (ts, errs)
+
+
+def test_rhs_single_type_meshes(lib):
+    for L in ("HHH", "KKK", "WWW"):
+        m = layered_mesh(2, 3, 3, L, seed=4)
+        o = DGOracle(m, 3)
+        q32 = random_state(o.ndof, 5).astype(np.float32)
+        got, _ = gpu_rhs(lib, m, 3, q32)
+        assert rel(got, o.rhs(q32.astype(np.float64))) < TOL, L
+
+
+@pytest.mark.parametrize("N", [2, 3])
+def test_lsrk_steps_match_oracle(lib, N):
+    """Ten LSRK(5,4) steps at the paper's dt from the projected standing mode."""
+    from oracle.dg import standing_mode
+    m = small_hybrid_mesh()
+    o = DGOracle(m, N)
+    q0 = o.project(standing_mode, 0.0).astype(np.float32)
+    g = lib.Mesh(m, N)
+    dt = g.timestep()
+    g.set_state(q0, on_device=False)
+    g.step(10, dt)
+    got = g.get_state(np.zeros_like(q0), on_device=False).astype(np.float64)
+    q = q0.astype(np.float64)
+    for _ in range(10):
+        q = o.lsrk_step(q, dt)
+    assert rel(got, q) < TOL, per_type_rel(o, got, q)
+
+
+def test_energy_matches_oracle(lib):
+    m = small_hybrid_mesh(seed=1)
+    o = DGOracle(m, 3)
+    q32 = random_state(o.ndof, 2).astype(np.float32)
+    g = lib.Mesh(m, 3)
+    qd = torch.from_numpy(q32).cuda()
+    E = g.energy(qd)
+    Eo = o.energy(q32.astype(np.float64))
+    assert abs(E - Eo) < 1e-6 * Eo
+
+
+def test_energy_nonincreasing_under_upwind_steps(lib):
+    m = small_hybrid_mesh()
+    o = DGOracle(m, 3)
+    q0 = o.project(lambda x, t: np.stack([np.exp(-8 * np.sum(x ** 2, 1)), 0 * x[:, 0], 0 * x[:, 0], 0 * x[:, 0]]))
+    g = lib.Mesh(m, 3)
+    g.set_state(q0.astype(np.float32), on_device=False)
+    E = [g.energy()]
+    for _ in range(5):
+        g.step(4)
+        E.append(g.energy())
+    assert all(b <= a * (1 + 1e-6) for a, b in zip(E, E[1:])), E
+
+
+def test_state_roundtrip_and_layout(lib):
+    m = small_hybrid_mesh()
+    g = lib.Mesh(m, 2)
+    o = DGOracle(m, 2)
+    assert g.ndof == o.ndof
+    for t in range(4):
+        off, K, npn = g.layout(t)
+        assert (off, K, npn) == (o.off[t], o.K[t], o.Np[t])
+    q = random_state(g.ndof, 9).astype(np.float32)
+    g.set_state(q, on_device=False)
+    back = g.get_state(np.zeros_like(q), on_device=False)
+    assert np.array_equal(back, q)

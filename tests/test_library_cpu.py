@@ -1,0 +1,70 @@
+"""libdg on the CPU: exported symbols and the host setup against the oracle (no GPU calls)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle.constants import trace_constant
+from oracle.dg import DGOracle
+from paper_1507_02557_b300.inputs import layered_mesh, small_hybrid_mesh
+
+dg = pytest.importorskip("paper_1507_02557_b300.dg")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_every_declared_symbol_is_exported():
+    hdr = open(os.path.join(ROOT, "include", "dg.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    declared = set(re.findall(r"\b(dg_[a-z_]+)\s*\(", hdr))
+    assert {"dg_mesh_create", "dg_rhs", "dg_step", "dg_energy", "dg_set_state"} <= declared
+    for name in declared:
+        assert hasattr(dg._lib, name), name
+    assert declared == set(dg.EXPORTS)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_host_setup_time_step_matches_oracle(N):
+    """Eq. dtK computed by the library's own host setup vs the oracle."""
+    m = small_hybrid_mesh()
+    dt, ct = dg.host_check(m, N)
+    o = DGOracle(m, N)
+    cto = [trace_constant(t, N) for t in range(4)]
+    assert np.allclose(ct, cto, rtol=1e-12)
+    assert abs(dt - o.global_dt(cto)) < 1e-12 * dt
+
+
+def test_host_setup_wave_speed_jump():
+    m = layered_mesh(3, 3, 5, "HWHTK", seed=3, c_of_layer=lambda k: 1.0 if k % 2 == 0 else 1.5)
+    dt, _ = dg.host_check(m, 3)
+    o = DGOracle(m, 3)
+    assert abs(dt - o.global_dt([trace_constant(t, 3) for t in range(4)])) < 1e-12 * dt
+
+
+def test_host_trace_constants_against_paper_table():
+    """Library C_T(N) vs the printed Table computedTrace (independent of the oracle)."""
+    tab = {1: [9, 9.93, 11.68, 12.22], 4: [45, 42.99, 47.59, 41.65]}
+    for N, row in tab.items():
+        _, ct = dg.host_check(small_hybrid_mesh(), N)
+        assert np.allclose(ct, row, atol=0.006)
+
+
+def test_host_setup_rejects_bad_meshes():
+    m = small_hybrid_mesh()
+    with pytest.raises(dg.DGError, match="not supported"):
+        dg.host_check(m, 7)
+    bad = small_hybrid_mesh()
+    c = bad.conn[0].copy()
+    c[0] = c[0][[1, 0, 3, 2, 5, 4, 7, 6]]          # mirrored hexahedron: J < 0
+    bad.conn[0] = c
+    with pytest.raises(dg.DGError, match="invalid mesh"):
+        dg.host_check(bad, 2)
+    dup = small_hybrid_mesh()
+    dup.conn[0] = np.concatenate([dup.conn[0], dup.conn[0][:1]])   # a face shared three times
+    dup.c2[0] = np.concatenate([dup.c2[0], dup.c2[0][:1]])
+    with pytest.raises(dg.DGError, match="invalid mesh"):
+        dg.host_check(dup, 2)
+    neg = small_hybrid_mesh()
+    neg.c2[3] = -neg.c2[3]
+    with pytest.raises(dg.DGError, match="invalid argument"):
+        dg.host_check(neg, 2)
