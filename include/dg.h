@@ -121,6 +121,20 @@ dg_status dg_state_ptr(dg_mesh *mesh, float **q_dev);
  * (NULL = the mesh's state).  Synchronises. */
 dg_status dg_energy(dg_mesh *mesh, const float *q_dev, double *E);
 
+/* dg_energy for callers that cannot allocate device memory while they run
+ * (inside a CUDA stream capture, in real-time loops that cannot take allocator
+ * latency, or under a framework that has reserved all device memory).  No
+ * counterpart in the paper.  Same result as dg_energy (summed in a fixed order,
+ * so bitwise reproducible); allocates nothing: the per-element partial sums live
+ * in a static device array of 2^20 + 1 doubles (8 MiB) that every GPU loading
+ * libdg holds until exit.  Meshes with more than 2^20 elements are rejected
+ * with DG_EINVAL.  The first call on a device looks up that array's address
+ * (cudaGetSymbolAddress) with the mesh's device current; make that first call
+ * before any stream capture.  The array is shared by all calls and keeps the
+ * last call's contents; calls that overlap on the GPU race on it.
+ * Synchronises. */
+dg_status dg_energy_noalloc(dg_mesh *mesh, const float *q_dev, double *E);
+
 /* Per-type kernel timing.  ms and launches (4 entries each, hex, wedge,
  * pyramid, tet; either may be NULL) receive the kernel time (CUDA events
  * recorded on the mesh's stream around each launch) and the launch count

@@ -9,7 +9,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libdg.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["refelem.cpp", "setup.cpp", "api.cpp", "kernels.cu"]
+SOURCES = ["refelem.cpp", "setup.cpp", "api.cpp", "kernels.cu", "noalloc.cu"]
 
 
 def nvcc():

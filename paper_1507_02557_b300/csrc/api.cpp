@@ -24,6 +24,8 @@ dg_status cuda_fail(cudaError_t e) {
 }
 }  // namespace
 
+void dg_set_last_error(const std::string& msg) { g_err = msg; }
+
 extern "C" {
 
 const char* dg_status_string(dg_status s) {

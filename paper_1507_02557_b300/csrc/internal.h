@@ -69,6 +69,9 @@ cudaError_t launch_stage(dg_mesh* m, float* q, float* res, const float* tin, flo
 cudaError_t launch_energy(dg_mesh* m, const float* q, double* acc);
 }  // namespace dgk
 
+// Message returned by dg_last_error() on this thread (api.cpp).
+void dg_set_last_error(const std::string& msg);
+
 // Host setup (setup.cpp).
 dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err);
 void dg_free(dg_mesh* m);
