@@ -1,11 +1,15 @@
-"""Throughput benchmark: GDOF-stage/s of the hybrid-mesh DG right-hand side + LSRK(5,4) stage.
+"""Throughput benchmark: GDOF-stage/s of the hybrid-mesh DG right-hand side + time-step update.
 
 Workload: the 64x64x80-cell layered hybrid mesh on [-1,1]^3 (layers
 H x34 | W x2 | H x36 | T | K x4 | U | H x2: 294,912 hex, 16,384 wedges, 40,960
 pyramids, 114,688 tets), order N = 4 (44,359,680 DOFs x 4 fields), wave speed
-1.0 / 1.5 alternating by layer, upwind flux.  One step = one LSRK(5,4) step (five
-right-hand-side evaluations and stage updates) over the whole mesh, all element
-types.  GDOF-stage/s = ndof * 5 * steps / time.
+1.0 / 1.5 alternating by layer, upwind flux, two time-step levels.
+
+Headline: one step = one coarse step of the two-level multi-rate AB3 scheme
+(every element's rhs once, the fine level's rhs a second time, AB3 updates);
+GDOF-stage/s = (ndof + ndof_fine) * steps / time, i.e. the element-stages
+actually performed.  Beside it ("single_rate"): one step = one LSRK(5,4) step
+(five fused stage kernels per element type), GDOF-stage/s = ndof * 5 * steps / time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
 
@@ -35,7 +39,7 @@ ORDER = 4
 
 def workload_config(nx, N, extra=None):
     cfg = {"workload": f"layered hybrid mesh {nx}x{nx}x80 cells, N={N}, c=1.0/1.5 by layer, upwind, "
-                       "LSRK(5,4) single-rate",
+                       "two-level multi-rate",
            "cells": [nx, nx, 80], "order": N, "l2_flush": "state 710 MB > 126 MB L2 (no flush needed)"}
     if extra:
         cfg.update(extra)
@@ -140,11 +144,28 @@ def run_reference(args, rank, world):
 
 
 def hex_alg_bytes(N):
-    """Algorithmic bytes of one hex element in the fused stage kernel and the trace kernel."""
+    """Algorithmic bytes of one hex element: fused LSRK stage, trace-only and rhs-only launches."""
     NP, NQ = (N + 1) ** 3, (N + 1) ** 2
-    stage = 4 * NP * 4 * 4 + 96 + 4 + 6 * 12 + 2 * 6 * NQ * 8   # q,res r/w; geometry; c2; sides; traces r+w
-    trace = 4 * NP * 4 + 96 + 6 * 12 + 6 * NQ * 8
-    return stage, trace
+    side = 96 + 6 * 12                                          # trilinear geometry + per-face side data
+    stage = 4 * NP * 4 * 4 + side + 4 + 2 * 6 * NQ * 8          # q,res read+write; c2; traces read+write
+    trace = 4 * NP * 4 + side + 6 * NQ * 8                      # q read; traces written
+    rhs = 4 * NP * 4 * 2 + side + 4 + 6 * NQ * 8                # q read, rhs written; traces read
+    return stage, trace, rhs
+
+
+def timed_run(g, torch, stream, steps, dt, barrier):
+    """K steps inside CUDA events on the library's stream; per-type kernel ms and launches."""
+    g.profile(1)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    local = torch.cuda.current_device()
+    with Clocks(local) as clk:
+        barrier()
+        ev0.record(stream)
+        g.step(steps, dt)
+        ev1.record(stream)
+        barrier()
+    kms, launches = g.profile(0)
+    return ev0.elapsed_time(ev1), kms, launches, clk.summary()
 
 
 def main():
@@ -172,91 +193,116 @@ def main():
         dist.init_process_group("nccl")
     from paper_1507_02557_b300 import dg
     from paper_1507_02557_b300.inputs import random_state, scale_mesh
+    import json
 
     mesh = scale_mesh(args.cells, args.cells)
     stream = torch.cuda.current_stream()
-    g = dg.Mesh(mesh, ORDER, stream=stream.cuda_stream)
-    ndof = g.ndof
-    q0 = (1e-3 * random_state(ndof, 1 + rank)).astype(np.float32)
-    g.set_state(q0, on_device=False)
-    dt = g.timestep()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    K_hex = mesh.nelem[0]
+    b_stage, b_trace, b_rhs = hex_alg_bytes(ORDER)
 
     def barrier():
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
 
-    # warm-up, then K timed steps (one dg_step call), per-type kernel events on the same stream
-    g.step(args.warmup, dt)
-    barrier()
-    g.profile(1)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with Clocks(local) as clk:
-        barrier()
-        ev0.record(stream)
-        g.step(args.steps, dt)
-        ev1.record(stream)
-        barrier()
-    ms = ev0.elapsed_time(ev1)
-    kms, launches = g.profile(0)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    stage_units = ndof * 5 * args.steps * world
-    value = stage_units / (ms / 1e3) / 1e9
+    def max_ms(ms):
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+        return ms
 
-    # dominant kernel roofline: the hexahedron stage kernel
-    import json as _json
-    peaks = {}
-    try:
-        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
-    hbm = float(peaks.get("hbm_gbs", 6400.0))
-    K_hex = mesh.nelem[0]
-    b_stage, b_trace = hex_alg_bytes(ORDER)
+    # ---- single-rate LSRK(5,4): fused stage kernels
+    g1 = dg.Mesh(mesh, ORDER, stream=stream.cuda_stream, nlevels=1)
+    ndof = g1.ndof
+    q0 = (1e-3 * random_state(ndof, 1 + rank)).astype(np.float32)
+    g1.set_state(q0, on_device=False)
+    dt = g1.timestep()
+    g1.step(args.warmup, dt)
+    ms1, kms1, l1, clk1 = timed_run(g1, torch, stream, args.steps, dt, barrier)
+    ms1 = max_ms(ms1)
     n_stage = 5 * args.steps
-    n_trace = launches[0] - n_stage
-    hex_bytes = K_hex * (b_stage * n_stage + b_trace * n_trace)
+    hex_bytes1 = K_hex * (b_stage * n_stage + b_trace * (l1[0] - n_stage))
+    ach1 = hex_bytes1 / (kms1[0] / 1e3) / 1e9
+    single = {"value": ndof * 5 * args.steps * world / (ms1 / 1e3) / 1e9, "unit": METRIC,
+              "ms_per_step": ms1 / args.steps, "integrator": "LSRK(5,4), 5 stages per step",
+              "kernel_ms": dict(zip(["hex", "wedge", "pyramid", "tet"], kms1)),
+              "hex_stage_kernel": {"achieved": ach1, "peak": hbm, "unit": "GB/s", "frac": ach1 / hbm},
+              "gpu_launches": int(sum(l1))}
+    del g1
+    torch.cuda.synchronize()
+
+    # ---- two-level multi-rate AB3 (the workload as specified): headline
+    g = dg.Mesh(mesh, ORDER, stream=stream.cuda_stream, nlevels=2)
+    g.set_state(q0, on_device=False)
+    h = g.timestep()
+    fine = g.level_type_counts(2)
+    npe = [(ORDER + 1) ** 3, (ORDER + 1) ** 2 * (ORDER + 2) // 2,
+           (ORDER + 1) * (ORDER + 2) * (2 * ORDER + 3) // 6, (ORDER + 1) * (ORDER + 2) * (ORDER + 3) // 6]
+    ndof_fine = sum(c * n for c, n in zip(fine, npe))
+    g.step(args.warmup, h)                                   # includes the LSRK start-up
+    ms, kms, launches, clk = timed_run(g, torch, stream, args.steps, h, barrier)
+    ms = max_ms(ms)
+    stage_units = (ndof + ndof_fine) * args.steps * world    # rhs evaluations actually performed
+    value = stage_units / (ms / 1e3) / 1e9
+    # hex kernels per coarse step: traces of all hexes twice, rhs of all hexes + the fine ones again
+    hex_bytes = args.steps * (2 * K_hex * b_trace + (K_hex + fine[0]) * b_rhs)
     achieved = hex_bytes / (kms[0] / 1e3) / 1e9
     traffic = None
-    tfile = os.path.join(ROOT, "profiles", "hex_stage_traffic.json")
-    if os.path.exists(tfile):
-        try:
-            traffic = _json.load(open(tfile)).get("bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
-
-    # end to end through the public API: per step, H2D of the state from pinned host memory,
-    # one LSRK step, and the step's energy read back to the host
+    # end to end through the public API with host buffers: one simulation call = H2D of the
+    # state from pinned host memory, K coarse steps (the first call after dg_set_state also runs
+    # the LSRK start-up of the history: 4 LSRK steps + 3 rhs, counted as performed stages),
+    # D2H of the final state into pinned host memory
     pinned = torch.from_numpy(q0).pin_memory()
+    out_h = torch.empty_like(pinned).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    g.set_state(pinned, on_device=False)
+    g.step(args.steps, h)
+    g.get_state(out_h, on_device=False)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_units = ((ndof + ndof_fine) * args.steps + 23 * ndof) * world
+    e2e = {"value": e2e_units / e2e_s / 1e9, "unit": METRIC,
+           "h2d_bytes_per_step": 4 * ndof * 4 / args.steps, "d2h_bytes_per_step": 4 * ndof * 4 / args.steps,
+           "steps": args.steps,
+           "note": "one public-API call sequence: dg_set_state(host) + dg_step(K) + dg_get_state(host), "
+                   "including the history start-up; copies amortised over the K steps"}
+    # per step re-upload (single-rate path has no history): H2D state + 1 LSRK step + energy to host
+    g1 = dg.Mesh(mesh, ORDER, stream=stream.cuda_stream, nlevels=1)
     barrier()
     t0 = time.perf_counter()
     e_steps = max(3, min(args.steps, 20))
     for _ in range(e_steps):
-        g.set_state(pinned, on_device=False)
-        g.step(1, dt)
-        g.energy()
+        g1.set_state(pinned, on_device=False)
+        g1.step(1, dt)
+        g1.energy()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": ndof * 5 * e_steps * world / e2e_s / 1e9, "unit": METRIC,
-           "h2d_bytes_per_step": 4 * ndof * 4, "d2h_bytes_per_step": 8, "steps": e_steps}
+    e2 = time.perf_counter() - t0
+    single["e2e_per_step_upload"] = {"value": ndof * 5 * e_steps * world / e2 / 1e9, "unit": METRIC,
+                                     "h2d_bytes_per_step": 4 * ndof * 4, "d2h_bytes_per_step": 8}
+    del g1
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(args.cells, ORDER, {
-                    "ndof": ndof, "elements": mesh.nelem, "dt": dt,
-                    "parallelism": "replicas" if world > 1 else "single GPU"}),
-                "roofline": {"bound": "hbm", "kernel": "hex_kernel<4,STAGE>", "achieved": achieved,
-                             "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-                             "alg_bytes_per_launch": K_hex * b_stage,
-                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+                    "integrator": "two-level multi-rate AB3 (step = one coarse step of 2h)",
+                    "ndof": ndof, "ndof_fine": ndof_fine, "elements": mesh.nelem, "fine_elements": fine,
+                    "h_fine": h, "parallelism": "replicas" if world > 1 else "single GPU"}),
+                "roofline": {"bound": "hbm", "kernel": "hexw_kernel<4,TRACE|RHS> (multi-rate)",
+                             "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                             "traffic": traffic, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
                 "kernel_ms": dict(zip(["hex", "wedge", "pyramid", "tet"], kms)),
-                "gpu_launches": int(sum(launches)),
-                "e2e": e2e, "clocks": clk.summary()}
+                "gpu_launches": int(sum(launches)) + 2 * 4 * args.steps,
+                "single_rate": single, "e2e": e2e, "clocks": clk}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

@@ -70,7 +70,7 @@ typedef struct {
   int hex_basis;           /* 0 = GL nodes (only value built) */
   int pyr_form;            /* 0 = skew-symmetric, 1 = strong (identical results, Sec. 2.2) */
   double tau_scale;        /* 1 = upwind, 0 = central flux */
-  int nlevels;             /* 1 = single-rate (only value built) */
+  int nlevels;             /* 1 = single-rate LSRK(5,4); 2 = two-level multi-rate AB3 */
   double cfl;              /* C of Eq. (dtK); <= 0 selects 0.5 */
   int precision;           /* 0 = FP32 (only value built) */
 } dg_mesh_desc;
@@ -83,16 +83,21 @@ dg_status dg_mesh_create(const dg_mesh_desc *desc, void *stream, dg_mesh **out);
 void dg_mesh_destroy(dg_mesh *mesh);
 
 /* Run the host part of dg_mesh_create only (face matching, geometry checks,
- * reference operators, Eq. dtK) without touching any GPU.  Returns the global
- * time step in *dt_min and, if trace_const is not NULL, the reference trace
- * constants C_T(N) of hex, wedge, pyramid, tet (Appendix B) in trace_const[4].
- * Same error codes as dg_mesh_create. */
-dg_status dg_host_check(const dg_mesh_desc *desc, double *dt_min, double *trace_const);
+ * reference operators, Eq. dtK, multi-rate levels) without touching any GPU.
+ * Returns the global time step in *dt_min; if not NULL, trace_const[4] receives
+ * the reference trace constants C_T(N) of hex, wedge, pyramid, tet (Appendix B)
+ * and level_count[nlevels] the element count of each time-step level (coarse
+ * first).  Same error codes as dg_mesh_create. */
+dg_status dg_host_check(const dg_mesh_desc *desc, double *dt_min, double *trace_const,
+                        int64_t *level_count);
 
 /* DOF layout of one element type: offset of its first DOF within a field,
  * its element count and DOFs per element. */
 dg_status dg_layout(const dg_mesh *mesh, int type, int64_t *offset, int64_t *nelem, int *Np);
 dg_status dg_ndof(const dg_mesh *mesh, int64_t *ndof);
+/* Elements of each type (counts[4]: hex, wedge, pyramid, tet) in time-step
+ * level `level` (1 = coarsest .. nlevels = finest, Sec. 2.4). */
+dg_status dg_level_counts(const dg_mesh *mesh, int level, int64_t *counts);
 
 /* Copy a state [4][ndof] into the mesh's state (and zero the LSRK residual).
  * q is a host pointer (on_device = 0) or a device pointer (on_device = 1). */
@@ -110,8 +115,14 @@ dg_status dg_rhs(dg_mesh *mesh, const float *q_dev, float *rhs_dev, double t);
  * each multi-rate level (nlevels entries). */
 dg_status dg_timestep(const dg_mesh *mesh, double *dt_min, int64_t *level_count);
 
-/* Advance the mesh's state by nsteps LSRK(5,4) steps of size dt (dt <= 0 uses
- * dtau_min).  *t_inout (may be NULL) is advanced by nsteps*dt.  Asynchronous. */
+/* Advance the mesh's state (dt <= 0 uses dtau_min).  Asynchronous.
+ *   nlevels = 1: nsteps LSRK(5,4) steps of size dt; *t_inout += nsteps*dt.
+ *   nlevels = 2: nsteps coarse steps of the two-level multi-rate Adams-Bashforth-3
+ *     scheme (reading of Sec. 2.4): fine elements step dt twice, coarse elements
+ *     step 2 dt once, coarse states at the half step are predicted from their
+ *     AB3 history.  The first call after dg_set_state first runs the start-up
+ *     (four LSRK(5,4) steps of size dt that record the rhs history);
+ *     *t_inout += 4 dt (start-up) + nsteps * 2 dt. */
 dg_status dg_step(dg_mesh *mesh, int nsteps, double dt, double *t_inout);
 
 /* Direct access to the device state [4][ndof] owned by the mesh. */

@@ -408,3 +408,94 @@ def standing_mode(x, time):
     a = np.sin(w) / np.sqrt(3.0)
     return np.stack([p, a * s[:, 0] * c[:, 1] * c[:, 2], a * c[:, 0] * s[:, 1] * c[:, 2],
                      a * c[:, 0] * c[:, 1] * s[:, 2]])
+
+
+# ---------------------------------------------------------------------- multi-rate AB3
+AB3 = np.array([23.0, -16.0, 5.0]) / 12.0          # int_0^1 of the quadratic through r^n, r^{n-1}, r^{n-2}
+AB3_HALF = np.array([17.0, -7.0, 2.0]) / 24.0      # int_0^{1/2} of the same quadratic
+
+
+def mr_levels(dg, CT, nlevels, cfl=0.5):
+    """Multi-rate levels of Sec. 2.4 (level 1 = coarsest, nlevels = finest).
+
+    dtau_lev = 2^(nlevels - lev) dtau_min.  Reading of the binning (the printed
+    inequality is reversed): element K gets the coarsest level whose step does
+    not exceed dtau_K.  A second sweep moves elements to finer levels until
+    face neighbours differ by at most one level.  Returns per-type int arrays.
+    """
+    dts = dg.local_dt(CT, cfl)
+    dmin = min(float(np.min(d)) for d in dts if len(d))
+    lev = []
+    for d in dts:
+        lv = np.full(len(d), nlevels, dtype=int)
+        for idx in range(len(d)):
+            for L in range(1, nlevels + 1):
+                if (2.0 ** (nlevels - L)) * dmin <= d[idx] * (1 + 1e-12):
+                    lv[idx] = L
+                    break
+        lev.append(lv)
+    sides = dg.geo.sides
+    changed = True
+    while changed:
+        changed = False
+        for s in sides:
+            if s.nbr < 0:
+                continue
+            o = sides[s.nbr]
+            a, b = lev[s.t][s.e], lev[o.t][o.e]
+            if a < b - 1:
+                lev[s.t][s.e] = b - 1
+                changed = True
+    return lev, dmin
+
+
+class MRAB3:
+    """Two-level multi-rate Adams-Bashforth 3 (reading of Sec. 2.4; details of the
+    scheme are deferred by the paper to other work).
+
+    Fine step h, coarse step 2h.  Per coarse step from t_n:
+      r = rhs(q) for all elements;
+      fine:    q_f <- q_f + h sum AB3 * (r_f^n, r_f^{n-1}, r_f^{n-2});
+      coarse:  predicted q_c(t_n + h) = q_c + 2h sum AB3_HALF * (r_c^n, r_c^{n-1}, r_c^{n-2});
+      r' = rhs(q_f, predicted q_c), fine part only;
+      fine:    q_f <- q_f + h sum AB3 * (r'_f, r_f^n, r_f^{n-1});
+      coarse:  q_c <- q_c + 2h sum AB3 * (r_c^n, r_c^{n-1}, r_c^{n-2}).
+    Start-up: four LSRK(5,4) steps of size h, recording rhs at t = 0, 2h (coarse
+    history) and 2h, 3h (fine history).
+    """
+
+    def __init__(self, dg, level):
+        self.dg = dg
+        mask = np.zeros((4, dg.ndof), dtype=bool)
+        mv = dg.split(mask)
+        for t in range(4):
+            mv[t][:] = (level[t] == 2)[None, :, None]
+        self.fine = mask
+        self.coarse = ~mask
+
+    def start(self, q, h):
+        """Returns (q(4h), history) with history = (coarse [r(2h), r(0)], fine [r(3h), r(2h)])."""
+        dg = self.dg
+        r0 = dg.rhs(q)
+        q = dg.lsrk_step(q, h)
+        q = dg.lsrk_step(q, h)
+        r2 = dg.rhs(q)
+        q = dg.lsrk_step(q, h)
+        r3 = dg.rhs(q)
+        q = dg.lsrk_step(q, h)
+        return q, ([r2, r0], [r3, r2])
+
+    def step(self, q, hist, h):
+        dg = self.dg
+        F, Cm = self.fine, self.coarse
+        (c1, c2), (f1, f2) = hist
+        r = dg.rhs(q)
+        qn = q.copy()
+        qn[F] = q[F] + h * (AB3[0] * r[F] + AB3[1] * f1[F] + AB3[2] * f2[F])
+        pred = qn.copy()
+        pred[Cm] = q[Cm] + 2 * h * (AB3_HALF[0] * r[Cm] + AB3_HALF[1] * c1[Cm] + AB3_HALF[2] * c2[Cm])
+        rh = dg.rhs(pred)
+        out = qn.copy()
+        out[F] = qn[F] + h * (AB3[0] * rh[F] + AB3[1] * r[F] + AB3[2] * f1[F])
+        out[Cm] = q[Cm] + 2 * h * (AB3[0] * r[Cm] + AB3[1] * c1[Cm] + AB3[2] * c2[Cm])
+        return out, ([r, c1], [rh, r])

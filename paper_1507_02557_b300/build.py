@@ -7,8 +7,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libdg.so")
-BUILD = os.path.join(ROOT, "_build")
+BUILD = os.environ.get("DG_BUILD_DIR", os.path.join(ROOT, "_build"))
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+EXTRA = os.environ.get("DG_NVCC_FLAGS", "").split()   # extra nvcc flags (variant builds)
 SOURCES = ["refelem.cpp", "setup.cpp", "api.cpp", "kernels.cu", "noalloc.cu"]
 
 
@@ -26,7 +27,7 @@ def build(verbose=False):
         deps = [src] + [os.path.join(SRC, h) for h in os.listdir(SRC) if h.endswith(".h")]
         deps.append(os.path.join(ROOT, "include", "dg.h"))
         if not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(d) for d in deps):
-            cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
+            cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2"] + EXTRA + [
                    "-I", os.path.join(ROOT, "include"), "-I", SRC, "-c", src, "-o", obj]
             if verbose:
                 print(" ".join(cmd), flush=True)

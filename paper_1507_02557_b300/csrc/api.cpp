@@ -51,8 +51,8 @@ dg_status dg_mesh_create(const dg_mesh_desc* d, void* stream, dg_mesh** out) {
     g_err = "N must be in 1..6";
     return DG_ENOTSUP;
   }
-  if (d->hex_basis != 0 || d->nlevels > 1 || d->precision != 0) {
-    g_err = "only GL hexahedra, single-rate stepping and FP32 are built";
+  if (d->hex_basis != 0 || d->nlevels > 2 || d->precision != 0) {
+    g_err = "only GL hexahedra, one or two time-step levels and FP32 are built";
     return DG_ENOTSUP;
   }
   if (d->nverts <= 0 || !d->xyz) return DG_EINVAL;
@@ -77,9 +77,9 @@ dg_status dg_mesh_create(const dg_mesh_desc* d, void* stream, dg_mesh** out) {
   return DG_OK;
 }
 
-dg_status dg_host_check(const dg_mesh_desc* d, double* dt_min, double* trace_const) {
+dg_status dg_host_check(const dg_mesh_desc* d, double* dt_min, double* trace_const, int64_t* level_count) {
   if (!d || d->nverts <= 0 || !d->xyz) return DG_EINVAL;
-  if (d->N < 1 || d->N > dgk::MAXN) return DG_ENOTSUP;
+  if (d->N < 1 || d->N > dgk::MAXN || d->nlevels > 2) return DG_ENOTSUP;
   for (int t = 0; t < 4; ++t)
     if (d->nelem[t] < 0 || (d->nelem[t] > 0 && (!d->conn[t] || !d->c2[t]))) return DG_EINVAL;
   dg_mesh m;
@@ -93,6 +93,8 @@ dg_status dg_host_check(const dg_mesh_desc* d, double* dt_min, double* trace_con
   if (dt_min) *dt_min = m.dt_min;
   if (trace_const)
     for (int t = 0; t < 4; ++t) trace_const[t] = ct[t];
+  if (level_count)
+    for (int L = 0; L < m.nlevels; ++L) level_count[L] = m.level_count[L];
   return DG_OK;
 }
 
@@ -109,6 +111,12 @@ dg_status dg_layout(const dg_mesh* m, int type, int64_t* offset, int64_t* nelem,
   if (offset) *offset = m->td[type].dof_off;
   if (nelem) *nelem = m->td[type].K;
   if (Np) *Np = m->td[type].Np;
+  return DG_OK;
+}
+
+dg_status dg_level_counts(const dg_mesh* m, int level, int64_t* counts) {
+  if (!m || !counts || level < 1 || level > m->nlevels) return DG_EINVAL;
+  for (int t = 0; t < 4; ++t) counts[t] = m->nlevels == 1 ? m->td[t].K : m->lev[level - 1].count[t];
   return DG_OK;
 }
 
@@ -132,6 +140,7 @@ dg_status dg_set_state(dg_mesh* m, const float* q, int on_device) {
   if (e != cudaSuccess) return cuda_fail(e);
   e = cudaMemsetAsync(m->res, 0, bytes, m->stream);
   if (e != cudaSuccess) return cuda_fail(e);
+  m->mr_started = false;
   return DG_OK;
 }
 
@@ -162,28 +171,106 @@ dg_status dg_rhs(dg_mesh* m, const float* q, float* rhs, double t) {
 dg_status dg_timestep(const dg_mesh* m, double* dt_min, int64_t* level_count) {
   if (!m || !dt_min) return DG_EINVAL;
   *dt_min = m->dt_min;
-  if (level_count) level_count[0] = m->td[0].K + m->td[1].K + m->td[2].K + m->td[3].K;
+  if (level_count)
+    for (int L = 0; L < m->nlevels; ++L) level_count[L] = m->level_count[L];
   return DG_OK;
 }
 
-dg_status dg_step(dg_mesh* m, int nsteps, double dt, double* t_inout) {
-  if (!m || nsteps < 0) return DG_EINVAL;
-  if (!(dt > 0)) dt = m->dt_min;
-  if (nsteps == 0) return DG_OK;
+}  // extern "C"
+
+namespace {
+
+// nsteps single-rate LSRK(5,4) steps: one trace launch, then fused stage kernels (ping-pong traces).
+cudaError_t lsrk_steps(dg_mesh* m, int nsteps, double dt) {
   const size_t plane2 = 2 * (size_t)m->nsides * m->nq;
   float* buf[2] = {m->trace, m->trace + plane2};
   cudaError_t e = dgk::launch_trace(m, m->q, buf[0]);
-  if (e != cudaSuccess) return cuda_fail(e);
+  if (e != cudaSuccess) return e;
   int cur = 0;
   for (int s = 0; s < nsteps; ++s)
     for (int k = 0; k < 5; ++k) {
       e = dgk::launch_stage(m, m->q, m->res, buf[cur], buf[cur ^ 1], (float)RK_A[k], (float)RK_B[k], (float)dt);
-      if (e != cudaSuccess) return cuda_fail(e);
+      if (e != cudaSuccess) return e;
       cur ^= 1;
     }
+  return cudaSuccess;
+}
+
+// rhs of the current state for the elements of sel, into slot (all traces refreshed first).
+cudaError_t rhs_to(dg_mesh* m, const float* q, float* slot, const dgk::Sel& sel) {
+  cudaError_t e = dgk::launch_trace(m, q, m->trace);
+  if (e != cudaSuccess) return e;
+  return dgk::launch_rhs_sel(m, q, m->trace, slot, sel);
+}
+
+// Two-level multi-rate AB3 (reading of Sec. 2.4), fine step h, coarse step 2h.
+// Start-up: four LSRK(5,4) steps of size h, recording rhs at t = 0, 2h, 3h.
+cudaError_t mrab3(dg_mesh* m, int nsteps, double h) {
+  const size_t fs = 4 * (size_t)m->ndof;
+  float* H[3] = {m->hist, m->hist + fs, m->hist + 2 * fs};
+  const dgk::Sel &C = m->lev[0], &F = m->lev[1];
+  cudaError_t e;
+  if (!m->mr_started) {
+    if ((e = rhs_to(m, m->q, H[2], m->all)) != cudaSuccess) return e;   // r(0)
+    if ((e = lsrk_steps(m, 2, h)) != cudaSuccess) return e;
+    if ((e = rhs_to(m, m->q, H[1], m->all)) != cudaSuccess) return e;   // r(2h)
+    if ((e = lsrk_steps(m, 1, h)) != cudaSuccess) return e;
+    if ((e = rhs_to(m, m->q, H[0], m->all)) != cudaSuccess) return e;   // r(3h)
+    if ((e = lsrk_steps(m, 1, h)) != cudaSuccess) return e;
+    m->cslot[0] = 0; m->cslot[1] = 1; m->cslot[2] = 2;   // coarse: new r^n, r(2h), r(0)
+    m->fslot[0] = 2; m->fslot[1] = 0; m->fslot[2] = 1;   // fine:   new r^n, r(3h), r(2h)
+    m->mr_started = true;
+  }
+  const float a0 = 23.f / 12.f, a1 = -16.f / 12.f, a2 = 5.f / 12.f;
+  const float b0 = 17.f / 24.f, b1 = -7.f / 24.f, b2 = 2.f / 24.f;
+  const float hf = (float)h, hc = (float)(2 * h);
+  float* pred = m->res;   // predicted coarse state (the LSRK residual is free between start-ups)
+  for (int s = 0; s < nsteps; ++s) {
+    int* c = m->cslot;
+    int* f = m->fslot;
+    // rhs at t_n: coarse -> H[c0], fine -> H[f0]
+    if ((e = dgk::launch_trace(m, m->q, m->trace)) != cudaSuccess) return e;
+    if ((e = dgk::launch_rhs_sel(m, m->q, m->trace, H[c[0]], C)) != cudaSuccess) return e;
+    if ((e = dgk::launch_rhs_sel(m, m->q, m->trace, H[f[0]], F)) != cudaSuccess) return e;
+    // fine AB3 to t_n + h; coarse prediction at t_n + h
+    if ((e = dgk::launch_ab(m, F, m->q, m->q, H[f[0]], H[f[1]], H[f[2]], hf * a0, hf * a1, hf * a2)) != cudaSuccess) return e;
+    if ((e = dgk::launch_ab(m, C, m->q, pred, H[c[0]], H[c[1]], H[c[2]], hc * b0, hc * b1, hc * b2)) != cudaSuccess) return e;
+    // traces at t_n + h (fine: state, coarse: prediction), fine rhs -> H[f2]
+    if ((e = dgk::launch_trace_sel(m, m->q, m->trace, F)) != cudaSuccess) return e;
+    if ((e = dgk::launch_trace_sel(m, pred, m->trace, C)) != cudaSuccess) return e;
+    if ((e = dgk::launch_rhs_sel(m, m->q, m->trace, H[f[2]], F)) != cudaSuccess) return e;
+    // fine AB3 to t_n + 2h; coarse AB3 to t_n + 2h
+    if ((e = dgk::launch_ab(m, F, m->q, m->q, H[f[2]], H[f[0]], H[f[1]], hf * a0, hf * a1, hf * a2)) != cudaSuccess) return e;
+    if ((e = dgk::launch_ab(m, C, m->q, m->q, H[c[0]], H[c[1]], H[c[2]], hc * a0, hc * a1, hc * a2)) != cudaSuccess) return e;
+    // rotate histories
+    int f0 = f[0], f1 = f[1], f2 = f[2];
+    f[0] = f1; f[1] = f2; f[2] = f0;
+    int c0 = c[0], c1 = c[1], c2 = c[2];
+    c[0] = c2; c[1] = c0; c[2] = c1;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" dg_status dg_step(dg_mesh* m, int nsteps, double dt, double* t_inout) {
+  if (!m || nsteps < 0) return DG_EINVAL;
+  if (!(dt > 0)) dt = m->dt_min;
+  if (nsteps == 0) return DG_OK;
+  if (m->nlevels == 2) {
+    bool fresh = !m->mr_started;
+    cudaError_t e = mrab3(m, nsteps, dt);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (t_inout) *t_inout += (fresh ? 4 * dt : 0.0) + nsteps * 2 * dt;
+    return DG_OK;
+  }
+  cudaError_t e = lsrk_steps(m, nsteps, dt);
+  if (e != cudaSuccess) return cuda_fail(e);
   if (t_inout) *t_inout += nsteps * dt;
   return DG_OK;
 }
+
+extern "C" {
 
 dg_status dg_energy(dg_mesh* m, const float* q, double* E) {
   if (!m || !E) return DG_EINVAL;

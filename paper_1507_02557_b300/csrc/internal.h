@@ -28,6 +28,12 @@ struct TypeDev {
   float* L = nullptr;         // non-hex lift matrices [nf][8][nq][Np]
 };
 
+// A selection of elements per type (multi-rate level): list = NULL means 0..count-1.
+struct Sel {
+  const int* list[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t count[4] = {0, 0, 0, 0};
+};
+
 }  // namespace dgk
 
 struct dg_mesh {
@@ -52,6 +58,13 @@ struct dg_mesh {
   std::vector<double> dtK[4];
   std::vector<double> tet_mhat;  // host copy of the reference tet mass (energy)
   float* tet_mhat_dev = nullptr;
+  // multi-rate (nlevels = 2): per-level element lists, RHS history, start-up flag
+  int nlevels = 1;
+  dgk::Sel all, lev[2];           // lev[0] = coarse (level 1), lev[1] = fine (level 2)
+  int64_t level_count[2] = {0, 0};
+  float* hist = nullptr;          // [3 slots][4][ndof]
+  int cslot[3] = {0, 1, 2}, fslot[3] = {2, 0, 1};   // slots of r^n, r^{n-1}, r^{n-2} per level
+  bool mr_started = false;
   // per-type kernel timing (dg_profile): event pairs recorded around each launch
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -67,6 +80,12 @@ cudaError_t launch_rhs(dg_mesh* m, const float* q, const float* tin, float* rhs)
 cudaError_t launch_stage(dg_mesh* m, float* q, float* res, const float* tin, float* tout, float a,
                          float b, float dt);
 cudaError_t launch_energy(dg_mesh* m, const float* q, double* acc);
+cudaError_t launch_trace_sel(dg_mesh* m, const float* q, float* tout, const Sel& sel);
+cudaError_t launch_rhs_sel(dg_mesh* m, const float* q, const float* tin, float* rhs, const Sel& sel);
+cudaError_t launch_ab(dg_mesh* m, const Sel& sel, const float* qin, float* qout, const float* r0,
+                      const float* r1, const float* r2, float h0, float h1, float h2);
+// Hex constants (1D D, V^f, GL weights and nodes) of order N <= 4 into constant memory.
+cudaError_t upload_hex_constants(int N, const float* hc, int count);
 }  // namespace dgk
 
 // Message returned by dg_last_error() on this thread (api.cpp).

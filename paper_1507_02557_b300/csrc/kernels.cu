@@ -43,7 +43,8 @@ struct Args {
   const float* tau;
   const float* hexc;
   const int* perm;
-  int K;
+  const int* elist;   // optional element list (multi-rate levels); NULL = elements 0..K-1
+  int K;              // number of elements processed
   int64_t dof_off, ndof, side_off;
   float a, b, dt, tau_scale;
   int skew;
@@ -101,8 +102,9 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
   __shared__ int s_perm[8 * NQ];
 
   const int le = threadIdx.x / TPE, tid = threadIdx.x % TPE;
-  const int64_t e = (int64_t)blockIdx.x * EPB + le;
-  const bool valid = e < A.K;
+  const int64_t li = (int64_t)blockIdx.x * EPB + le;
+  const bool valid = li < A.K;
+  const int64_t e = valid ? (A.elist ? (int64_t)A.elist[li] : li) : 0;
   for (int i = threadIdx.x; i < n1 * n1; i += blockDim.x) s_D[i] = A.hexc[i];
   for (int i = threadIdx.x; i < n1; i += blockDim.x) {
     s_Vm[i] = A.hexc[n1 * n1 + i];
@@ -292,6 +294,343 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
   }
 }
 
+// ============================================================================ hexahedra, warp per element
+// For N <= 4: a warp owns EPW = 32 / (N+1)^2 elements; lane (i,j) of an element keeps
+// the column (i,j,0..N) of all four fields in registers.  t-derivatives and the
+// t-face traces come from registers; r/s-derivatives and r/s-face traces read the
+// element's nodes as float4 (p,u,v,w) from shared memory.  Only warp-level
+// synchronisation after the start of the block.
+__constant__ float c_hexw[5][64];   // per N: D1[n1*n1] (row = node), Vm[n1], Vp[n1], w[n1], r[n1]
+
+cudaError_t upload_hex_constants(int N, const float* hc, int count) {
+  if (N < 1 || N > 4 || count > 64) return cudaSuccess;
+  return cudaMemcpyToSymbol(c_hexw, hc, count * sizeof(float), N * 64 * sizeof(float));
+}
+
+template <int N>
+struct HexW {
+  static constexpr int n1 = N + 1, NP = n1 * n1 * n1, NQ = n1 * n1;
+  static constexpr int EPW = 32 / NQ;   // elements per warp
+  static constexpr int WPB = 4;         // warps per block
+  static constexpr int EPB = EPW * WPB;
+};
+
+__device__ __forceinline__ float4 f4fma(float a, float4 x, float4 y) {
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+
+// Outward unit normal and surface Jacobian at point (a,b) of hex face f (local face parameters).
+template <int N>
+__device__ __forceinline__ void hexw_face_geom(const float* g, const float* rr, int f, int a, int b, float nv[3],
+                                               float& Js) {
+  const int ax = f >> 1;
+  const float sg = (f & 1) ? 1.f : -1.f;
+  float u[3], v[3];
+  if (ax == 0) {   // r = sg: x_s x x_t
+    const float s = rr[a], t = rr[b];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      u[d] = g[3 + d] + g[9 + d] * sg + (g[15 + d] + g[18 + d] * sg) * t;
+      v[d] = g[6 + d] + g[12 + d] * sg + (g[15 + d] + g[18 + d] * sg) * s;
+    }
+  } else if (ax == 1) {   // s = sg: x_t x x_r
+    const float r = rr[a], t = rr[b];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      u[d] = g[6 + d] + g[15 + d] * sg + (g[12 + d] + g[18 + d] * sg) * r;
+      v[d] = g[d] + g[9 + d] * sg + (g[12 + d] + g[18 + d] * sg) * t;
+    }
+  } else {   // t = sg: x_r x x_s
+    const float r = rr[a], s = rr[b];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      u[d] = g[d] + g[12 + d] * sg + (g[9 + d] + g[18 + d] * sg) * s;
+      v[d] = g[3 + d] + g[15 + d] * sg + (g[9 + d] + g[18 + d] * sg) * r;
+    }
+  }
+  cross3(u, v, nv);
+  Js = sqrtf(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+  const float inv = sg / Js;
+  nv[0] *= inv;
+  nv[1] *= inv;
+  nv[2] *= inv;
+}
+
+#ifndef DG_HEXW_MINB
+#define DG_HEXW_MINB 4
+#endif
+template <int N, int MODE>
+__global__ void __launch_bounds__(128, DG_HEXW_MINB) hexw_kernel(Args A) {
+  using H = HexW<N>;
+  constexpr int n1 = H::n1, NP = H::NP, NQ = H::NQ, EPW = H::EPW, WPB = H::WPB;
+  __shared__ float4 s_q[WPB][EPW][NP];
+  __shared__ float4 s_F[WPB][EPW][4][NQ];
+  __shared__ float4 s_N[WPB][EPW][6][NQ];
+  __shared__ float s_g[WPB][EPW][24];
+  __shared__ int s_nb[WPB][EPW][6], s_code[WPB][EPW][6];
+  __shared__ float s_tau[WPB][EPW][6];
+  __shared__ int s_perm[8 * NQ];
+
+  const float* Dm = c_hexw[N];
+  const float* Vm = Dm + n1 * n1;
+  const float* Vp = Vm + n1;
+  const float* W1 = Vp + n1;
+  const float* R1 = W1 + n1;
+
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sub = lane / NQ, col = lane % NQ;
+  const int i = col % n1, j = col / n1;
+  const int64_t li = ((int64_t)blockIdx.x * WPB + w) * EPW + sub;
+  const bool act = sub < EPW && li < A.K;
+  const int64_t e = act ? (A.elist ? (int64_t)A.elist[li] : li) : 0;
+  const int su = sub < EPW ? sub : 0;
+  const int64_t base = A.dof_off + e * NP;
+
+  for (int x = threadIdx.x; x < 8 * NQ; x += blockDim.x) s_perm[x] = A.perm[x];
+  float q[4][n1], res[4][n1];
+  if (act) {
+#pragma unroll
+    for (int k = 0; k < n1; ++k)
+#pragma unroll
+      for (int f = 0; f < 4; ++f) q[f][k] = A.q[f * A.ndof + base + col + NQ * k];
+#ifdef DG_HEXW_RES_EARLY
+    if (MODE == MODE_STAGE) {
+#pragma unroll
+      for (int k = 0; k < n1; ++k)
+#pragma unroll
+        for (int f = 0; f < 4; ++f) res[f][k] = A.res[f * A.ndof + base + col + NQ * k];
+    }
+#endif
+    if (col < 24) s_g[w][su][col] = A.geo[e * 24 + col];
+    if (NQ < 24 && col < NQ) {   // small N: fewer lanes than coefficients
+      for (int x = col + NQ; x < 24; x += NQ) s_g[w][su][x] = A.geo[e * 24 + x];
+    }
+    if (col < 6) {
+      const int64_t gs = A.side_off + e * 6 + col;
+      s_nb[w][su][col] = A.nbr[gs];
+      s_code[w][su][col] = A.code[gs];
+      s_tau[w][su][col] = A.tau[gs];
+    }
+#pragma unroll
+    for (int k = 0; k < n1; ++k) s_q[w][su][col + NQ * k] = make_float4(q[0][k], q[1][k], q[2][k], q[3][k]);
+  }
+  if (NQ < 6 && act) {   // N = 1: 4 lanes per element, 6 faces
+    for (int x = col + NQ; x < 6; x += NQ) {
+      const int64_t gs = A.side_off + e * 6 + x;
+      s_nb[w][su][x] = A.nbr[gs];
+      s_code[w][su][x] = A.code[gs];
+      s_tau[w][su][x] = A.tau[gs];
+    }
+  }
+  __syncthreads();
+  const float* g = s_g[w][su];
+  const float c2 = act ? A.c2[e] : 0.f;
+  float rhs[4][n1];
+  float Jn[n1];
+
+  if (MODE != MODE_TRACE && act) {
+    // ---- volume: collocated strong form (Alg. hex_vol), metrics built along the column
+    float Dri[n1], Dsj[n1];
+#pragma unroll
+    for (int m = 0; m < n1; ++m) {
+      Dri[m] = Dm[i * n1 + m];
+      Dsj[m] = Dm[j * n1 + m];
+    }
+    const float r = R1[i], s = R1[j];
+    float Ar[3], Br[3], As[3], Bs[3], xt[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      Ar[d] = g[d] + g[9 + d] * s;
+      Br[d] = g[12 + d] + g[18 + d] * s;
+      As[d] = g[3 + d] + g[9 + d] * r;
+      Bs[d] = g[15 + d] + g[18 + d] * r;
+      xt[d] = g[6 + d] + g[12 + d] * r + g[15 + d] * s + g[18 + d] * r * s;
+    }
+    float G0a[3], G0b[3], G1a[3], G1b[3], G2a[3], G2b[3], G2c[3], tmp[3];
+    cross3(As, xt, G0a);
+    cross3(Bs, xt, G0b);
+    cross3(xt, Ar, G1a);
+    cross3(xt, Br, G1b);
+    cross3(Ar, As, G2a);
+    cross3(Ar, Bs, G2b);
+    cross3(Br, As, tmp);
+    G2b[0] += tmp[0]; G2b[1] += tmp[1]; G2b[2] += tmp[2];
+    cross3(Br, Bs, G2c);
+#pragma unroll
+    for (int k = 0; k < n1; ++k) {
+      const float t = R1[k];
+      float g0[3], g1[3], g2[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        g0[d] = G0a[d] + t * G0b[d];
+        g1[d] = G1a[d] + t * G1b[d];
+        g2[d] = G2a[d] + t * (G2b[d] + t * G2c[d]);
+      }
+      const float J = (Ar[0] + t * Br[0]) * g0[0] + (Ar[1] + t * Br[1]) * g0[1] + (Ar[2] + t * Br[2]) * g0[2];
+      Jn[k] = J;
+      const float iJ = 1.f / J;
+      float4 dr = make_float4(0.f, 0.f, 0.f, 0.f), ds = dr;
+#pragma unroll
+      for (int m = 0; m < n1; ++m) {
+        dr = f4fma(Dri[m], s_q[w][su][m + n1 * j + NQ * k], dr);
+        ds = f4fma(Dsj[m], s_q[w][su][i + n1 * m + NQ * k], ds);
+      }
+      float dt[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int m = 0; m < n1; ++m) {
+        const float dk = Dm[k * n1 + m];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) dt[f] = fmaf(dk, q[f][m], dt[f]);
+      }
+      const float drf[4] = {dr.x, dr.y, dr.z, dr.w}, dsf[4] = {ds.x, ds.y, ds.z, ds.w};
+      // -div u and -c^2 grad p
+      float div = 0.f;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) div += g0[d] * drf[1 + d] + g1[d] * dsf[1 + d] + g2[d] * dt[1 + d];
+      rhs[0][k] = -div * iJ;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) rhs[1 + d][k] = -c2 * iJ * (g0[d] * drf[0] + g1[d] * dsf[0] + g2[d] * dt[0]);
+    }
+  }
+  if (MODE != MODE_TRACE) {
+    // ---- fluxes at this lane's point (a,b) = (i,j) of all six faces
+    float4 F45[2];
+    if (act) {
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) {
+        float4 tm = make_float4(0.f, 0.f, 0.f, 0.f), tp = tm;
+#pragma unroll
+        for (int m = 0; m < n1; ++m) {
+          float4 v;
+          if (ax == 0) v = s_q[w][su][m + n1 * i + NQ * j];
+          else if (ax == 1) v = s_q[w][su][i + n1 * m + NQ * j];
+          else v = make_float4(q[0][m], q[1][m], q[2][m], q[3][m]);
+          tm = f4fma(Vm[m], v, tm);
+          tp = f4fma(Vp[m], v, tp);
+        }
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+          const int f = 2 * ax + sd;
+          const float4 tr = sd ? tp : tm;
+          float nv[3], Js;
+          hexw_face_geom<N>(g, R1, f, i, j, nv, Js);
+          s_N[w][su][f][col] = make_float4(nv[0], nv[1], nv[2], Js);
+          const float unm = nv[0] * tr.y + nv[1] * tr.z + nv[2] * tr.w;
+          const int nb = s_nb[w][su][f];
+          float P = 0.f, UN = 0.f;
+          if (nb >= 0) {
+            const int64_t gs = A.side_off + e * 6 + f;
+            const int cidx = s_perm[s_code[w][su][f] * NQ + col];
+            P = A.tin[gs * NQ + cidx];
+            UN = A.tin[A.plane + gs * NQ + cidx];
+          }
+          const float ta = s_tau[w][su][f];
+          float fp, fu;
+          flux(nb < 0, tr.x, unm, P, UN, A.tau_scale * ta, A.tau_scale / ta, false, fp, fu);
+          const float wg = W1[i] * W1[j] * Js;
+          const float4 Fv = make_float4(wg * fp, wg * fu * nv[0], wg * fu * nv[1], wg * fu * nv[2]);
+          if (ax < 2) s_F[w][su][f][col] = Fv;
+          else F45[sd] = Fv;
+        }
+      }
+    }
+    __syncwarp();
+    if (act) {
+      // ---- lift (Alg. hex_surf), M^{-1} = 1/(w w w J), LSRK update
+#pragma unroll
+      for (int k = 0; k < n1; ++k) {
+        const float4 F0 = s_F[w][su][0][j + n1 * k], F1 = s_F[w][su][1][j + n1 * k];
+        const float4 F2 = s_F[w][su][2][i + n1 * k], F3 = s_F[w][su][3][i + n1 * k];
+        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+        sum = f4fma(Vm[i], F0, sum);
+        sum = f4fma(Vp[i], F1, sum);
+        sum = f4fma(Vm[j], F2, sum);
+        sum = f4fma(Vp[j], F3, sum);
+        sum = f4fma(Vm[k], F45[0], sum);
+        sum = f4fma(Vp[k], F45[1], sum);
+        const float iM = 1.f / (W1[i] * W1[j] * W1[k] * Jn[k]);
+        rhs[0][k] += iM * sum.x;
+        rhs[1][k] += c2 * iM * sum.y;
+        rhs[2][k] += c2 * iM * sum.z;
+        rhs[3][k] += c2 * iM * sum.w;
+      }
+      if (MODE == MODE_RHS) {
+#pragma unroll
+        for (int k = 0; k < n1; ++k)
+#pragma unroll
+          for (int f = 0; f < 4; ++f) A.rhs[f * A.ndof + base + col + NQ * k] = rhs[f][k];
+      } else {
+#ifndef DG_HEXW_RES_EARLY
+#pragma unroll
+        for (int k = 0; k < n1; ++k)
+#pragma unroll
+          for (int f = 0; f < 4; ++f) res[f][k] = A.res[f * A.ndof + base + col + NQ * k];
+#endif
+#pragma unroll
+        for (int k = 0; k < n1; ++k)
+#pragma unroll
+          for (int f = 0; f < 4; ++f) {
+            const int64_t id = f * A.ndof + base + col + NQ * k;
+            const float rr = A.a * res[f][k] + A.dt * rhs[f][k];
+            q[f][k] += A.b * rr;
+            A.res[id] = rr;
+            A.qout[id] = q[f][k];
+          }
+      }
+    }
+    if (MODE == MODE_STAGE) {
+      __syncwarp();
+      if (act) {
+#pragma unroll
+        for (int k = 0; k < n1; ++k) s_q[w][su][col + NQ * k] = make_float4(q[0][k], q[1][k], q[2][k], q[3][k]);
+      }
+      __syncwarp();
+    }
+  }
+  if ((MODE == MODE_TRACE || MODE == MODE_STAGE) && act) {
+    // ---- traces of the (updated) state into the neighbours' inboxes
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      float4 tm = make_float4(0.f, 0.f, 0.f, 0.f), tp = tm;
+#pragma unroll
+      for (int m = 0; m < n1; ++m) {
+        float4 v;
+        if (ax == 0) v = s_q[w][su][m + n1 * i + NQ * j];
+        else if (ax == 1) v = s_q[w][su][i + n1 * m + NQ * j];
+        else v = make_float4(q[0][m], q[1][m], q[2][m], q[3][m]);
+        tm = f4fma(Vm[m], v, tm);
+        tp = f4fma(Vp[m], v, tp);
+      }
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        const int f = 2 * ax + sd;
+        const int nb = s_nb[w][su][f];
+        if (nb < 0) continue;
+        float nv[3];
+        if (MODE == MODE_STAGE) {
+          const float4 nn = s_N[w][su][f][col];
+          nv[0] = nn.x; nv[1] = nn.y; nv[2] = nn.z;
+        } else {
+          float Js;
+          hexw_face_geom<N>(g, R1, f, i, j, nv, Js);
+        }
+        const float4 tr = sd ? tp : tm;
+        const int cidx = s_perm[s_code[w][su][f] * NQ + col];
+        A.tout[(int64_t)nb * NQ + cidx] = tr.x;
+        A.tout[A.plane + (int64_t)nb * NQ + cidx] = nv[0] * tr.y + nv[1] * tr.z + nv[2] * tr.w;
+      }
+    }
+  }
+}
+
+template <int N, int MODE>
+static void launch_hexw_n(const Args& A, cudaStream_t s) {
+  using H = HexW<N>;
+  if (A.K == 0) return;
+  dim3 grid((A.K + H::EPB - 1) / H::EPB);
+  hexw_kernel<N, MODE><<<grid, 32 * H::WPB, 0, s>>>(A);
+}
+
 // ============================================================================ wedge, pyramid, tet
 __host__ __device__ constexpr int np_of(int t, int N) {
   return t == DG_WEDGE ? (N + 1) * (N + 1) * (N + 2) / 2
@@ -318,7 +657,7 @@ __global__ void __launch_bounds__(128) gen_kernel(Args A) {
   __shared__ int s_code[NF];
 
   const int tid = threadIdx.x;
-  const int64_t e = blockIdx.x;
+  const int64_t e = A.elist ? (int64_t)A.elist[blockIdx.x] : (int64_t)blockIdx.x;
   const int64_t base = A.dof_off + e * NP;
   for (int x = tid; x < 4 * NP; x += NT) s_q[x / NP][x % NP] = A.q[(x / NP) * A.ndof + base + x % NP];
   if (tid < NF) s_code[tid] = A.code[A.side_off + e * NF + tid];
@@ -577,6 +916,25 @@ __global__ void __launch_bounds__(128) energy_kernel(Args A, const float* mhat, 
   if (tid == 0) atomicAdd(acc, 0.5 * s_red[0]);
 }
 
+// ============================================================================ multi-rate AB3 update
+// q_out = q_in + h0*r0 + h1*r1 + h2*r2 on the DOFs of the listed elements (all four fields).
+__global__ void __launch_bounds__(256) ab_update_kernel(const int* elist, int K, int Np, int64_t dof_off,
+                                                        int64_t ndof, const float* qin, float* qout,
+                                                        const float* r0, const float* r1, const float* r2,
+                                                        float h0, float h1, float h2) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= (int64_t)K * Np) return;
+  const int64_t li = x / Np;
+  const int n = (int)(x % Np);
+  const int64_t e = elist ? (int64_t)elist[li] : li;
+  const int64_t id = dof_off + e * Np + n;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const int64_t k = f * ndof + id;
+    qout[k] = qin[k] + h0 * r0[k] + h1 * r1[k] + h2 * r2[k];
+  }
+}
+
 // ============================================================================ launchers
 static Args make_args(dg_mesh* m, int t) {
   const TypeDev& td = m->td[t];
@@ -595,6 +953,7 @@ static Args make_args(dg_mesh* m, int t) {
   A.hexc = m->hexc;
   A.perm = m->hexperm;
   A.K = td.K;
+  A.elist = nullptr;
   A.dof_off = td.dof_off;
   A.ndof = m->ndof;
   A.side_off = td.side_off;
@@ -639,7 +998,7 @@ static void launch_type(dg_mesh* m, const Args& A, int t) {
   switch (m->N) {
 #define DG_CASE(NN)                                                   \
   case NN:                                                            \
-    if (t == DG_HEX) launch_hex_n<NN, MODE>(A, s);                    \
+    if (t == DG_HEX) { if (NN <= 4) launch_hexw_n<(NN <= 4 ? NN : 4), MODE>(A, s); else launch_hex_n<NN, MODE>(A, s); } \
     else if (t == DG_WEDGE) launch_gen_n<DG_WEDGE, NN, MODE>(A, s);   \
     else if (t == DG_PYR) launch_gen_n<DG_PYR, NN, MODE>(A, s);       \
     else launch_gen_n<DG_TET, NN, MODE>(A, s);                        \
@@ -657,8 +1016,48 @@ static void launch_type(dg_mesh* m, const Args& A, int t) {
 }
 
 template <int MODE>
-static void launch_all(dg_mesh* m, Args* A) {
-  for (int t = 0; t < 4; ++t) launch_type<MODE>(m, A[t], t);
+static void launch_all(dg_mesh* m, Args* A, const Sel* sel = nullptr) {
+  for (int t = 0; t < 4; ++t) {
+    if (sel) {
+      A[t].elist = sel->list[t];
+      A[t].K = (int)sel->count[t];
+    }
+    launch_type<MODE>(m, A[t], t);
+  }
+}
+
+cudaError_t launch_trace_sel(dg_mesh* m, const float* q, float* tout, const Sel& sel) {
+  Args A[4];
+  for (int t = 0; t < 4; ++t) {
+    A[t] = make_args(m, t);
+    A[t].q = q;
+    A[t].tout = tout;
+  }
+  launch_all<MODE_TRACE>(m, A, &sel);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_sel(dg_mesh* m, const float* q, const float* tin, float* rhs, const Sel& sel) {
+  Args A[4];
+  for (int t = 0; t < 4; ++t) {
+    A[t] = make_args(m, t);
+    A[t].q = q;
+    A[t].tin = tin;
+    A[t].rhs = rhs;
+  }
+  launch_all<MODE_RHS>(m, A, &sel);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ab(dg_mesh* m, const Sel& sel, const float* qin, float* qout, const float* r0,
+                      const float* r1, const float* r2, float h0, float h1, float h2) {
+  for (int t = 0; t < 4; ++t) {
+    const int64_t n = sel.count[t] * (int64_t)m->td[t].Np;
+    if (n == 0) continue;
+    ab_update_kernel<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(
+        sel.list[t], (int)sel.count[t], m->td[t].Np, m->td[t].dof_off, m->ndof, qin, qout, r0, r1, r2, h0, h1, h2);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_trace(dg_mesh* m, const float* q, float* tout) {

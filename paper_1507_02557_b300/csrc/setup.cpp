@@ -633,6 +633,8 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
         for (int i = 0; i < n1; ++i) hc.push_back((float)B[t].w1[i]);
         for (int i = 0; i < n1; ++i) hc.push_back((float)B[t].r1[i]);
         m->hexc = upload(hc, owned);
+        if (!g_host_only && dgk::upload_hex_constants(N, hc.data(), (int)hc.size()) != cudaSuccess)
+          throw SetupError(DG_ECUDA, "constant upload failed");
         // local face point (iu + n1 iv) -> canonical index, per code
         std::vector<int> perm(dgk::NCODES * nq, 0);
         const double P[4][2] = {{-1, -1}, {1, -1}, {-1, 1}, {1, 1}};
@@ -813,6 +815,53 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
         m->dtK[t][e] = dte;
         m->dt_min = std::min(m->dt_min, dte);
       }
+    }
+
+    // --- multi-rate levels (Sec. 2.4): level 1 = coarse, nlevels = fine; dtau_lev = 2^(nlevels-lev) dtau_min
+    const int nlev = d->nlevels < 1 ? 1 : d->nlevels;
+    m->nlevels = nlev;
+    std::vector<std::vector<int>> level(4);
+    for (int t = 0; t < 4; ++t) {
+      level[t].assign(m->td[t].K, nlev);
+      for (int e = 0; e < m->td[t].K; ++e)
+        for (int L = 1; L <= nlev; ++L)
+          if (std::ldexp(m->dt_min, nlev - L) <= m->dtK[t][e] * (1 + 1e-12)) {
+            level[t][e] = L;
+            break;
+          }
+    }
+    for (bool changed = true; changed;) {   // neighbours differ by at most one level
+      changed = false;
+      for (int64_t s = 0; s < side; ++s) {
+        if (nbr[s] < 0) continue;
+        int t, f, t2, f2;
+        int64_t e, e2;
+        side_elem(s, t, e, f);
+        side_elem(nbr[s], t2, e2, f2);
+        if (level[t][e] < level[t2][e2] - 1) {
+          level[t][e] = level[t2][e2] - 1;
+          changed = true;
+        }
+      }
+    }
+    for (int t = 0; t < 4; ++t) {
+      m->all.count[t] = m->td[t].K;
+      m->all.list[t] = nullptr;
+    }
+    if (nlev == 2) {
+      for (int L = 0; L < 2; ++L) {
+        for (int t = 0; t < 4; ++t) {
+          std::vector<int> lst;
+          for (int e = 0; e < m->td[t].K; ++e)
+            if (level[t][e] == L + 1) lst.push_back(e);
+          m->lev[L].count[t] = (int64_t)lst.size();
+          m->lev[L].list[t] = upload(lst, owned);
+          m->level_count[L] += (int64_t)lst.size();
+        }
+      }
+      m->hist = alloc_zero<float>(3 * 4 * (size_t)m->ndof, owned);
+    } else {
+      m->level_count[0] = m->td[0].K + m->td[1].K + m->td[2].K + m->td[3].K;
     }
 
     // --- side arrays, state, traces

@@ -18,7 +18,7 @@ if not os.path.exists(LIB_PATH):
 _lib = C.CDLL(LIB_PATH)
 
 HEX, WEDGE, PYR, TET = 0, 1, 2, 3
-EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_host_check", "dg_layout", "dg_ndof",
+EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_host_check", "dg_layout", "dg_ndof", "dg_level_counts",
            "dg_set_state", "dg_get_state", "dg_rhs", "dg_timestep", "dg_step", "dg_state_ptr",
            "dg_energy", "dg_energy_noalloc", "dg_profile", "dg_adjoint_step", "dg_status_string", "dg_last_error")
 
@@ -35,9 +35,10 @@ _vp = C.c_void_p
 _lib.dg_mesh_create.argtypes = [C.POINTER(Desc), _vp, C.POINTER(_vp)]
 _lib.dg_mesh_destroy.argtypes = [_vp]
 _lib.dg_mesh_destroy.restype = None
-_lib.dg_host_check.argtypes = [C.POINTER(Desc), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+_lib.dg_host_check.argtypes = [C.POINTER(Desc), C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]
 _lib.dg_layout.argtypes = [_vp, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int)]
 _lib.dg_ndof.argtypes = [_vp, C.POINTER(C.c_int64)]
+_lib.dg_level_counts.argtypes = [_vp, C.c_int, C.POINTER(C.c_int64)]
 _lib.dg_set_state.argtypes = [_vp, _vp, C.c_int]
 _lib.dg_get_state.argtypes = [_vp, _vp, C.c_int]
 _lib.dg_rhs.argtypes = [_vp, _vp, _vp, C.c_double]
@@ -70,7 +71,7 @@ def _ptr(x):
     return x.ctypes.data_as(_vp)
 
 
-def _desc(mesh, N, tau_scale, pyr_form, cfl, keep):
+def _desc(mesh, N, tau_scale, pyr_form, cfl, keep, nlevels=1):
     d = Desc()
     xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
     keep.append(xyz)
@@ -84,30 +85,34 @@ def _desc(mesh, N, tau_scale, pyr_form, cfl, keep):
         d.conn[t] = cn.ctypes.data_as(C.POINTER(C.c_int32))
         d.c2[t] = c2.ctypes.data_as(C.POINTER(C.c_double))
     d.N, d.hex_basis, d.pyr_form = N, 0, pyr_form
-    d.tau_scale, d.nlevels, d.cfl, d.precision = tau_scale, 1, cfl, 0
+    d.tau_scale, d.nlevels, d.cfl, d.precision = tau_scale, nlevels, cfl, 0
     return d
 
 
-def host_check(mesh, N, tau_scale=1.0, pyr_form=0, cfl=0.5):
-    """dg_host_check: (dt_min, [C_T hex, wedge, pyr, tet]) from the host setup alone."""
+def host_check(mesh, N, tau_scale=1.0, pyr_form=0, cfl=0.5, nlevels=1, levels=False):
+    """dg_host_check: (dt_min, [C_T hex, wedge, pyr, tet][, level counts]) from the host setup alone."""
     keep = []
-    d = _desc(mesh, N, tau_scale, pyr_form, cfl, keep)
+    d = _desc(mesh, N, tau_scale, pyr_form, cfl, keep, nlevels)
     dt = C.c_double()
     ct = (C.c_double * 4)()
-    _check(_lib.dg_host_check(C.byref(d), C.byref(dt), ct))
+    lc = (C.c_int64 * 2)()
+    _check(_lib.dg_host_check(C.byref(d), C.byref(dt), ct, C.cast(lc, _vp)))
+    if levels:
+        return dt.value, list(ct), list(lc)[:nlevels]
     return dt.value, list(ct)
 
 
 class Mesh:
     """A dg_mesh on the current CUDA device (see include/dg.h)."""
 
-    def __init__(self, mesh, N, tau_scale=1.0, pyr_form=0, cfl=0.5, stream=None):
+    def __init__(self, mesh, N, tau_scale=1.0, pyr_form=0, cfl=0.5, stream=None, nlevels=1):
         keep = []
-        d = _desc(mesh, N, tau_scale, pyr_form, cfl, keep)
+        d = _desc(mesh, N, tau_scale, pyr_form, cfl, keep, nlevels)
         h = _vp()
         _check(_lib.dg_mesh_create(C.byref(d), _vp(stream or 0), C.byref(h)))
         self._h = h
         self.N = N
+        self.nlevels = nlevels
         n = C.c_int64()
         _check(_lib.dg_ndof(h, C.byref(n)))
         self.ndof = n.value
@@ -143,6 +148,19 @@ class Mesh:
         dt = C.c_double()
         _check(_lib.dg_timestep(self._h, C.byref(dt), None))
         return dt.value
+
+    def level_type_counts(self, level):
+        """Elements per type (hex, wedge, pyramid, tet) in time-step level 1..nlevels."""
+        c = (C.c_int64 * 4)()
+        _check(_lib.dg_level_counts(self._h, int(level), c))
+        return list(c)
+
+    def level_counts(self):
+        """Element counts of the time-step levels (coarse first)."""
+        dt = C.c_double()
+        lc = (C.c_int64 * 2)()
+        _check(_lib.dg_timestep(self._h, C.byref(dt), lc))
+        return list(lc)[: self.nlevels]
 
     def step(self, nsteps, dt=0.0, t=0.0):
         tt = C.c_double(t)

@@ -129,3 +129,29 @@ def test_state_roundtrip_and_layout(lib):
     g.set_state(q, on_device=False)
     back = g.get_state(np.zeros_like(q), on_device=False)
     assert np.array_equal(back, q)
+
+
+@pytest.mark.parametrize("N", [2, 3])
+def test_multirate_ab3_matches_oracle(lib, N):
+    """Two-level MRAB3 (Sec. 2.4 reading): start-up + 5 coarse steps vs the oracle."""
+    from oracle.constants import trace_constant
+    from oracle.dg import MRAB3, mr_levels, standing_mode
+    m = MESHES["cjump"]()
+    o = DGOracle(m, N)
+    lev, dmin = mr_levels(o, [trace_constant(t, N) for t in range(4)], 2)
+    g = lib.Mesh(m, N, nlevels=2)
+    assert g.level_counts() == [sum(int(np.sum(l == L)) for l in lev) for L in (1, 2)]
+    for L in (1, 2):
+        assert g.level_type_counts(L) == [int(np.sum(l == L)) for l in lev]
+    h = g.timestep()
+    assert abs(h - dmin) < 1e-12 * dmin
+    q0 = o.project(standing_mode, 0.0).astype(np.float32)
+    g.set_state(q0, on_device=False)
+    t = g.step(5, h)
+    got = g.get_state(np.zeros_like(q0), on_device=False).astype(np.float64)
+    mr = MRAB3(o, lev)
+    q, hist = mr.start(q0.astype(np.float64), h)
+    for _ in range(5):
+        q, hist = mr.step(q, hist, h)
+    assert abs(t - 14 * h) < 1e-12
+    assert rel(got, q) < TOL, per_type_rel(o, got, q)

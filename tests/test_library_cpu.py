@@ -68,3 +68,15 @@ def test_host_setup_rejects_bad_meshes():
     neg.c2[3] = -neg.c2[3]
     with pytest.raises(dg.DGError, match="invalid argument"):
         dg.host_check(neg, 2)
+
+
+def test_host_setup_multirate_levels_match_oracle():
+    """Sec. 2.4 level binning and neighbour smoothing: library vs oracle element counts."""
+    from oracle.dg import mr_levels
+    m = layered_mesh(3, 3, 5, "HWHTK", seed=3, c_of_layer=lambda k: 1.0 if k % 2 == 0 else 1.5)
+    N = 2
+    _, _, lc = dg.host_check(m, N, nlevels=2, levels=True)
+    o = DGOracle(m, N)
+    lev, _ = mr_levels(o, [trace_constant(t, N) for t in range(4)], 2)
+    want = [sum(int(np.sum(l == L)) for l in lev) for L in (1, 2)]
+    assert lc == want and lc[1] > 0

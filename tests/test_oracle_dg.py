@@ -163,3 +163,28 @@ def test_convergence_to_standing_mode():
             q = dg.lsrk_step(q, T / nst)
         errs.append(dg.l2_error(q, standing_mode, T))
     assert np.log2(errs[0] / errs[1]) > N + 0.5
+
+
+def test_mrab3_is_third_order():
+    """Two-level MRAB3 (Sec. 2.4 reading): halving the fine step divides the error by ~8."""
+    from oracle.dg import MRAB3, mr_levels
+    m = layered_mesh(3, 3, 5, "HWHTK", seed=3, c_of_layer=lambda k: 1.0 if k % 2 == 0 else 1.5)
+    N = 2
+    o = DGOracle(m, N)
+    lev, dmin = mr_levels(o, [trace_constant(t, N) for t in range(4)], 2)
+    assert sum(int(np.sum(l == 2)) for l in lev) > 0 and sum(int(np.sum(l == 1)) for l in lev) > 0
+    q0 = o.project(standing_mode, 0.0)
+    errs = []
+    for h in (dmin, dmin / 2):
+        mr = MRAB3(o, lev)
+        q, hist = mr.start(q0, h)
+        nsteps = int(round((0.06 - 4 * h) / (2 * h)))
+        for _ in range(nsteps):
+            q, hist = mr.step(q, hist, h)
+        T = 4 * h + 2 * h * nsteps
+        nref = int(np.ceil(T / (dmin / 4)))
+        qr = q0.copy()
+        for _ in range(nref):
+            qr = o.lsrk_step(qr, T / nref)
+        errs.append(np.linalg.norm(q - qr) / np.linalg.norm(qr))
+    assert 6.0 < errs[0] / errs[1] < 11.0, errs
