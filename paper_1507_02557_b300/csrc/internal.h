@@ -26,6 +26,12 @@ struct TypeDev {
   float* ops = nullptr;       // volume operators (type-specific layout, see setup.cpp)
   float* Tt = nullptr;        // non-hex trace matrices [nf][8][Np][nq]
   float* L = nullptr;         // non-hex lift matrices [nf][8][nq][Np]
+  // orientation-free operators of the warp-per-element kernels (kernels_gen2.cu)
+  float4* sgeo2 = nullptr;    // [K*nf][nq]: triangle faces at canonical points, quads at local points
+  float* sisq2 = nullptr;     // wedge: 1/sqrt(J) in the same order
+  float* ops2 = nullptr;      // float operators (layout in setup.cpp: build_gen2_ops)
+  int* iops2 = nullptr;       // integer tables (face-node gathers, lattice permutations)
+  int nops2 = 0, niops2 = 0;  // sizes (elements)
 };
 
 // A selection of elements per type (multi-rate level): list = NULL means 0..count-1.

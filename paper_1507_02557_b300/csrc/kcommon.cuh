@@ -1,0 +1,63 @@
+// Shared definitions of the CUDA kernels (kernels.cu, kernels_gen2.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.h"
+
+namespace dgk {
+
+enum { MODE_TRACE = 0, MODE_RHS = 1, MODE_STAGE = 2 };
+
+struct Args {
+  const float* q;     // state in  [4][ndof]
+  float* qout;        // state out (stage: may alias q)
+  float* res;         // LSRK residual [4][ndof]
+  float* rhs;         // rhs out [4][ndof]
+  const float* tin;   // inbox to read: plane 0 = p, plane 1 = u.n
+  float* tout;        // inboxes to write
+  int64_t plane;      // nsides * nq
+  const float* geo;
+  const float4* sgeo;
+  const float* sisq;
+  const float* c2;
+  const float* Tt;
+  const float* L;
+  const float* ops;
+  const int* nbr;
+  const int* code;
+  const float* tau;
+  const float* hexc;
+  const int* perm;
+  const float4* sgeo2;  // orientation-free kernels: face geometry in their point order
+  const float* sisq2;
+  const float* ops2;
+  const int* iops2;
+  const int* elist;   // optional element list (multi-rate levels); NULL = elements 0..K-1
+  int K;              // number of elements processed
+  int64_t dof_off, ndof, side_off;
+  float a, b, dt, tau_scale;
+  int skew;
+};
+
+__device__ __forceinline__ void flux(bool wall, float pm, float unm, float P, float UN, float tp,
+                                     float tu, bool skew, float& fp, float& fu) {
+  if (wall) {
+    P = -pm;
+    UN = -unm;
+  }
+  float jp = P - pm;
+  float jun = -UN - unm;
+  fp = skew ? 0.5f * tp * jp - 0.5f * (unm - UN) : 0.5f * (tp * jp - jun);
+  fu = 0.5f * (tu * jun - jp);
+}
+
+
+__host__ __device__ constexpr int np_of(int t, int N) {
+  return t == DG_WEDGE ? (N + 1) * (N + 1) * (N + 2) / 2
+         : t == DG_PYR ? (N + 1) * (N + 2) * (2 * N + 3) / 6
+                       : (N + 1) * (N + 2) * (N + 3) / 6;
+}
+
+}  // namespace dgk

@@ -18,49 +18,9 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "kcommon.cuh"
 
 namespace dgk {
-
-enum { MODE_TRACE = 0, MODE_RHS = 1, MODE_STAGE = 2 };
-
-struct Args {
-  const float* q;     // state in  [4][ndof]
-  float* qout;        // state out (stage: may alias q)
-  float* res;         // LSRK residual [4][ndof]
-  float* rhs;         // rhs out [4][ndof]
-  const float* tin;   // inbox to read: plane 0 = p, plane 1 = u.n
-  float* tout;        // inboxes to write
-  int64_t plane;      // nsides * nq
-  const float* geo;
-  const float4* sgeo;
-  const float* sisq;
-  const float* c2;
-  const float* Tt;
-  const float* L;
-  const float* ops;
-  const int* nbr;
-  const int* code;
-  const float* tau;
-  const float* hexc;
-  const int* perm;
-  const int* elist;   // optional element list (multi-rate levels); NULL = elements 0..K-1
-  int K;              // number of elements processed
-  int64_t dof_off, ndof, side_off;
-  float a, b, dt, tau_scale;
-  int skew;
-};
-
-__device__ __forceinline__ void flux(bool wall, float pm, float unm, float P, float UN, float tp,
-                                     float tu, bool skew, float& fp, float& fu) {
-  if (wall) {
-    P = -pm;
-    UN = -unm;
-  }
-  float jp = P - pm;
-  float jun = -UN - unm;
-  fp = skew ? 0.5f * tp * jp - 0.5f * (unm - UN) : 0.5f * (tp * jp - jun);
-  fu = 0.5f * (tu * jun - jp);
-}
 
 // ============================================================================ hexahedra
 template <int N>
@@ -632,11 +592,6 @@ static void launch_hexw_n(const Args& A, cudaStream_t s) {
 }
 
 // ============================================================================ wedge, pyramid, tet
-__host__ __device__ constexpr int np_of(int t, int N) {
-  return t == DG_WEDGE ? (N + 1) * (N + 1) * (N + 2) / 2
-         : t == DG_PYR ? (N + 1) * (N + 2) * (2 * N + 3) / 6
-                       : (N + 1) * (N + 2) * (N + 3) / 6;
-}
 
 template <int T, int N>
 struct GenCfg {
@@ -952,6 +907,10 @@ static Args make_args(dg_mesh* m, int t) {
   A.tau = m->side_tau;
   A.hexc = m->hexc;
   A.perm = m->hexperm;
+  A.sgeo2 = td.sgeo2;
+  A.sisq2 = td.sisq2;
+  A.ops2 = td.ops2;
+  A.iops2 = td.iops2;
   A.K = td.K;
   A.elist = nullptr;
   A.dof_off = td.dof_off;
@@ -976,6 +935,9 @@ static void launch_gen_n(const Args& A, cudaStream_t s) {
   gen_kernel<T, N, MODE><<<A.K, 128, 0, s>>>(A);
 }
 
+template <int MODE>
+bool launch_gen2(int t, int N, const Args& A, cudaStream_t s);   // kernels_gen2.cu
+
 // Event pair around one type's launch when dg_profile is on.
 static int ev_take(dg_mesh* m) {
   if (m->ev_next == m->ev_pool.size()) {
@@ -999,6 +961,7 @@ static void launch_type(dg_mesh* m, const Args& A, int t) {
 #define DG_CASE(NN)                                                   \
   case NN:                                                            \
     if (t == DG_HEX) { if (NN <= 4) launch_hexw_n<(NN <= 4 ? NN : 4), MODE>(A, s); else launch_hex_n<NN, MODE>(A, s); } \
+    else if (launch_gen2<MODE>(t, NN, A, s)) {}                       \
     else if (t == DG_WEDGE) launch_gen_n<DG_WEDGE, NN, MODE>(A, s);   \
     else if (t == DG_PYR) launch_gen_n<DG_PYR, NN, MODE>(A, s);       \
     else launch_gen_n<DG_TET, NN, MODE>(A, s);                        \

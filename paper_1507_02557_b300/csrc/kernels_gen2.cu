@@ -1,0 +1,453 @@
+// Warp-per-element kernels for tetrahedra, pyramids and wedges (sm_103a).
+//
+// Persistent blocks stage the element type's reference operators in shared memory
+// once; each warp then walks over elements.  All operators are independent of the
+// face orientation:
+//   triangle faces  the trace is taken at the equispaced face lattice (a gather for
+//                   the nodal tet, a small matrix for the pyramid and the wedge),
+//                   permuted into the canonical face frame, and interpolated to the
+//                   canonical face quadrature points (matrix E); the lift applies E^T,
+//                   the inverse permutation and the transposed lattice evaluation
+//                   (for polynomial traces this equals the face quadrature of Sec. 2.3);
+//   quad faces      the trace is taken at the local GL points and permuted.
+// The four fields p,u,v,w travel together as float4, so every operator entry read
+// from shared memory feeds four FMAs.
+// Volume terms: Alg. tet_vol (strong form, constant metrics), Alg. pyr_vol (skew
+// form with transposed operators), Alg. wedge_vol1/2 (LSC-DG skew form at the
+// wedge cubature points).  Flux, walls and M^{-1} as in kernels.cu.
+#include <cuda_runtime.h>
+
+#include "kcommon.cuh"
+
+namespace dgk {
+
+template <int T, int N>
+struct G2 {
+  static constexpr int NP = np_of(T, N), NQ = (N + 1) * (N + 1), NFN = (N + 1) * (N + 2) / 2;
+  static constexpr int NF = T == DG_TET ? 4 : 5;
+  static constexpr int NTRI = T == DG_WEDGE ? 2 : 4;
+  static constexpr int NQUAD = NF - NTRI;
+  static constexpr int NC = T == DG_WEDGE ? (N + 1) * (N + 1) * (N + 1) : 0;
+  static constexpr int NW = T == DG_WEDGE ? 12 : 16;                   // warps per block
+  static constexpr int N1 = N + 1, NT = NFN;                            // wedge: 1D points, triangle modes
+  static constexpr int VOL = T == DG_WEDGE ? NQ * NT * 4 + 2 * N1 * N1 + NQ * N1 : NP * NP * 4;
+  static constexpr int TN = NTRI * NFN * NP;                            // tet: M^-1 lift; others: lattice evals
+  static constexpr int TQ = NQUAD * NQ * NP;
+  static constexpr int OPS = VOL + TN + TQ + NQ * NFN;
+  static constexpr int IOPS = 12 * NFN + 8 * NQ + (T == DG_TET ? 4 * NFN : 0);
+  static constexpr int OPS_B = ((OPS * 4 + 15) / 16) * 16;
+  static constexpr int IOPS_B = ((IOPS * 4 + 15) / 16) * 16;
+  // per-warp float4 buffers: q4, W4 (wedge: Y/Z pair + X1,X2), F4, G4 (local-order moments),
+  // V4 (canonical lattice values)
+  static constexpr int WB = NP + (T == DG_WEDGE ? 2 * NT * N1 + 2 * NC : NP) + NF * NQ + 2 * NTRI * NFN;
+  static constexpr int SMEM = OPS_B + IOPS_B + NW * WB * 16;
+  static constexpr int R = (NP + 31) / 32;
+};
+
+__device__ __forceinline__ float4 f4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+__device__ __forceinline__ void f4acc(float4& s, float c, const float4& v) {
+  s.x = fmaf(c, v.x, s.x);
+  s.y = fmaf(c, v.y, s.y);
+  s.z = fmaf(c, v.z, s.z);
+  s.w = fmaf(c, v.w, s.w);
+}
+
+// face f of type T: triangle index (or -1) and quad index (or -1)
+template <int T>
+__device__ __forceinline__ int tri_of(int f) {
+  return T == DG_TET ? f : T == DG_PYR ? (f == 0 ? -1 : f - 1) : (f < 2 ? f : -1);
+}
+template <int T>
+__device__ __forceinline__ int quad_of(int f) {
+  return T == DG_TET ? -1 : T == DG_PYR ? (f == 0 ? 0 : -1) : (f >= 2 ? f - 2 : -1);
+}
+template <int T>
+__device__ __forceinline__ int face_of_tri(int ti) {
+  return T == DG_PYR ? ti + 1 : ti;
+}
+
+template <int T, int N, int MODE>
+__global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
+  using C = G2<T, N>;
+  constexpr int NP = C::NP, NQ = C::NQ, NFN = C::NFN, NF = C::NF, NTRI = C::NTRI, NQUAD = C::NQUAD;
+  constexpr int NC = C::NC, NW = C::NW, R = C::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sop = reinterpret_cast<float*>(smem_raw);
+  int* sio = reinterpret_cast<int*>(smem_raw + C::OPS_B);
+  float4* swarp = reinterpret_cast<float4*>(smem_raw + C::OPS_B + C::IOPS_B);
+  for (int x = threadIdx.x; x < C::OPS; x += blockDim.x) sop[x] = A.ops2[x];
+  for (int x = threadIdx.x; x < C::IOPS; x += blockDim.x) sio[x] = A.iops2[x];
+  __syncthreads();
+
+  const float4* DV4 = reinterpret_cast<const float4*>(sop);     // tet/pyr [NP][NP]; wedge Vt4 [NQ][NT]
+  const float* V1 = sop + NQ * C::NT * 4;                        // wedge [N1][N1] (l, j)
+  const float* D1 = V1 + C::N1 * C::N1;
+  const float* wq = D1 + C::N1 * C::N1;                          // wedge weights [NQ][N1]
+  const float* Tn = sop + C::VOL;                                // [NTRI][NFN][NP]
+  const float* Tq = Tn + C::TN;                                  // [NQUAD][NQ][NP]
+  const float* E = Tq + C::TQ;                                   // [NQ][NFN]
+  const int* tperm = sio;                                        // [6][NFN] local lattice -> canonical
+  const int* qperm = sio + 12 * NFN;                             // [8][NQ] local GL point -> canonical
+  const int* fnode = qperm + 8 * NQ;                             // tet [4][NFN]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ int s_code[NW][NF];
+  int* code = s_code[warp];
+  float4* q4 = swarp + warp * C::WB;
+  float4* W4 = q4 + NP;
+  float4* F4 = W4 + (T == DG_WEDGE ? 2 * C::NT * C::N1 + 2 * NC : NP);
+  float4* G4 = F4 + NF * NQ;
+  float4* V4 = G4 + NTRI * NFN;
+
+  for (int64_t li = (int64_t)blockIdx.x * NW + warp; li < A.K; li += (int64_t)gridDim.x * NW) {
+    const int64_t e = A.elist ? (int64_t)A.elist[li] : li;
+    const int64_t base = A.dof_off + e * NP;
+    const float c2 = A.c2[e];
+    if (lane < NF) code[lane] = A.code[A.side_off + e * NF + lane];
+    for (int n = lane; n < NP; n += 32)
+      q4[n] = f4(A.q[base + n], A.q[A.ndof + base + n], A.q[2 * A.ndof + base + n], A.q[3 * A.ndof + base + n]);
+    __syncwarp();
+
+    // canonical lattice values of the triangle faces (V4) from q4
+    auto lattice_values = [&]() {
+      for (int x = lane; x < NTRI * NFN; x += 32) {
+        const int ti = x / NFN, nl = x % NFN;
+        float4 v;
+        if (T == DG_TET) {
+          v = q4[fnode[ti * NFN + nl]];
+        } else {
+          v = f4(0.f, 0.f, 0.f, 0.f);
+          const float* row = Tn + (ti * NFN + nl) * NP;
+          #pragma unroll 4
+        for (int m = 0; m < NP; ++m) f4acc(v, row[m], q4[m]);
+        }
+        V4[ti * NFN + tperm[code[face_of_tri<T>(ti)] * NFN + nl]] = v;
+      }
+    };
+    // trace (p,u,v,w) at point idx of face f (triangle: canonical point; quad: local point)
+    auto trace_at = [&](int f, int idx) {
+      float4 tr = f4(0.f, 0.f, 0.f, 0.f);
+      const int ti = tri_of<T>(f);
+      if (ti >= 0) {
+        const float* er = E + idx * NFN;
+        const float4* vc = V4 + ti * NFN;
+        #pragma unroll 4
+        for (int n = 0; n < NFN; ++n) f4acc(tr, er[n], vc[n]);
+      } else {
+        const float* row = Tq + (quad_of<T>(f) * NQ + idx) * NP;
+        #pragma unroll 4
+        for (int m = 0; m < NP; ++m) f4acc(tr, row[m], q4[m]);
+      }
+      if (T == DG_WEDGE) {
+        const float is = A.sisq2[(e * NF + f) * NQ + idx];
+        tr.x *= is; tr.y *= is; tr.z *= is; tr.w *= is;
+      }
+      return tr;
+    };
+
+    float4 acc[R];
+    if (MODE != MODE_TRACE) {
+      // ---------------------------------------------------------------- volume
+      if (T == DG_TET) {
+        const float* g = A.geo + e * 12;
+        float G[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) G[i] = g[i];
+        for (int n = lane; n < NP; n += 32) {
+          const float4 v = q4[n];
+          W4[n] = f4(G[0] * v.y + G[1] * v.z + G[2] * v.w, G[3] * v.y + G[4] * v.z + G[5] * v.w,
+                     G[6] * v.y + G[7] * v.z + G[8] * v.w, v.x);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int n = lane + 32 * r;
+          if (n >= NP) break;
+          float dvr = 0.f, dvs = 0.f, dvt = 0.f, dpr = 0.f, dps = 0.f, dpt = 0.f;
+          const float4* drow = DV4 + n * NP;
+          #pragma unroll 4
+        for (int m = 0; m < NP; ++m) {
+            const float4 d = drow[m], w = W4[m];
+            dvr = fmaf(d.x, w.x, dvr);
+            dvs = fmaf(d.y, w.y, dvs);
+            dvt = fmaf(d.z, w.z, dvt);
+            dpr = fmaf(d.x, w.w, dpr);
+            dps = fmaf(d.y, w.w, dps);
+            dpt = fmaf(d.z, w.w, dpt);
+          }
+          const float div = dvr + dvs + dvt;
+          acc[r] = f4(-div, -c2 * (G[0] * dpr + G[3] * dps + G[6] * dpt), -c2 * (G[1] * dpr + G[4] * dps + G[7] * dpt),
+                      -c2 * (G[2] * dpr + G[5] * dps + G[8] * dpt));
+        }
+      } else if (T == DG_PYR) {
+        const float* geo = A.geo + e * NP * 10;
+        for (int m = lane; m < NP; m += 32) {
+          const float* g = geo + m * 10;
+          const float4 v = q4[m];
+          const float J = g[9];
+          W4[m] = f4(J * (g[0] * v.y + g[1] * v.z + g[2] * v.w), J * (g[3] * v.y + g[4] * v.z + g[5] * v.w),
+                     J * (g[6] * v.y + g[7] * v.z + g[8] * v.w), v.x);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int n = lane + 32 * r;
+          if (n >= NP) break;
+          float pr = 0.f, ps = 0.f, pt = 0.f, dpr = 0.f, dps = 0.f, dpt = 0.f;
+          #pragma unroll 4
+        for (int m = 0; m < NP; ++m) {
+            const float4 dc = DV4[m * NP + n], w = W4[m];   // (D^a)^T
+            pr = fmaf(dc.x, w.x, pr);
+            ps = fmaf(dc.y, w.y, ps);
+            pt = fmaf(dc.z, w.z, pt);
+            const float4 dr = DV4[n * NP + m];
+            dpr = fmaf(dr.x, w.w, dpr);
+            dps = fmaf(dr.y, w.w, dps);
+            dpt = fmaf(dr.z, w.w, dpt);
+          }
+          const float* g = geo + n * 10;
+          const float pint = pr + ps + pt;
+          acc[r] = f4(pint / g[9], -c2 * (g[0] * dpr + g[3] * dps + g[6] * dpt),
+                      -c2 * (g[1] * dpr + g[4] * dps + g[7] * dpt), -c2 * (g[2] * dpr + g[5] * dps + g[8] * dpt));
+        }
+      } else {   // wedge, sum-factorised (triangle x 1D) form of Alg. wedge_vol1/2
+        constexpr int NT = C::NT, N1 = C::N1;
+        float4* Y4 = W4;                  // phase 1: [NT][N1] sum_j V1 q ; phase 2: ZA
+        float4* Ys4 = W4 + NT * N1;       // phase 1: [NT][N1] sum_j D1 p (x); phase 2: ZB
+        float4* X1 = W4 + 2 * NT * N1;    // [NC] w (A0, A1, A2, UJ)
+        float4* X2 = X1 + NC;             // [NC] w (GU0, GU1, GU2, 0)
+        const float* geo = A.geo + e * NC * 12;
+        for (int x = lane; x < NT * N1; x += 32) {
+          const int mt = x / N1, l = x % N1;
+          float4 y = f4(0.f, 0.f, 0.f, 0.f);
+          float ys = 0.f;
+#pragma unroll
+          for (int j = 0; j < N1; ++j) {
+            const float4 v = q4[mt + NT * j];
+            f4acc(y, V1[l * N1 + j], v);
+            ys = fmaf(D1[l * N1 + j], v.x, ys);
+          }
+          Y4[x] = y;
+          Ys4[x] = f4(ys, 0.f, 0.f, 0.f);
+        }
+        __syncwarp();
+        for (int qc = lane; qc < NC; qc += 32) {
+          const int qt = qc % NQ, l = qc / NQ;
+          float P = 0.f, Pr = 0.f, Ps = 0.f, Pt = 0.f, U0 = 0.f, U1 = 0.f, U2 = 0.f;
+          const float4* vrow = DV4 + qt * NT;
+#pragma unroll 5
+          for (int mt = 0; mt < NT; ++mt) {
+            const float4 v = vrow[mt], y = Y4[mt * N1 + l];
+            P = fmaf(v.x, y.x, P);
+            Pr = fmaf(v.y, y.x, Pr);
+            Pt = fmaf(v.z, y.x, Pt);
+            Ps = fmaf(v.x, Ys4[mt * N1 + l].x, Ps);
+            U0 = fmaf(v.x, y.y, U0);
+            U1 = fmaf(v.x, y.z, U1);
+            U2 = fmaf(v.x, y.w, U2);
+          }
+          const float* g = geo + qc * 12;
+          const float w = wq[qt * N1 + l];
+          const float A0 = g[0] * Pr + g[3] * Ps + g[6] * Pt - P * g[9];
+          const float A1 = g[1] * Pr + g[4] * Ps + g[7] * Pt - P * g[10];
+          const float A2 = g[2] * Pr + g[5] * Ps + g[8] * Pt - P * g[11];
+          const float UJ = U0 * g[9] + U1 * g[10] + U2 * g[11];
+          X1[qc] = f4(w * A0, w * A1, w * A2, w * UJ);
+          X2[qc] = f4(w * (g[0] * U0 + g[1] * U1 + g[2] * U2), w * (g[3] * U0 + g[4] * U1 + g[5] * U2),
+                      w * (g[6] * U0 + g[7] * U1 + g[8] * U2), 0.f);
+        }
+        __syncwarp();
+        float4* ZA = Y4;
+        float4* ZB = Ys4;
+        for (int x = lane; x < NT * N1; x += 32) {
+          const int mt = x / N1, l = x % N1;
+          float4 za = f4(0.f, 0.f, 0.f, 0.f);
+          float zr = 0.f, zs = 0.f;
+#pragma unroll 5
+          for (int qt = 0; qt < NQ; ++qt) {
+            const float4 v = DV4[qt * NT + mt], x1 = X1[qt + NQ * l], x2 = X2[qt + NQ * l];
+            f4acc(za, v.x, x1);
+            zr = fmaf(v.y, x2.x, fmaf(v.z, x2.z, zr));
+            zs = fmaf(v.x, x2.y, zs);
+          }
+          ZA[x] = za;
+          ZB[x] = f4(zr, zs, 0.f, 0.f);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int n = lane + 32 * r;
+          if (n >= NP) break;
+          const int mt = n % NT, j = n / NT;
+          float u0 = 0.f, u1 = 0.f, u2 = 0.f, pp = 0.f;
+#pragma unroll
+          for (int l = 0; l < N1; ++l) {
+            const float v1 = V1[l * N1 + j], d1 = D1[l * N1 + j];
+            const float4 za = ZA[mt * N1 + l], zb = ZB[mt * N1 + l];
+            u0 = fmaf(v1, za.x, u0);
+            u1 = fmaf(v1, za.y, u1);
+            u2 = fmaf(v1, za.z, u2);
+            pp = fmaf(v1, zb.x - za.w, fmaf(d1, zb.y, pp));
+          }
+          acc[r] = f4(pp, -c2 * u0, -c2 * u1, -c2 * u2);
+        }
+      }
+      // ---------------------------------------------------------------- face fluxes
+      lattice_values();
+      __syncwarp();
+      for (int fq = lane; fq < NF * NQ; fq += 32) {
+        const int f = fq / NQ, idx = fq % NQ;
+        const float4 tr = trace_at(f, idx);
+        const int ci = tri_of<T>(f) >= 0 ? idx : qperm[code[f] * NQ + idx];
+        const int64_t gs = A.side_off + e * NF + f;
+        const float4 sg = A.sgeo2[(e * NF + f) * NQ + idx];
+        const float unm = sg.x * tr.y + sg.y * tr.z + sg.z * tr.w;
+        const int nb = A.nbr[gs];
+        float P = 0.f, UN = 0.f;
+        if (nb >= 0) {
+          P = A.tin[gs * NQ + ci];
+          UN = A.tin[A.plane + gs * NQ + ci];
+        }
+        const float ta = A.tau[gs];
+        float fp, fu;
+        flux(nb < 0, tr.x, unm, P, UN, A.tau_scale * ta, A.tau_scale / ta, T != DG_TET && A.skew, fp, fu);
+        F4[fq] = f4(sg.w * fp, sg.w * fu * sg.x, sg.w * fu * sg.y, sg.w * fu * sg.z);
+      }
+      __syncwarp();
+      // lattice moments of the triangle-face fluxes, in local lattice order
+      for (int x = lane; x < NTRI * NFN; x += 32) {
+        const int ti = x / NFN, nl = x % NFN;
+        const int f = face_of_tri<T>(ti);
+        const int nc = tperm[code[f] * NFN + nl];
+        float4 gsum = f4(0.f, 0.f, 0.f, 0.f);
+        const float4* fr = F4 + f * NQ;
+        #pragma unroll 4
+        for (int q = 0; q < NQ; ++q) f4acc(gsum, E[q * NFN + nc], fr[q]);
+        G4[x] = gsum;
+      }
+      __syncwarp();
+      // ---------------------------------------------------------------- lift, M^{-1}, update
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int n = lane + 32 * r;
+        if (n >= NP) break;
+        float4 sum = f4(0.f, 0.f, 0.f, 0.f);
+        #pragma unroll 4
+        for (int x = 0; x < NTRI * NFN; ++x) f4acc(sum, Tn[x * NP + n], G4[x]);
+#pragma unroll
+        for (int qi = 0; qi < NQUAD; ++qi) {
+          const int f = T == DG_PYR ? 0 : 2 + qi;
+          const float* col = Tq + qi * NQ * NP + n;
+          const float4* fr = F4 + f * NQ;
+          #pragma unroll 4
+        for (int lp = 0; lp < NQ; ++lp) f4acc(sum, col[lp * NP], fr[lp]);
+        }
+        float iM = 1.f;
+        if (T == DG_TET) iM = 1.f / A.geo[e * 12 + 9];
+        if (T == DG_PYR) iM = 1.f / A.geo[(e * NP + n) * 10 + 9];
+        acc[r].x += iM * sum.x;
+        acc[r].y += c2 * iM * sum.y;
+        acc[r].z += c2 * iM * sum.z;
+        acc[r].w += c2 * iM * sum.w;
+      }
+      if (MODE == MODE_RHS) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int n = lane + 32 * r;
+          if (n >= NP) break;
+          A.rhs[base + n] = acc[r].x;
+          A.rhs[A.ndof + base + n] = acc[r].y;
+          A.rhs[2 * A.ndof + base + n] = acc[r].z;
+          A.rhs[3 * A.ndof + base + n] = acc[r].w;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int n = lane + 32 * r;
+          if (n >= NP) break;
+          const float rv[4] = {acc[r].x, acc[r].y, acc[r].z, acc[r].w};
+          const float4 qo = q4[n];
+          const float qv[4] = {qo.x, qo.y, qo.z, qo.w};
+          float qn[4];
+#pragma unroll
+          for (int fl = 0; fl < 4; ++fl) {
+            const int64_t id = fl * A.ndof + base + n;
+            const float rr = A.a * A.res[id] + A.dt * rv[fl];
+            qn[fl] = qv[fl] + A.b * rr;
+            A.res[id] = rr;
+            A.qout[id] = qn[fl];
+          }
+          acc[r] = f4(qn[0], qn[1], qn[2], qn[3]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int n = lane + 32 * r;
+          if (n < NP) q4[n] = acc[r];
+        }
+        __syncwarp();
+      }
+    }
+    if (MODE == MODE_TRACE || MODE == MODE_STAGE) {
+      lattice_values();
+      __syncwarp();
+      for (int fq = lane; fq < NF * NQ; fq += 32) {
+        const int f = fq / NQ, idx = fq % NQ;
+        const int64_t gs = A.side_off + e * NF + f;
+        const int nb = A.nbr[gs];
+        if (nb < 0) continue;
+        const float4 tr = trace_at(f, idx);
+        const int ci = tri_of<T>(f) >= 0 ? idx : qperm[code[f] * NQ + idx];
+        const float4 sg = A.sgeo2[(e * NF + f) * NQ + idx];
+        A.tout[(int64_t)nb * NQ + ci] = tr.x;
+        A.tout[A.plane + (int64_t)nb * NQ + ci] = sg.x * tr.y + sg.y * tr.z + sg.z * tr.w;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int T, int N, int MODE>
+static bool launch_one(const Args& A, cudaStream_t s) {
+  using C = G2<T, N>;
+  if (C::SMEM > 227 * 1024) return false;
+  static int blocks = 0;   // persistent grid: resident blocks per SM x SMs (computed once)
+  if (blocks == 0) {
+    if (cudaFuncSetAttribute(gen2_kernel<T, N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
+        cudaSuccess)
+      return false;
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gen2_kernel<T, N, MODE>, C::NW * 32, C::SMEM);
+    if (per < 1) return false;
+    blocks = per * sms;
+  }
+  const int64_t need = ((int64_t)A.K + C::NW - 1) / C::NW;
+  const int grid = (int)(need < blocks ? need : blocks);
+  gen2_kernel<T, N, MODE><<<grid, C::NW * 32, C::SMEM, s>>>(A);
+  return true;
+}
+
+template <int MODE>
+bool launch_gen2(int t, int N, const Args& A, cudaStream_t s) {
+  if (A.K == 0) return true;
+  if (!A.ops2) return false;
+  switch (N) {
+#define G2_CASE(NN)                                                        \
+  case NN:                                                                 \
+    if (t == DG_TET) return launch_one<DG_TET, NN, MODE>(A, s);            \
+    if (t == DG_PYR) return launch_one<DG_PYR, NN, MODE>(A, s);            \
+    if (t == DG_WEDGE) return launch_one<DG_WEDGE, NN, MODE>(A, s);        \
+    return false;
+    G2_CASE(1) G2_CASE(2) G2_CASE(3) G2_CASE(4)
+#undef G2_CASE
+    default: return false;
+  }
+}
+
+template bool launch_gen2<MODE_TRACE>(int, int, const Args&, cudaStream_t);
+template bool launch_gen2<MODE_RHS>(int, int, const Args&, cudaStream_t);
+template bool launch_gen2<MODE_STAGE>(int, int, const Args&, cudaStream_t);
+
+}  // namespace dgk

@@ -362,8 +362,10 @@ void Basis::eval(const double* rst, double* phi, double* g) const {
       }
     }
   } else {  // PYR: l^k_i(a) l^k_j(b) h^k P^{(2k+3,0)}_{N-k}(c) / sqrt(w_i w_j gamma_k)
+    // At the apex (h = 0) a and b are undefined but bounded inside the pyramid and every
+    // level k >= 1 carries h^k -> 0; any bounded (a,b) gives the limit (values only).
     double t = rst[2], h = 0.5 * (1 - t);
-    double a = (1 + rst[0]) / h - 1, b = (1 + rst[1]) / h - 1;
+    double a = h > 1e-14 ? (1 + rst[0]) / h - 1 : 0.0, b = h > 1e-14 ? (1 + rst[1]) / h - 1 : 0.0;
     std::vector<double> la(N + 1), dla(N + 1), lb(N + 1), dlb(N + 1);
     int kprev = -1;
     for (int m = 0; m < Np; ++m) {

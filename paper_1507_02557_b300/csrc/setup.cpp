@@ -321,6 +321,78 @@ T* alloc_zero(size_t n, std::vector<void*>& owned) {
 
 std::vector<void*>& owned_list(dg_mesh* m);
 
+
+// ----------------------------------------------------------------------------- orientation-free face operators
+// Triangle faces use the equispaced face lattice (l0,l1,l2), l0+l1+l2 = N, indexed
+// by (l1,l2) with l2 outer, l1 inner.  A lattice node has barycentric weights l/N on
+// the face's local corners; in the canonical frame its weights are l permuted by the
+// face key, so the frame only permutes lattice nodes.  E[q][n] interpolates values at
+// the canonical lattice to the canonical quadrature points (exact for P_N traces).
+// Quadrilateral faces are handled at local GL points plus a permutation (hexperm).
+int lattice_index(int N, int l1, int l2) {
+  int idx = 0;
+  for (int b = 0; b < l2; ++b) idx += N + 1 - b;
+  return idx + l1;
+}
+
+void lattice_tables(int N, std::vector<int>& tperm, std::vector<int>& tinv, std::vector<double>& E,
+                    const std::vector<double>& tpts) {
+  const int nfn = (N + 1) * (N + 2) / 2, nq = (N + 1) * (N + 1);
+  tperm.assign(6 * nfn, 0);
+  tinv.assign(6 * nfn, 0);
+  for (int c = 0; c < 6; ++c) {
+    int key[4];
+    face_code_key(3, c, key);
+    for (int l2 = 0; l2 <= N; ++l2)
+      for (int l1 = 0; l1 + l2 <= N; ++l1) {
+        int l[3] = {N - l1 - l2, l1, l2};
+        int m1 = l[key[1]], m2 = l[key[2]];
+        int nl = lattice_index(N, l1, l2), nc = lattice_index(N, m1, m2);
+        tperm[c * nfn + nl] = nc;
+        tinv[c * nfn + nc] = nl;
+      }
+  }
+  // Lagrange basis of the lattice via monomials in (lam1, lam2), evaluated at the face points
+  std::vector<double> V(nfn * nfn);
+  auto mono = [&](double a, double b, double* out) {
+    int k = 0;
+    for (int i = 0; i <= N; ++i)
+      for (int j = 0; i + j <= N; ++j) out[k++] = std::pow(a, i) * std::pow(b, j);
+  };
+  for (int l2 = 0; l2 <= N; ++l2)
+    for (int l1 = 0; l1 + l2 <= N; ++l1) mono((double)l1 / N, (double)l2 / N, &V[lattice_index(N, l1, l2) * nfn]);
+  // invert V (rows = nodes, cols = monomials)
+  std::vector<double> I(nfn * nfn, 0.0);
+  for (int i = 0; i < nfn; ++i) I[i * nfn + i] = 1;
+  for (int c = 0; c < nfn; ++c) {
+    int p = c;
+    for (int r = c + 1; r < nfn; ++r)
+      if (std::fabs(V[r * nfn + c]) > std::fabs(V[p * nfn + c])) p = r;
+    for (int k = 0; k < nfn; ++k) {
+      std::swap(V[p * nfn + k], V[c * nfn + k]);
+      std::swap(I[p * nfn + k], I[c * nfn + k]);
+    }
+    double dv = 1.0 / V[c * nfn + c];
+    for (int k = 0; k < nfn; ++k) { V[c * nfn + k] *= dv; I[c * nfn + k] *= dv; }
+    for (int r = 0; r < nfn; ++r) {
+      if (r == c) continue;
+      double f = V[r * nfn + c];
+      for (int k = 0; k < nfn; ++k) { V[r * nfn + k] -= f * V[c * nfn + k]; I[r * nfn + k] -= f * I[c * nfn + k]; }
+    }
+  }
+  // ell_n(x) = sum_k mono_k(x) I[k][n]   (I = V^{-1}: V[n][k] = mono_k(x_n))
+  E.assign(nq * nfn, 0.0);
+  std::vector<double> mv(nfn);
+  for (int q = 0; q < nq; ++q) {
+    mono(0.5 * (1 + tpts[2 * q]), 0.5 * (1 + tpts[2 * q + 1]), mv.data());
+    for (int n = 0; n < nfn; ++n) {
+      double v = 0;
+      for (int k = 0; k < nfn; ++k) v += mv[k] * I[k * nfn + n];
+      E[q * nfn + n] = v;
+    }
+  }
+}
+
 }  // namespace
 
 // ----------------------------------------------------------------------------- registry of allocations
@@ -569,8 +641,8 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
       td.geo = upload(geo, owned);
 
       // face geometry (non-hex: stored; all types: time-step data)
-      std::vector<float4> sgeo;
-      std::vector<float> sisq;
+      std::vector<float4> sgeo, sgeo2;
+      std::vector<float> sisq, sisq2;
       for (int64_t e = 0; e < K; ++e) {
         load_xv(e);
         for (int f = 0; f < nf; ++f) {
@@ -583,9 +655,14 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
           const double* og = face_outward(t, f);
           taup[t][e] = std::max(taup[t][e], taud[s]);
           tauu[t][e] = std::max(tauu[t][e], 1.0 / taud[s]);
+          for (int pass = 0; pass < (t == HEX ? 1 : 2); ++pass)
           for (int q = 0; q < nq; ++q) {
             double rst[3], d1[3], d2[3], F[9], G[9];
-            face_point(t, f, key, pts[2 * q], pts[2 * q + 1], rst, d1, d2);
+            // pass 0: canonical points; pass 1: the order of the orientation-free kernels
+            // (canonical points on triangles, local points on quadrilaterals)
+            static const int ident[4] = {0, 1, 2, 3};
+            const int* kk = (pass == 1 && fnv == 4) ? ident : key;
+            face_point(t, f, kk, pts[2 * q], pts[2 * q + 1], rst, d1, d2);
             map_jacobian(t, xv.data(), rst, F);
             double J = inverse_metric(F, G);
             double x1[3], x2[3], nn[3];
@@ -601,21 +678,28 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
                             d1[0] * d2[1] - d1[1] * d2[0]};
             double Jsref = std::sqrt(rc[0] * rc[0] + rc[1] * rc[1] + rc[2] * rc[2]);
             double nl = std::sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
-            jsmax[t][e] = std::max(jsmax[t][e], Js / Jsref);
-            jsj[t][e] = std::max(jsj[t][e], Js / Jsref / J);
+            if (pass == 0) {
+              jsmax[t][e] = std::max(jsmax[t][e], Js / Jsref);
+              jsj[t][e] = std::max(jsj[t][e], Js / Jsref / J);
+            }
             if (!(J > 0)) throw SetupError(DG_EMESH, "J <= 0 at a face point");
             if (t != HEX) {
               double wj = w[q] * Js;
               if (t == WEDGE) wj /= std::sqrt(J);
-              sgeo.push_back(make_float4((float)(nn[0] / nl), (float)(nn[1] / nl), (float)(nn[2] / nl), (float)wj));
-              if (t == WEDGE) sisq.push_back((float)(1.0 / std::sqrt(J)));
+              float4 gv = make_float4((float)(nn[0] / nl), (float)(nn[1] / nl), (float)(nn[2] / nl), (float)wj);
+              (pass == 0 ? sgeo : sgeo2).push_back(gv);
+              if (t == WEDGE) (pass == 0 ? sisq : sisq2).push_back((float)(1.0 / std::sqrt(J)));
             }
           }
         }
       }
       if (t != HEX) {
         td.sgeo = upload(sgeo, owned);
-        if (t == WEDGE) td.sisq = upload(sisq, owned);
+        td.sgeo2 = upload(sgeo2, owned);
+        if (t == WEDGE) {
+          td.sisq = upload(sisq, owned);
+          td.sisq2 = upload(sisq2, owned);
+        }
       }
 
       // reference operators
@@ -801,6 +885,163 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
           }
         }
         td.ops = upload(ops, owned);
+
+        // ---- orientation-free operators (kernels_gen2.cu); float layout:
+        //  tet:   DV4[Np][Np] (D^r,D^s,D^t,0) | Lf[4][nfn][Np] = Mhat^{-1}[i][fnode] | E[nq][nfn]
+        //  pyr:   DV4[Np][Np] | Tn[4][nfn][Np] (tri faces 1..4) | Tq[nq][Np] (base) | E[nq][nfn]
+        //  wedge: VV4[nc][Np] (V,V_r,V_s,V_t) | wq[nc] | Tn[2][nfn][Np] | Tq[3][nq][Np] | E[nq][nfn]
+        //  int layout: tperm[6][nfn] | tinv[6][nfn] | qperm[8][nq] | (tet) fnode[4][nfn]
+        const int nfn = (N + 1) * (N + 2) / 2;
+        std::vector<int> tperm, tinv;
+        std::vector<double> E;
+        lattice_tables(N, tperm, tinv, E, tpts);
+        std::vector<float> o2;
+        std::vector<int> i2(tperm.begin(), tperm.end());
+        i2.insert(i2.end(), tinv.begin(), tinv.end());
+        {
+          // quad perm (same construction as the hexahedron's)
+          const double P[4][2] = {{-1, -1}, {1, -1}, {-1, 1}, {1, 1}};
+          std::vector<double> gx, gw;
+          gauss_jacobi(n1, 0, 0, gx, gw);
+          std::vector<int> qp(dgk::NCODES * nq, 0);
+          for (int c = 0; c < dgk::NCODES; ++c) {
+            int key[4];
+            face_code_key(4, c, key);
+            for (int ib = 0; ib < n1; ++ib)
+              for (int ia = 0; ia < n1; ++ia) {
+                double uv[2];
+                for (int k2 = 0; k2 < 2; ++k2)
+                  uv[k2] = P[key[0]][k2] + 0.5 * (1 + gx[ia]) * (P[key[1]][k2] - P[key[0]][k2]) +
+                           0.5 * (1 + gx[ib]) * (P[key[2]][k2] - P[key[0]][k2]);
+                int iu = 0, iv = 0;
+                for (int i = 0; i < n1; ++i) {
+                  if (std::fabs(gx[i] - uv[0]) < std::fabs(gx[iu] - uv[0])) iu = i;
+                  if (std::fabs(gx[i] - uv[1]) < std::fabs(gx[iv] - uv[1])) iv = i;
+                }
+                qp[c * nq + iu + n1 * iv] = ia + n1 * ib;
+              }
+          }
+          i2.insert(i2.end(), qp.begin(), qp.end());
+        }
+        auto lattice_rst = [&](int f, int l1, int l2, double rst[3]) {
+          const int* fv = face_verts(t, f);
+          const double l[3] = {(double)(N - l1 - l2) / N, (double)l1 / N, (double)l2 / N};
+          for (int c = 0; c < 3; ++c)
+            rst[c] = l[0] * vert_rst(t, fv[0])[c] + l[1] * vert_rst(t, fv[1])[c] + l[2] * vert_rst(t, fv[2])[c];
+        };
+        std::vector<double> gg(3 * Np);
+        if (t == TET || t == PYR) {
+          // DV4[n][m] = (D^r, D^s, D^t)[n][m], row n = node / test function
+          for (int n = 0; n < Np; ++n)
+            for (int mm = 0; mm < Np; ++mm) {
+              if (t == TET) {
+                // ops holds DT[a][m][n]
+                for (int a = 0; a < 3; ++a) o2.push_back(ops[(a * Np + mm) * Np + n]);
+              } else {
+                for (int a = 0; a < 3; ++a) o2.push_back(ops[(a * Np + n) * Np + mm]);
+              }
+              o2.push_back(0.f);
+            }
+        }
+        if (t == TET) {
+          std::vector<int> fnode(4 * nfn, -1);
+          for (int f = 0; f < 4; ++f)
+            for (int l2 = 0; l2 <= N; ++l2)
+              for (int l1 = 0; l1 + l2 <= N; ++l1) {
+                double rst[3];
+                lattice_rst(f, l1, l2, rst);
+                for (int n = 0; n < Np; ++n) {
+                  const double* x = &B[t].nodes[3 * n];
+                  if (std::fabs(x[0] - rst[0]) + std::fabs(x[1] - rst[1]) + std::fabs(x[2] - rst[2]) < 1e-9)
+                    fnode[f * nfn + lattice_index(N, l1, l2)] = n;
+                }
+              }
+          for (int v : fnode)
+            if (v < 0) throw SetupError(DG_EINVAL, "tet face lattice not found among the nodes");
+          for (int f = 0; f < 4; ++f)
+            for (int n = 0; n < nfn; ++n)
+              for (int i = 0; i < Np; ++i) o2.push_back((float)Minv[i * Np + fnode[f * nfn + n]]);
+          i2.insert(i2.end(), fnode.begin(), fnode.end());
+        } else {
+          if (t == WEDGE) {
+            // tensor-product factors of the wedge basis and cubature (Sec. 2.3.3): phi_(mt,j) =
+            // phi_tri_mt(r,t) phi_1D_j(s); points (qt, l).  Layout: Vt4[nqt][ntri] (phi, d/dr, d/dt, 0) |
+            // V1[n1 (l)][n1 (j)] | D1[n1][n1] | w[nqt][n1] (w[qt] * w_l).
+            const int ntri = Np / n1, nqt = nq;   // (N+1)(N+2)/2 triangle modes, (N+1)^2 triangle points
+            std::vector<double> tp, tww, sx, sw;
+            tri_rule(N, tp, tww);
+            gauss_jacobi(n1, 0, 0, sx, sw);
+            std::vector<double> Vt(nqt * ntri), Vtr(nqt * ntri), Vtt(nqt * ntri), V1(n1 * n1), D1(n1 * n1);
+            // separable factors from the full basis: phi_(mt,0) = phi_tri_mt * phi_1D_0, phi_1D_0 = 1/sqrt(2)
+            for (int qt = 0; qt < nqt; ++qt) {
+              double rst[3] = {tp[2 * qt], 0.0, tp[2 * qt + 1]};
+              B[t].eval(rst, phi.data(), gg.data());
+              for (int mt = 0; mt < ntri; ++mt) {
+                Vt[qt * ntri + mt] = phi[mt] * std::sqrt(2.0);
+                Vtr[qt * ntri + mt] = gg[mt] * std::sqrt(2.0);
+                Vtt[qt * ntri + mt] = gg[2 * Np + mt] * std::sqrt(2.0);
+              }
+            }
+            for (int l = 0; l < n1; ++l)
+              for (int j = 0; j < n1; ++j) {
+                V1[l * n1 + j] = std::sqrt((2.0 * j + 1) / 2) * jacobi(j, 0, 0, sx[l]);
+                D1[l * n1 + j] = std::sqrt((2.0 * j + 1) / 2) * jacobi_deriv(j, 0, 0, sx[l]);
+              }
+            // check the factorisation against the full basis at every cubature point
+            for (int q = 0; q < td.nc; ++q) {
+              const int qt = q % nqt, l = q / nqt;
+              B[t].eval(&wedge_pts[3 * q], phi.data(), gg.data());
+              for (int mm = 0; mm < Np; ++mm) {
+                const int mt = mm % ntri, j = mm / ntri;
+                const double ref[4] = {phi[mm], gg[mm], gg[Np + mm], gg[2 * Np + mm]};
+                const double fac[4] = {Vt[qt * ntri + mt] * V1[l * n1 + j], Vtr[qt * ntri + mt] * V1[l * n1 + j],
+                                       Vt[qt * ntri + mt] * D1[l * n1 + j], Vtt[qt * ntri + mt] * V1[l * n1 + j]};
+                for (int c = 0; c < 4; ++c)
+                  if (std::fabs(ref[c] - fac[c]) > 1e-10 * (1 + std::fabs(ref[c])))
+                    throw SetupError(DG_EINVAL, "wedge basis does not factor");
+              }
+            }
+            for (int qt = 0; qt < nqt; ++qt)
+              for (int mt = 0; mt < ntri; ++mt) {
+                o2.push_back((float)Vt[qt * ntri + mt]);
+                o2.push_back((float)Vtr[qt * ntri + mt]);
+                o2.push_back((float)Vtt[qt * ntri + mt]);
+                o2.push_back(0.f);
+              }
+            for (double v : V1) o2.push_back((float)v);
+            for (double v : D1) o2.push_back((float)v);
+            for (int qt = 0; qt < nqt; ++qt)
+              for (int l = 0; l < n1; ++l) o2.push_back((float)(tww[qt] * sw[l]));
+          }
+          // triangle-face lattice evaluations, then quad-face local GL evaluations
+          std::vector<double> gx, gw;
+          gauss_jacobi(n1, 0, 0, gx, gw);
+          for (int f = 0; f < nf; ++f) {
+            if (face_nverts(t, f) != 3) continue;
+            for (int l2 = 0; l2 <= N; ++l2)
+              for (int l1 = 0; l1 + l2 <= N; ++l1) {
+                double rst[3];
+                lattice_rst(f, l1, l2, rst);
+                B[t].eval(rst, phi.data(), nullptr);
+                for (int i = 0; i < Np; ++i) o2.push_back((float)phi[i]);
+              }
+          }
+          static const int ident[4] = {0, 1, 2, 3};
+          for (int f = 0; f < nf; ++f) {
+            if (face_nverts(t, f) != 4) continue;
+            for (int q = 0; q < nq; ++q) {
+              double rst[3], d1[3], d2[3];
+              face_point(t, f, ident, qpts[2 * q], qpts[2 * q + 1], rst, d1, d2);
+              B[t].eval(rst, phi.data(), nullptr);
+              for (int i = 0; i < Np; ++i) o2.push_back((float)phi[i]);
+            }
+          }
+        }
+        for (double v : E) o2.push_back((float)v);
+        td.ops2 = upload(o2, owned);
+        td.iops2 = upload(i2, owned);
+        td.nops2 = (int)o2.size();
+        td.niops2 = (int)i2.size();
       }
     }
 
