@@ -144,13 +144,20 @@ def run_reference(args, rank, world):
 
 
 def hex_alg_bytes(N):
-    """Algorithmic bytes of one hex element: fused LSRK stage, trace-only and rhs-only launches."""
+    """Algorithmic bytes of one hex element per launch of each kernel mode.
+
+    stage: fused LSRK stage (q, res read and written; traces read and written)
+    trace: trace-only launch (q read, traces written)
+    mrc:   fused multi-rate coarse step (q, two history slots read; rhs, q written; traces read,
+           half-step and full-step traces written)
+    mrf:   fused multi-rate fine substep (as mrc with one trace set written)
+    """
     NP, NQ = (N + 1) ** 3, (N + 1) ** 2
-    side = 96 + 6 * 12                                          # trilinear geometry + per-face side data
-    stage = 4 * NP * 4 * 4 + side + 4 + 2 * 6 * NQ * 8          # q,res read+write; c2; traces read+write
-    trace = 4 * NP * 4 + side + 6 * NQ * 8                      # q read; traces written
-    rhs = 4 * NP * 4 * 2 + side + 4 + 6 * NQ * 8                # q read, rhs written; traces read
-    return stage, trace, rhs
+    side = 96 + 6 * 12 + 4                                      # trilinear geometry, per-face side data, c2
+    st = 4 * NP * 4                                             # one state-sized array of one element
+    tr = 6 * NQ * 8                                             # one trace set (p, u.n) of one element
+    return {"stage": 4 * st + 2 * tr + side, "trace": st + tr + side - 4,
+            "mrc": 5 * st + 3 * tr + side, "mrf": 5 * st + 2 * tr + side}
 
 
 def timed_run(g, torch, stream, steps, dt, barrier):
@@ -204,7 +211,7 @@ def main():
         pass
     hbm = float(peaks.get("hbm_gbs", 6400.0))
     K_hex = mesh.nelem[0]
-    b_stage, b_trace, b_rhs = hex_alg_bytes(ORDER)
+    hb = hex_alg_bytes(ORDER)
 
     def barrier():
         if dist:
@@ -228,7 +235,7 @@ def main():
     ms1, kms1, l1, clk1 = timed_run(g1, torch, stream, args.steps, dt, barrier)
     ms1 = max_ms(ms1)
     n_stage = 5 * args.steps
-    hex_bytes1 = K_hex * (b_stage * n_stage + b_trace * (l1[0] - n_stage))
+    hex_bytes1 = K_hex * (hb["stage"] * n_stage + hb["trace"] * (l1[0] - n_stage))
     ach1 = hex_bytes1 / (kms1[0] / 1e3) / 1e9
     single = {"value": ndof * 5 * args.steps * world / (ms1 / 1e3) / 1e9, "unit": METRIC,
               "ms_per_step": ms1 / args.steps, "integrator": "LSRK(5,4), 5 stages per step",
@@ -251,8 +258,9 @@ def main():
     ms = max_ms(ms)
     stage_units = (ndof + ndof_fine) * args.steps * world    # rhs evaluations actually performed
     value = stage_units / (ms / 1e3) / 1e9
-    # hex kernels per coarse step: traces of all hexes twice, rhs of all hexes + the fine ones again
-    hex_bytes = args.steps * (2 * K_hex * b_trace + (K_hex + fine[0]) * b_rhs)
+    # hex kernels: one trace launch per dg_step call, then per coarse step the fused coarse
+    # step of the coarse hexes and two fused substeps of the fine hexes
+    hex_bytes = K_hex * hb["trace"] + args.steps * ((K_hex - fine[0]) * hb["mrc"] + 2 * fine[0] * hb["mrf"])
     achieved = hex_bytes / (kms[0] / 1e3) / 1e9
     traffic = None
     # end to end through the public API with host buffers: one simulation call = H2D of the
@@ -297,7 +305,7 @@ def main():
                     "integrator": "two-level multi-rate AB3 (step = one coarse step of 2h)",
                     "ndof": ndof, "ndof_fine": ndof_fine, "elements": mesh.nelem, "fine_elements": fine,
                     "h_fine": h, "parallelism": "replicas" if world > 1 else "single GPU"}),
-                "roofline": {"bound": "hbm", "kernel": "hexw_kernel<4,TRACE|RHS> (multi-rate)",
+                "roofline": {"bound": "hbm", "kernel": "hexw_kernel<4,MRC> (fused multi-rate coarse step)",
                              "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                              "traffic": traffic, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
                 "kernel_ms": dict(zip(["hex", "wedge", "pyramid", "tet"], kms)),

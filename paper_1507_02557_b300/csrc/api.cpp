@@ -251,6 +251,57 @@ cudaError_t mrab3(dg_mesh* m, int nsteps, double h) {
   return cudaSuccess;
 }
 
+// Fused form of mrab3 for N <= 4: one kernel per type and level and substep computes the rhs,
+// stores it in the history, applies the AB3 update (and the coarse half-step prediction) and
+// deposits the traces for the next substep.  Trace buffers: A (t_n), B (t_n + h), C (t_n + 2h).
+cudaError_t mrab3_fused(dg_mesh* m, int nsteps, double h) {
+  const size_t fs = 4 * (size_t)m->ndof;
+  float* H[3] = {m->hist, m->hist + fs, m->hist + 2 * fs};
+  const dgk::Sel &C = m->lev[0], &F = m->lev[1];
+  cudaError_t e;
+  if (!m->mr_started) {
+    if ((e = rhs_to(m, m->q, H[2], m->all)) != cudaSuccess) return e;   // r(0)
+    if ((e = lsrk_steps(m, 2, h)) != cudaSuccess) return e;
+    if ((e = rhs_to(m, m->q, H[1], m->all)) != cudaSuccess) return e;   // r(2h)
+    if ((e = lsrk_steps(m, 1, h)) != cudaSuccess) return e;
+    if ((e = rhs_to(m, m->q, H[0], m->all)) != cudaSuccess) return e;   // r(3h)
+    if ((e = lsrk_steps(m, 1, h)) != cudaSuccess) return e;
+    m->cslot[0] = 0; m->cslot[1] = 1; m->cslot[2] = 2;
+    m->fslot[0] = 2; m->fslot[1] = 0; m->fslot[2] = 1;
+    m->mr_started = true;
+  }
+  const size_t plane2 = 2 * (size_t)m->nsides * m->nq;
+  float* TA = m->trace;
+  float* TB = m->trace + plane2;
+  float* TC = m->trace3;
+  if ((e = dgk::launch_trace(m, m->q, TA)) != cudaSuccess) return e;
+  const float hc = (float)(2 * h), hf = (float)h;
+  const float ac[3] = {hc * 23.f / 12.f, -hc * 16.f / 12.f, hc * 5.f / 12.f};
+  const float pc[3] = {hc * 17.f / 24.f, -hc * 7.f / 24.f, hc * 2.f / 24.f};
+  const float af[3] = {hf * 23.f / 12.f, -hf * 16.f / 12.f, hf * 5.f / 12.f};
+  const float zero[3] = {0.f, 0.f, 0.f};
+  for (int s = 0; s < nsteps; ++s) {
+    int* c = m->cslot;
+    int* f = m->fslot;
+    if ((e = dgk::launch_mr(m, true, C, m->q, TA, TB, TC, H[c[0]], H[c[1]], H[c[2]], ac, pc)) != cudaSuccess)
+      return e;
+    if ((e = dgk::launch_mr(m, false, F, m->q, TA, TB, nullptr, H[f[0]], H[f[1]], H[f[2]], af, zero)) !=
+        cudaSuccess)
+      return e;
+    if ((e = dgk::launch_mr(m, false, F, m->q, TB, TC, nullptr, H[f[2]], H[f[0]], H[f[1]], af, zero)) !=
+        cudaSuccess)
+      return e;
+    int f0 = f[0], f1 = f[1], f2 = f[2];
+    f[0] = f1; f[1] = f2; f[2] = f0;
+    int c0 = c[0], c1 = c[1], c2 = c[2];
+    c[0] = c2; c[1] = c0; c[2] = c1;
+    float* tmp = TA;
+    TA = TC;
+    TC = tmp;
+  }
+  return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" dg_status dg_step(dg_mesh* m, int nsteps, double dt, double* t_inout) {
@@ -259,7 +310,7 @@ extern "C" dg_status dg_step(dg_mesh* m, int nsteps, double dt, double* t_inout)
   if (nsteps == 0) return DG_OK;
   if (m->nlevels == 2) {
     bool fresh = !m->mr_started;
-    cudaError_t e = mrab3(m, nsteps, dt);
+    cudaError_t e = m->N <= 4 ? mrab3_fused(m, nsteps, dt) : mrab3(m, nsteps, dt);
     if (e != cudaSuccess) return cuda_fail(e);
     if (t_inout) *t_inout += (fresh ? 4 * dt : 0.0) + nsteps * 2 * dt;
     return DG_OK;

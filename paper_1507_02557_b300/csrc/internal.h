@@ -69,6 +69,7 @@ struct dg_mesh {
   dgk::Sel all, lev[2];           // lev[0] = coarse (level 1), lev[1] = fine (level 2)
   int64_t level_count[2] = {0, 0};
   float* hist = nullptr;          // [3 slots][4][ndof]
+  float* trace3 = nullptr;        // third trace buffer of the fused multi-rate schedule
   int cslot[3] = {0, 1, 2}, fslot[3] = {2, 0, 1};   // slots of r^n, r^{n-1}, r^{n-2} per level
   bool mr_started = false;
   // per-type kernel timing (dg_profile): event pairs recorded around each launch
@@ -88,6 +89,12 @@ cudaError_t launch_stage(dg_mesh* m, float* q, float* res, const float* tin, flo
 cudaError_t launch_energy(dg_mesh* m, const float* q, double* acc);
 cudaError_t launch_trace_sel(dg_mesh* m, const float* q, float* tout, const Sel& sel);
 cudaError_t launch_rhs_sel(dg_mesh* m, const float* q, const float* tin, float* rhs, const Sel& sel);
+// Fused multi-rate AB3 step for the elements of sel (N <= 4): coarse elements write the traces of
+// the half-step prediction to tout and of the new state to tout2; fine elements those of the new
+// state to tout.  rhs -> hw, q += c0 rhs + c1 h1 + c2 h2, prediction q + p0 rhs + p1 h1 + p2 h2.
+cudaError_t launch_mr(dg_mesh* m, bool coarse, const Sel& sel, float* q, const float* tin, float* tout,
+                      float* tout2, float* hw, const float* h1, const float* h2, const float c[3],
+                      const float p[3]);
 cudaError_t launch_ab(dg_mesh* m, const Sel& sel, const float* qin, float* qout, const float* r0,
                       const float* r1, const float* r2, float h0, float h1, float h2);
 // Hex constants (1D D, V^f, GL weights and nodes) of order N <= 4 into constant memory.

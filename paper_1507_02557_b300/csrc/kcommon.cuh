@@ -8,7 +8,9 @@
 
 namespace dgk {
 
-enum { MODE_TRACE = 0, MODE_RHS = 1, MODE_STAGE = 2 };
+// TRACE: traces only; RHS: write rhs; STAGE: fused LSRK stage;
+// MRC / MRF: fused multi-rate AB3 step of a coarse / fine element (see api.cpp).
+enum { MODE_TRACE = 0, MODE_RHS = 1, MODE_STAGE = 2, MODE_MRC = 3, MODE_MRF = 4 };
 
 struct Args {
   const float* q;     // state in  [4][ndof]
@@ -39,6 +41,13 @@ struct Args {
   int64_t dof_off, ndof, side_off;
   float a, b, dt, tau_scale;
   int skew;
+  // multi-rate AB3 (MRC, MRF): rhs written to hw; q <- q + ab0 r + ab1 h1 + ab2 h2; coarse elements
+  // also emit the traces of the prediction q + pr0 r + pr1 h1 + pr2 h2 to tout and of the new q to tout2
+  float* hw;
+  const float* h1;
+  const float* h2;
+  float ab0, ab1, ab2, pr0, pr1, pr2;
+  float* tout2;
 };
 
 __device__ __forceinline__ void flux(bool wall, float pm, float unm, float P, float UN, float tp,

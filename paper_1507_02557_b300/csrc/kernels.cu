@@ -267,6 +267,10 @@ cudaError_t upload_hex_constants(int N, const float* hc, int count) {
   return cudaMemcpyToSymbol(c_hexw, hc, count * sizeof(float), N * 64 * sizeof(float));
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 template <int N>
 struct HexW {
   static constexpr int n1 = N + 1, NP = n1 * n1 * n1, NQ = n1 * n1;
@@ -380,6 +384,29 @@ __global__ void __launch_bounds__(128, DG_HEXW_MINB) hexw_kernel(Args A) {
       s_nb[w][su][x] = A.nbr[gs];
       s_code[w][su][x] = A.code[gs];
       s_tau[w][su][x] = A.tau[gs];
+    }
+  }
+  // L2 prefetch of what this element reads late: the residual (or the two history slots)
+  // and its face inboxes; one 128-byte line per lane
+  if (act && MODE != MODE_TRACE) {
+    constexpr int LPF = (NP * 4 + 127) / 128 + 1;         // lines per field array of one element
+    const int64_t b4 = base * 4;
+    for (int x = col; x < 4 * LPF; x += NQ) {
+      const int f = x / LPF, l = x % LPF;
+      const int64_t line = (b4 & ~127LL) + 128LL * l;
+      if (line >= b4 + NP * 4) continue;                 // only lines holding this element's values
+      const int64_t off = f * A.ndof * 4 + (line < b4 ? b4 : line);
+      if (MODE == MODE_STAGE) prefetch_l2(reinterpret_cast<const char*>(A.res) + off);
+      if (MODE == MODE_MRC || MODE == MODE_MRF) {
+        prefetch_l2(reinterpret_cast<const char*>(A.h1) + off);
+        prefetch_l2(reinterpret_cast<const char*>(A.h2) + off);
+      }
+    }
+    if (col < 12) {   // inboxes of the six faces, both planes (NQ floats each, <= 2 lines)
+      const int64_t gs0 = (A.side_off + e * 6) * NQ * 4;
+      const int64_t o = gs0 + (col % 6) * NQ * 4 + (col >= 6 ? A.plane * 4 : 0);
+      prefetch_l2(reinterpret_cast<const char*>(A.tin) + o);
+      prefetch_l2(reinterpret_cast<const char*>(A.tin) + o + NQ * 4 - 4);
     }
   }
   __syncthreads();
@@ -519,7 +546,7 @@ __global__ void __launch_bounds__(128, DG_HEXW_MINB) hexw_kernel(Args A) {
         for (int k = 0; k < n1; ++k)
 #pragma unroll
           for (int f = 0; f < 4; ++f) A.rhs[f * A.ndof + base + col + NQ * k] = rhs[f][k];
-      } else {
+      } else if (MODE == MODE_STAGE) {
 #ifndef DG_HEXW_RES_EARLY
 #pragma unroll
         for (int k = 0; k < n1; ++k)
@@ -536,19 +563,35 @@ __global__ void __launch_bounds__(128, DG_HEXW_MINB) hexw_kernel(Args A) {
             A.res[id] = rr;
             A.qout[id] = q[f][k];
           }
-      }
-    }
-    if (MODE == MODE_STAGE) {
-      __syncwarp();
-      if (act) {
+      } else {   // MRC / MRF: AB3 update; MRC keeps the new state in res[] and the prediction in q[]
 #pragma unroll
-        for (int k = 0; k < n1; ++k) s_q[w][su][col + NQ * k] = make_float4(q[0][k], q[1][k], q[2][k], q[3][k]);
+        for (int k = 0; k < n1; ++k)
+#pragma unroll
+          for (int f = 0; f < 4; ++f) {
+            const int64_t id = f * A.ndof + base + col + NQ * k;
+            const float r0 = rhs[f][k], r1 = A.h1[id], r2 = A.h2[id];
+            A.hw[id] = r0;
+            const float qn = q[f][k] + A.ab0 * r0 + A.ab1 * r1 + A.ab2 * r2;
+            A.qout[id] = qn;
+            if (MODE == MODE_MRC) {
+              res[f][k] = qn;
+              q[f][k] += A.pr0 * r0 + A.pr1 * r1 + A.pr2 * r2;
+            } else {
+              q[f][k] = qn;
+            }
+          }
       }
-      __syncwarp();
     }
   }
-  if ((MODE == MODE_TRACE || MODE == MODE_STAGE) && act) {
-    // ---- traces of the (updated) state into the neighbours' inboxes
+  // ---- traces of the state in q[] / s_q into the neighbours' inboxes
+  auto emit = [&](float* tout) {
+    __syncwarp();
+    if (act) {
+#pragma unroll
+      for (int k = 0; k < n1; ++k) s_q[w][su][col + NQ * k] = make_float4(q[0][k], q[1][k], q[2][k], q[3][k]);
+    }
+    __syncwarp();
+    if (!act) return;
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
       float4 tm = make_float4(0.f, 0.f, 0.f, 0.f), tp = tm;
@@ -567,7 +610,7 @@ __global__ void __launch_bounds__(128, DG_HEXW_MINB) hexw_kernel(Args A) {
         const int nb = s_nb[w][su][f];
         if (nb < 0) continue;
         float nv[3];
-        if (MODE == MODE_STAGE) {
+        if (MODE != MODE_TRACE) {
           const float4 nn = s_N[w][su][f][col];
           nv[0] = nn.x; nv[1] = nn.y; nv[2] = nn.z;
         } else {
@@ -576,10 +619,20 @@ __global__ void __launch_bounds__(128, DG_HEXW_MINB) hexw_kernel(Args A) {
         }
         const float4 tr = sd ? tp : tm;
         const int cidx = s_perm[s_code[w][su][f] * NQ + col];
-        A.tout[(int64_t)nb * NQ + cidx] = tr.x;
-        A.tout[A.plane + (int64_t)nb * NQ + cidx] = nv[0] * tr.y + nv[1] * tr.z + nv[2] * tr.w;
+        tout[(int64_t)nb * NQ + cidx] = tr.x;
+        tout[A.plane + (int64_t)nb * NQ + cidx] = nv[0] * tr.y + nv[1] * tr.z + nv[2] * tr.w;
       }
     }
+  };
+  if (MODE != MODE_RHS) emit(A.tout);
+  if (MODE == MODE_MRC) {
+    if (act) {
+#pragma unroll
+      for (int k = 0; k < n1; ++k)
+#pragma unroll
+        for (int f = 0; f < 4; ++f) q[f][k] = res[f][k];
+    }
+    emit(A.tout2);
   }
 }
 
@@ -951,6 +1004,7 @@ static int ev_take(dg_mesh* m) {
 template <int MODE>
 static void launch_type(dg_mesh* m, const Args& A, int t) {
   if (A.K == 0) return;
+  if (MODE >= MODE_MRC && m->N > 4) return;   // fused multi-rate kernels exist for N <= 4 only
   cudaStream_t s = m->stream;
   int e0 = -1;
   if (m->profiling) {
@@ -960,11 +1014,11 @@ static void launch_type(dg_mesh* m, const Args& A, int t) {
   switch (m->N) {
 #define DG_CASE(NN)                                                   \
   case NN:                                                            \
-    if (t == DG_HEX) { if (NN <= 4) launch_hexw_n<(NN <= 4 ? NN : 4), MODE>(A, s); else launch_hex_n<NN, MODE>(A, s); } \
+    if (t == DG_HEX) { if (NN <= 4) launch_hexw_n<(NN <= 4 ? NN : 4), MODE>(A, s); else launch_hex_n<NN, (MODE > 2 ? 1 : MODE)>(A, s); } \
     else if (launch_gen2<MODE>(t, NN, A, s)) {}                       \
-    else if (t == DG_WEDGE) launch_gen_n<DG_WEDGE, NN, MODE>(A, s);   \
-    else if (t == DG_PYR) launch_gen_n<DG_PYR, NN, MODE>(A, s);       \
-    else launch_gen_n<DG_TET, NN, MODE>(A, s);                        \
+    else if (t == DG_WEDGE) launch_gen_n<DG_WEDGE, NN, (MODE > 2 ? 1 : MODE)>(A, s);   \
+    else if (t == DG_PYR) launch_gen_n<DG_PYR, NN, (MODE > 2 ? 1 : MODE)>(A, s);       \
+    else launch_gen_n<DG_TET, NN, (MODE > 2 ? 1 : MODE)>(A, s);                        \
     break;
     DG_CASE(1) DG_CASE(2) DG_CASE(3) DG_CASE(4) DG_CASE(5) DG_CASE(6)
 #undef DG_CASE
@@ -1020,6 +1074,28 @@ cudaError_t launch_ab(dg_mesh* m, const Sel& sel, const float* qin, float* qout,
     ab_update_kernel<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(
         sel.list[t], (int)sel.count[t], m->td[t].Np, m->td[t].dof_off, m->ndof, qin, qout, r0, r1, r2, h0, h1, h2);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mr(dg_mesh* m, bool coarse, const Sel& sel, float* q, const float* tin, float* tout,
+                      float* tout2, float* hw, const float* h1, const float* h2, const float c[3],
+                      const float p[3]) {
+  Args A[4];
+  for (int t = 0; t < 4; ++t) {
+    A[t] = make_args(m, t);
+    A[t].q = q;
+    A[t].qout = q;
+    A[t].tin = tin;
+    A[t].tout = tout;
+    A[t].tout2 = tout2;
+    A[t].hw = hw;
+    A[t].h1 = h1;
+    A[t].h2 = h2;
+    A[t].ab0 = c[0]; A[t].ab1 = c[1]; A[t].ab2 = c[2];
+    A[t].pr0 = p[0]; A[t].pr1 = p[1]; A[t].pr2 = p[2];
+  }
+  if (coarse) launch_all<MODE_MRC>(m, A, &sel);
+  else launch_all<MODE_MRF>(m, A, &sel);
   return cudaGetLastError();
 }
 

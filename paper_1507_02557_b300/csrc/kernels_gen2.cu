@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
       return tr;
     };
 
-    float4 acc[R];
+    float4 acc[R], pred[R];
     if (MODE != MODE_TRACE) {
       // ---------------------------------------------------------------- volume
       if (T == DG_TET) {
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
           A.rhs[2 * A.ndof + base + n] = acc[r].z;
           A.rhs[3 * A.ndof + base + n] = acc[r].w;
         }
-      } else {
+      } else if (MODE == MODE_STAGE) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const int n = lane + 32 * r;
@@ -386,9 +386,38 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
           if (n < NP) q4[n] = acc[r];
         }
         __syncwarp();
+      } else {   // MRC / MRF: AB3 update; q4 <- prediction (MRC) or new state (MRF), acc <- new state
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int n = lane + 32 * r;
+          if (n >= NP) break;
+          const float rv[4] = {acc[r].x, acc[r].y, acc[r].z, acc[r].w};
+          const float4 qo = q4[n];
+          const float qv[4] = {qo.x, qo.y, qo.z, qo.w};
+          float qn[4], qp[4];
+#pragma unroll
+          for (int fl = 0; fl < 4; ++fl) {
+            const int64_t id = fl * A.ndof + base + n;
+            const float r0 = rv[fl], r1 = A.h1[id], r2 = A.h2[id];
+            A.hw[id] = r0;
+            qn[fl] = qv[fl] + A.ab0 * r0 + A.ab1 * r1 + A.ab2 * r2;
+            qp[fl] = qv[fl] + A.pr0 * r0 + A.pr1 * r1 + A.pr2 * r2;
+            A.qout[id] = qn[fl];
+          }
+          acc[r] = f4(qn[0], qn[1], qn[2], qn[3]);
+          pred[r] = f4(qp[0], qp[1], qp[2], qp[3]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int n = lane + 32 * r;
+          if (n < NP) q4[n] = MODE == MODE_MRC ? pred[r] : acc[r];
+        }
+        __syncwarp();
       }
     }
-    if (MODE == MODE_TRACE || MODE == MODE_STAGE) {
+    // traces of the state in q4 into the neighbours' inboxes
+    auto emit = [&](float* tout) {
       lattice_values();
       __syncwarp();
       for (int fq = lane; fq < NF * NQ; fq += 32) {
@@ -399,9 +428,20 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
         const float4 tr = trace_at(f, idx);
         const int ci = tri_of<T>(f) >= 0 ? idx : qperm[code[f] * NQ + idx];
         const float4 sg = A.sgeo2[(e * NF + f) * NQ + idx];
-        A.tout[(int64_t)nb * NQ + ci] = tr.x;
-        A.tout[A.plane + (int64_t)nb * NQ + ci] = sg.x * tr.y + sg.y * tr.z + sg.z * tr.w;
+        tout[(int64_t)nb * NQ + ci] = tr.x;
+        tout[A.plane + (int64_t)nb * NQ + ci] = sg.x * tr.y + sg.y * tr.z + sg.z * tr.w;
       }
+      __syncwarp();
+    };
+    if (MODE != MODE_RHS) emit(A.tout);
+    if (MODE == MODE_MRC) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int n = lane + 32 * r;
+        if (n < NP) q4[n] = acc[r];
+      }
+      __syncwarp();
+      emit(A.tout2);
     }
     __syncwarp();
   }
@@ -449,5 +489,7 @@ bool launch_gen2(int t, int N, const Args& A, cudaStream_t s) {
 template bool launch_gen2<MODE_TRACE>(int, int, const Args&, cudaStream_t);
 template bool launch_gen2<MODE_RHS>(int, int, const Args&, cudaStream_t);
 template bool launch_gen2<MODE_STAGE>(int, int, const Args&, cudaStream_t);
+template bool launch_gen2<MODE_MRC>(int, int, const Args&, cudaStream_t);
+template bool launch_gen2<MODE_MRF>(int, int, const Args&, cudaStream_t);
 
 }  // namespace dgk

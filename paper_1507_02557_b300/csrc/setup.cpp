@@ -1101,6 +1101,7 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
         }
       }
       m->hist = alloc_zero<float>(3 * 4 * (size_t)m->ndof, owned);
+      m->trace3 = alloc_zero<float>(2 * (size_t)side * nq, owned);
     } else {
       m->level_count[0] = m->td[0].K + m->td[1].K + m->td[2].K + m->td[3].K;
     }
