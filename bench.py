@@ -143,6 +143,9 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+HEX_MRC_DRAM_BYTES_PER_ELEMENT = 969425408 / 73728   # 550,659,072 read + 418,766,336 written
+
+
 def hex_alg_bytes(N):
     """Algorithmic bytes of one hex element per launch of each kernel mode.
 
@@ -262,7 +265,10 @@ def main():
     # step of the coarse hexes and two fused substeps of the fine hexes
     hex_bytes = K_hex * hb["trace"] + args.steps * ((K_hex - fine[0]) * hb["mrc"] + 2 * fine[0] * hb["mrf"])
     achieved = hex_bytes / (kms[0] / 1e3) / 1e9
-    traffic = None
+    # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the TMA-staged
+    # hexw_kernel<4,MRC>, measured with ncu on the 32x32x80-cell mesh (73,728 hexahedra) and
+    # scaled by the elements of one full-size launch
+    traffic = HEX_MRC_DRAM_BYTES_PER_ELEMENT * (K_hex - fine[0])
     # end to end through the public API with host buffers: one simulation call = H2D of the
     # state from pinned host memory, K coarse steps (the first call after dg_set_state also runs
     # the LSRK start-up of the history: 4 LSRK steps + 3 rhs, counted as performed stages),

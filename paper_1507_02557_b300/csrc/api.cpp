@@ -22,6 +22,20 @@ dg_status cuda_fail(cudaError_t e) {
   g_err = cudaGetErrorString(e);
   return DG_ECUDA;
 }
+
+// The device error word after a synchronization: bit 0 = a bounded device wait timed out
+// (the word is cleared once reported).
+dg_status device_flags(const dg_mesh* m) {
+  int v = 0;
+  if (!m->derr) return DG_OK;
+  cudaError_t e = cudaMemcpyAsync(&v, m->derr, sizeof(int), cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (v == 0) return DG_OK;
+  cudaMemsetAsync(m->derr, 0, sizeof(int), m->stream);
+  g_err = "a bounded device wait timed out";
+  return DG_ETIMEOUT;
+}
 }  // namespace
 
 void dg_set_last_error(const std::string& msg) { g_err = msg; }
@@ -153,6 +167,7 @@ dg_status dg_get_state(const dg_mesh* m, float* q, int on_device) {
   if (!on_device) {
     e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return cuda_fail(e);
+    return device_flags(m);
   }
   return DG_OK;
 }
@@ -334,6 +349,8 @@ dg_status dg_energy(dg_mesh* m, const float* q, double* E) {
   if (e != cudaSuccess) return cuda_fail(e);
   e = cudaStreamSynchronize(m->stream);
   if (e != cudaSuccess) return cuda_fail(e);
+  const dg_status st = device_flags(m);
+  if (st != DG_OK) return st;
   if (!std::isfinite(*E)) return DG_ENONFINITE;
   return DG_OK;
 }

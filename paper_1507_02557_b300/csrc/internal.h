@@ -1,5 +1,6 @@
 // Internal state of a dg_mesh and the kernel launch interface.
 #pragma once
+#include <cuda.h>   // CUtensorMap (TMA descriptors)
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -33,6 +34,16 @@ struct TypeDev {
   int* iops2 = nullptr;       // integer tables (face-node gathers, lattice permutations)
   int nops2 = 0, niops2 = 0;  // sizes (elements)
 };
+
+// 1D TMA descriptor of a flat float array of n values, copied in boxes of `box` floats.
+struct TmaArr {
+  CUtensorMap map;
+  const float* base = nullptr;
+  int64_t n = 0;
+  int box = 0;
+  bool ok = false;
+};
+bool tma_map_1d(TmaArr& t, const float* base, int64_t n, int box);   // kernels.cu
 
 // A selection of elements per type (multi-rate level): list = NULL means 0..count-1.
 struct Sel {
@@ -72,6 +83,8 @@ struct dg_mesh {
   float* trace3 = nullptr;        // third trace buffer of the fused multi-rate schedule
   int cslot[3] = {0, 1, 2}, fslot[3] = {2, 0, 1};   // slots of r^n, r^{n-1}, r^{n-2} per level
   bool mr_started = false;
+  int* derr = nullptr;            // device error word: bit 0 = a bounded device wait timed out
+  dgk::TmaArr tma[5];             // q, res, hist, trace, trace3 (hex TMA staging)
   // per-type kernel timing (dg_profile): event pairs recorded around each launch
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;

@@ -320,20 +320,139 @@ __device__ __forceinline__ void hexw_face_geom(const float* g, const float* rr, 
   nv[2] *= inv;
 }
 
-#ifndef DG_HEXW_MINB
-#define DG_HEXW_MINB 4
+// ---------------------------------------------------------------------------- pipelined hex kernel
+// Persistent warp-per-element kernel for N <= 4.  Lane (i,j) owns the node column (i,j,:).
+// While a warp computes element g, the copies of the next element's operands into shared
+// memory are in flight:
+//   main(g')  node values and side data (geometry coefficients, neighbours, codes, tau, c^2);
+//             double-buffered, issued at the start of element g
+//   in(g')    the two inbox planes (p, u.n) of its six faces; issued after g's flux phase
+//   aux(g')   the residual (LSRK stage) or the two history slots (multi-rate); issued after
+//             g's update
+// so every global read of the element loop is a shared-memory read of data requested one
+// element earlier.  Writes (state, residual / history, traces) go straight to global memory.
+// Two copy engines:
+//   TMA = false  4-byte cp.async by every lane (any N <= 4, any buffers)
+//   TMA = true   N = 4, EPW = 1: one lane issues 1D bulk tensor copies (cp.async.bulk.tensor)
+//                of whole field slices into planar staging buffers, completing on per-warp
+//                mbarriers; the start coordinate of each slice is rounded down to 16 bytes
+//                and the slice read from the remainder (boxes of 128 / 160 floats cover the
+//                125-node field slice / the 150-point inbox plane plus that remainder; reads
+//                past the end of an array are zero-filled by the copy engine).
+//                Side data still uses cp.async.
+// Waits on mbarriers are bounded (~1 s of SM clock); on a timeout the warp sets bit 0 of the
+// device error word, waits (bounded) for its own copies in flight and leaves the loop.
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(sdst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory");
+}
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_1d(void* dst, const CUtensorMap* map, int x, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.1d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2}], [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(smem_u32(bar))
+      : "memory");
+}
+// Wait for the completion of phase `parity` of an mbarrier; false after ~2^31 SM clocks.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const unsigned a = smem_u32(bar);
+  const long long t0 = clock64();
+  while (true) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1LL << 31)) return false;
+  }
+}
+
+// 3 resident blocks of 4 warps per SM: the register budget that needs no spills
+#ifndef DG_HEXP_MINB
+#define DG_HEXP_MINB 3
 #endif
-template <int N, int MODE>
-__global__ void __launch_bounds__(128, DG_HEXW_MINB) hexw_kernel(Args A) {
-  using H = HexW<N>;
-  constexpr int n1 = H::n1, NP = H::NP, NQ = H::NQ, EPW = H::EPW, WPB = H::WPB;
-  __shared__ float4 s_q[WPB][EPW][NP];
-  __shared__ float4 s_F[WPB][EPW][4][NQ];
-  __shared__ float4 s_N[WPB][EPW][6][NQ];
-  __shared__ float s_g[WPB][EPW][24];
-  __shared__ int s_nb[WPB][EPW][6], s_code[WPB][EPW][6];
-  __shared__ float s_tau[WPB][EPW][6];
-  __shared__ int s_perm[8 * NQ];
+template <int N, int MODE, bool TMA>
+struct HexP {
+  static constexpr int n1 = N + 1, NP = n1 * n1 * n1, NQ = n1 * n1;
+  static constexpr int EPW = 32 / NQ, WPB = 4;
+  static constexpr int NAUX = MODE == MODE_STAGE ? 1 : (MODE == MODE_MRC || MODE == MODE_MRF) ? 2 : 0;
+  static constexpr int SD = 44;   // side data words: geometry [24], nbr [6], code [6], tau [6], c2
+  static constexpr int R128(int x) { return (x + 127) / 128 * 128; }
+  // cp.async layout (bytes, per warp): q [2][EPW][NP] float4, aux [EPW][NAUX][NP] float4,
+  // F [EPW][4][NQ] float4, Nrm [EPW][6][NQ] float4, in [EPW][2][6 NQ] float, sd [2][EPW][SD]
+  static constexpr int C_AUX = 2 * EPW * NP * 16;
+  static constexpr int C_F = C_AUX + EPW * NAUX * NP * 16;
+  static constexpr int C_N = C_F + EPW * 4 * NQ * 16;
+  static constexpr int C_IN = C_N + EPW * 6 * NQ * 16;
+  static constexpr int C_SD = C_IN + EPW * 12 * NQ * 4;
+  static constexpr int C_PW = ((C_SD + 2 * EPW * SD * 4 + 15) / 16) * 16;
+  // TMA layout (EPW = 1): planar staging qp [2][4][QB], node-major copy q4 [NP] float4,
+  // aux [NAUX][4][QB], in [2][IB], F, Nrm, sd [2][SD], 4 mbarriers (main[2], in, aux)
+  static constexpr int QB = 128, IB = 160;
+  static constexpr int T_Q4 = 2 * 4 * QB * 4;
+  static constexpr int T_AUX = T_Q4 + R128(NP * 16);
+  static constexpr int T_IN = T_AUX + NAUX * 4 * QB * 4;
+  static constexpr int T_F = T_IN + 2 * IB * 4;
+  static constexpr int T_N = T_F + 4 * NQ * 16;
+  static constexpr int T_SD = T_N + 6 * NQ * 16;
+  static constexpr int T_BAR = ((T_SD + 2 * SD * 4 + 7) / 8) * 8;
+  static constexpr int T_PW = R128(T_BAR + 4 * 8);
+  static constexpr int PW = TMA ? T_PW : C_PW;
+  static constexpr int PERM_B = R128(8 * NQ * 4);
+  static constexpr int SMEM = PERM_B + WPB * PW;
+  static_assert(!TMA || (EPW == 1 && NP + 3 <= QB && 6 * NQ + 3 <= IB && NAUX > 0), "TMA path: N = 4 updates");
+};
+
+// 1D tensor maps of the arrays the TMA path reads, with the float offsets of the kernel's
+// pointers inside them
+struct HexMaps {
+  CUtensorMap q, a0, a1, in;
+  long long qoff, a0off, a1off, inoff;
+};
+
+template <int N, int MODE, bool TMA>
+__global__ void __launch_bounds__(128, DG_HEXP_MINB) hexw_kernel(Args A, const __grid_constant__ HexMaps M) {
+  using H = HexP<N, MODE, TMA>;
+  constexpr int n1 = H::n1, NP = H::NP, NQ = H::NQ, EPW = H::EPW, WPB = H::WPB, SD = H::SD;
+  constexpr int QB = H::QB, IB = H::IB;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  int* s_perm = reinterpret_cast<int*>(smem_raw);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* pw = smem_raw + H::PERM_B + w * H::PW;
+  const int sub = lane / NQ, col = lane % NQ;
+  const int i = col % n1, j = col / n1;
+  const int su = sub < EPW ? sub : 0;
+  // cp.async layout
+  auto SQ = [&](int b) { return reinterpret_cast<float4*>(pw) + (b * EPW + su) * NP; };
+  float4* c_aux = reinterpret_cast<float4*>(pw + H::C_AUX) + su * H::NAUX * NP;
+  float* c_in = reinterpret_cast<float*>(pw + H::C_IN) + su * 12 * NQ;
+  // TMA layout
+  float* t_qp = reinterpret_cast<float*>(pw);
+  float4* t_q4 = reinterpret_cast<float4*>(pw + H::T_Q4);
+  float* t_aux = reinterpret_cast<float*>(pw + H::T_AUX);
+  float* t_in = reinterpret_cast<float*>(pw + H::T_IN);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(pw + H::T_BAR);
+  // both
+  float4* s_F = reinterpret_cast<float4*>(pw + (TMA ? H::T_F : H::C_F)) + su * 4 * NQ;
+  float4* s_N = reinterpret_cast<float4*>(pw + (TMA ? H::T_N : H::C_N)) + su * 6 * NQ;
+  auto SDp = [&](int b) { return reinterpret_cast<float*>(pw + (TMA ? H::T_SD : H::C_SD)) + (b * EPW + su) * SD; };
 
   const float* Dm = c_hexw[N];
   const float* Vm = Dm + n1 * n1;
@@ -341,156 +460,252 @@ __global__ void __launch_bounds__(128, DG_HEXW_MINB) hexw_kernel(Args A) {
   const float* W1 = Vp + n1;
   const float* R1 = W1 + n1;
 
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sub = lane / NQ, col = lane % NQ;
-  const int i = col % n1, j = col / n1;
-  const int64_t li = ((int64_t)blockIdx.x * WPB + w) * EPW + sub;
-  const bool act = sub < EPW && li < A.K;
-  const int64_t e = act ? (A.elist ? (int64_t)A.elist[li] : li) : 0;
-  const int su = sub < EPW ? sub : 0;
-  const int64_t base = A.dof_off + e * NP;
-
   for (int x = threadIdx.x; x < 8 * NQ; x += blockDim.x) s_perm[x] = A.perm[x];
-  float q[4][n1], res[4][n1];
-  if (act) {
+  if (TMA && lane == 0) {
 #pragma unroll
-    for (int k = 0; k < n1; ++k)
-#pragma unroll
-      for (int f = 0; f < 4; ++f) q[f][k] = A.q[f * A.ndof + base + col + NQ * k];
-#ifdef DG_HEXW_RES_EARLY
-    if (MODE == MODE_STAGE) {
-#pragma unroll
-      for (int k = 0; k < n1; ++k)
-#pragma unroll
-        for (int f = 0; f < 4; ++f) res[f][k] = A.res[f * A.ndof + base + col + NQ * k];
-    }
-#endif
-    if (col < 24) s_g[w][su][col] = A.geo[e * 24 + col];
-    if (NQ < 24 && col < NQ) {   // small N: fewer lanes than coefficients
-      for (int x = col + NQ; x < 24; x += NQ) s_g[w][su][x] = A.geo[e * 24 + x];
-    }
-    if (col < 6) {
-      const int64_t gs = A.side_off + e * 6 + col;
-      s_nb[w][su][col] = A.nbr[gs];
-      s_code[w][su][col] = A.code[gs];
-      s_tau[w][su][col] = A.tau[gs];
-    }
-#pragma unroll
-    for (int k = 0; k < n1; ++k) s_q[w][su][col + NQ * k] = make_float4(q[0][k], q[1][k], q[2][k], q[3][k]);
-  }
-  if (NQ < 6 && act) {   // N = 1: 4 lanes per element, 6 faces
-    for (int x = col + NQ; x < 6; x += NQ) {
-      const int64_t gs = A.side_off + e * 6 + x;
-      s_nb[w][su][x] = A.nbr[gs];
-      s_code[w][su][x] = A.code[gs];
-      s_tau[w][su][x] = A.tau[gs];
-    }
-  }
-  // L2 prefetch of what this element reads late: the residual (or the two history slots)
-  // and its face inboxes; one 128-byte line per lane
-  if (act && MODE != MODE_TRACE) {
-    constexpr int LPF = (NP * 4 + 127) / 128 + 1;         // lines per field array of one element
-    const int64_t b4 = base * 4;
-    for (int x = col; x < 4 * LPF; x += NQ) {
-      const int f = x / LPF, l = x % LPF;
-      const int64_t line = (b4 & ~127LL) + 128LL * l;
-      if (line >= b4 + NP * 4) continue;                 // only lines holding this element's values
-      const int64_t off = f * A.ndof * 4 + (line < b4 ? b4 : line);
-      if (MODE == MODE_STAGE) prefetch_l2(reinterpret_cast<const char*>(A.res) + off);
-      if (MODE == MODE_MRC || MODE == MODE_MRF) {
-        prefetch_l2(reinterpret_cast<const char*>(A.h1) + off);
-        prefetch_l2(reinterpret_cast<const char*>(A.h2) + off);
-      }
-    }
-    if (col < 12) {   // inboxes of the six faces, both planes (NQ floats each, <= 2 lines)
-      const int64_t gs0 = (A.side_off + e * 6) * NQ * 4;
-      const int64_t o = gs0 + (col % 6) * NQ * 4 + (col >= 6 ? A.plane * 4 : 0);
-      prefetch_l2(reinterpret_cast<const char*>(A.tin) + o);
-      prefetch_l2(reinterpret_cast<const char*>(A.tin) + o + NQ * 4 - 4);
-    }
+    for (int k = 0; k < 4; ++k) mbar_init(bar + k, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
-  const float* g = s_g[w][su];
-  const float c2 = act ? A.c2[e] : 0.f;
-  float rhs[4][n1];
-  float Jn[n1];
 
-  if (MODE != MODE_TRACE && act) {
-    // ---- volume: collocated strong form (Alg. hex_vol), metrics built along the column
-    float Dri[n1], Dsj[n1];
+  // element of this lane in group g (or -1)
+  auto elem = [&](int g) -> int {
+    const int li = (g * WPB + w) * EPW + sub;
+    if (sub >= EPW || li >= A.K) return -1;
+    return A.elist ? A.elist[li] : li;
+  };
+  unsigned pend = 0;    // TMA: barriers with copies in flight (bit k = bar[k])
+  unsigned phase = 0;   // TMA: parity of the next completion of each barrier
+  // start coordinate of a TMA slice, rounded down to 16 bytes
+  auto x16 = [](long long x) { return (int)(x & ~3LL); };
+  auto stage_main = [&](int b, int e) {
+    if (e >= 0) {
+      if (TMA) {
+        if (lane == 0) {
+          const long long x = M.qoff + A.dof_off + (long long)e * NP;
+          mbar_expect_tx(bar + b, 4 * QB * 4);
 #pragma unroll
-    for (int m = 0; m < n1; ++m) {
-      Dri[m] = Dm[i * n1 + m];
-      Dsj[m] = Dm[j * n1 + m];
+          for (int f = 0; f < 4; ++f) tma_load_1d(t_qp + (b * 4 + f) * QB, &M.q, x16(x + f * A.ndof), bar + b);
+        }
+      } else {
+        const float* qs = A.q + A.dof_off + (int64_t)e * NP + col;
+        float* dq = reinterpret_cast<float*>(SQ(b)) + 4 * col;
+#pragma unroll
+        for (int k = 0; k < n1; ++k)
+#pragma unroll
+          for (int f = 0; f < 4; ++f) cp_async4(dq + 4 * NQ * k + f, qs + f * A.ndof + NQ * k);
+      }
+      const int64_t gs0 = A.side_off + (int64_t)e * 6;
+      float* ds = SDp(b);
+      for (int x = col; x < SD - 1; x += NQ) {
+        const void* src = x < 24   ? static_cast<const void*>(A.geo + (int64_t)e * 24 + x)
+                          : x < 30 ? static_cast<const void*>(A.nbr + gs0 + (x - 24))
+                          : x < 36 ? static_cast<const void*>(A.code + gs0 + (x - 30))
+                          : x < 42 ? static_cast<const void*>(A.tau + gs0 + (x - 36))
+                                   : static_cast<const void*>(A.c2 + e);
+        cp_async4(ds + x, src);
+      }
+      if (TMA) pend |= 1u << b;
     }
-    const float r = R1[i], s = R1[j];
-    float Ar[3], Br[3], As[3], Bs[3], xt[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      Ar[d] = g[d] + g[9 + d] * s;
-      Br[d] = g[12 + d] + g[18 + d] * s;
-      As[d] = g[3 + d] + g[9 + d] * r;
-      Bs[d] = g[15 + d] + g[18 + d] * r;
-      xt[d] = g[6 + d] + g[12 + d] * r + g[15 + d] * s + g[18 + d] * r * s;
+    cp_async_commit();
+  };
+  auto stage_in = [&](int e) {
+    if (MODE != MODE_TRACE && e >= 0) {
+      const long long x = (A.side_off + (long long)e * 6) * NQ;
+      if (TMA) {
+        if (lane == 0) {
+          mbar_expect_tx(bar + 2, 2 * IB * 4);
+          tma_load_1d(t_in, &M.in, x16(M.inoff + x), bar + 2);
+          tma_load_1d(t_in + IB, &M.in, x16(M.inoff + A.plane + x), bar + 2);
+        }
+        pend |= 4u;
+      } else {
+        const float* src = A.tin + x;
+        for (int y = col; y < 12 * NQ; y += NQ) cp_async4(c_in + y, src + (y >= 6 * NQ ? A.plane - 6 * NQ : 0) + y);
+      }
     }
-    float G0a[3], G0b[3], G1a[3], G1b[3], G2a[3], G2b[3], G2c[3], tmp[3];
-    cross3(As, xt, G0a);
-    cross3(Bs, xt, G0b);
-    cross3(xt, Ar, G1a);
-    cross3(xt, Br, G1b);
-    cross3(Ar, As, G2a);
-    cross3(Ar, Bs, G2b);
-    cross3(Br, As, tmp);
-    G2b[0] += tmp[0]; G2b[1] += tmp[1]; G2b[2] += tmp[2];
-    cross3(Br, Bs, G2c);
+    cp_async_commit();
+  };
+  auto stage_aux = [&](int e) {
+    if (H::NAUX > 0 && e >= 0) {
+      if (TMA) {
+        if (lane == 0) {
+          const long long x = A.dof_off + (long long)e * NP;
+          mbar_expect_tx(bar + 3, H::NAUX * 4 * QB * 4);
 #pragma unroll
-    for (int k = 0; k < n1; ++k) {
-      const float t = R1[k];
-      float g0[3], g1[3], g2[3];
+          for (int f = 0; f < 4; ++f) {
+            tma_load_1d(t_aux + f * QB, &M.a0, x16(M.a0off + x + f * A.ndof), bar + 3);
+            if (H::NAUX > 1) tma_load_1d(t_aux + (4 + f) * QB, &M.a1, x16(M.a1off + x + f * A.ndof), bar + 3);
+          }
+        }
+        pend |= 8u;
+      } else {
+        const float* s0 = (MODE == MODE_STAGE ? A.res : A.h1) + A.dof_off + (int64_t)e * NP + col;
+        const float* s1 = A.h2 + A.dof_off + (int64_t)e * NP + col;
+        float* d = reinterpret_cast<float*>(c_aux) + 4 * col;
+#pragma unroll
+        for (int k = 0; k < n1; ++k)
+#pragma unroll
+          for (int f = 0; f < 4; ++f) {
+            cp_async4(d + 4 * NQ * k + f, s0 + f * A.ndof + NQ * k);
+            if (H::NAUX > 1) cp_async4(d + 4 * NP + 4 * NQ * k + f, s1 + f * A.ndof + NQ * k);
+          }
+      }
+    }
+    cp_async_commit();
+  };
+  // TMA: wait for barrier k (warp-uniform); false on a timeout
+  auto wait_bar = [&](int k) -> bool {
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(bar + k, (phase >> k) & 1u));
+    if (ok) {
+      phase ^= 1u << k;
+      pend &= ~(1u << k);
+    }
+    return ok;
+  };
+
+  int g = blockIdx.x;
+  const int gstride = gridDim.x;
+  // TMA (EPW = 1): the warp's element is lane 0's
+  auto welem = [&](int e) { return TMA ? __shfl_sync(0xffffffffu, e, 0) : e; };
+  int e_c = elem(g), e_n = elem(g + gstride);
+  stage_main(0, welem(e_c));
+  stage_in(welem(e_c));
+  stage_aux(welem(e_c));
+  int b = 0;
+  bool bail = false;
+  for (; (g * WPB + w) * EPW < A.K; g += gstride, b ^= 1) {
+    const int e_nn = elem(g + 2 * gstride);   // consumed one element later
+    stage_main(b ^ 1, welem(e_n));
+    cp_async_wait<2>();                       // main(g) and in(g) have landed
+    if (TMA && !(wait_bar(b) && wait_bar(2))) {
+      bail = true;
+      break;
+    }
+    __syncwarp();
+    const bool act = e_c >= 0;
+    const int64_t e = act ? e_c : 0;
+    const int64_t base = A.dof_off + e * NP;
+    const float* g_ = SDp(b);
+    const int* s_nb = reinterpret_cast<const int*>(g_ + 24);
+    const int* s_code = reinterpret_cast<const int*>(g_ + 30);
+    const float* s_tau = g_ + 36;
+    const float c2 = act ? g_[42] : 0.f;
+    float4* s_q = TMA ? t_q4 : SQ(b);
+    float q[4][n1];
+    if (TMA) {   // planar slices -> registers and the node-major copy
+      int o[4];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) o[f] = (int)((M.qoff + base + f * A.ndof) & 3) + (b * 4 + f) * QB;
+      if (act) {
+#pragma unroll
+        for (int k = 0; k < n1; ++k) {
+#pragma unroll
+          for (int f = 0; f < 4; ++f) q[f][k] = t_qp[o[f] + col + NQ * k];
+          s_q[col + NQ * k] = make_float4(q[0][k], q[1][k], q[2][k], q[3][k]);
+        }
+      }
+      __syncwarp();
+    } else {
+#pragma unroll
+      for (int k = 0; k < n1; ++k) {
+        const float4 v = s_q[col + NQ * k];
+        q[0][k] = v.x;
+        q[1][k] = v.y;
+        q[2][k] = v.z;
+        q[3][k] = v.w;
+      }
+    }
+    float rhs[4][n1];
+    float Jn[n1];
+
+    if (MODE != MODE_TRACE && act) {
+      // ---- volume: collocated strong form (Alg. hex_vol), metrics built along the column
+      float Dri[n1], Dsj[n1];
+#pragma unroll
+      for (int m = 0; m < n1; ++m) {
+        Dri[m] = Dm[i * n1 + m];
+        Dsj[m] = Dm[j * n1 + m];
+      }
+      const float r = R1[i], s = R1[j];
+      float Ar[3], Br[3], As[3], Bs[3], xt[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        g0[d] = G0a[d] + t * G0b[d];
-        g1[d] = G1a[d] + t * G1b[d];
-        g2[d] = G2a[d] + t * (G2b[d] + t * G2c[d]);
+        Ar[d] = g_[d] + g_[9 + d] * s;
+        Br[d] = g_[12 + d] + g_[18 + d] * s;
+        As[d] = g_[3 + d] + g_[9 + d] * r;
+        Bs[d] = g_[15 + d] + g_[18 + d] * r;
+        xt[d] = g_[6 + d] + g_[12 + d] * r + g_[15 + d] * s + g_[18 + d] * r * s;
       }
-      const float J = (Ar[0] + t * Br[0]) * g0[0] + (Ar[1] + t * Br[1]) * g0[1] + (Ar[2] + t * Br[2]) * g0[2];
-      Jn[k] = J;
-      const float iJ = 1.f / J;
-      float4 dr = make_float4(0.f, 0.f, 0.f, 0.f), ds = dr;
+      float G0a[3], G0b[3], G1a[3], G1b[3], G2a[3], G2b[3], G2c[3], tmp[3];
+      cross3(As, xt, G0a);
+      cross3(Bs, xt, G0b);
+      cross3(xt, Ar, G1a);
+      cross3(xt, Br, G1b);
+      cross3(Ar, As, G2a);
+      cross3(Ar, Bs, G2b);
+      cross3(Br, As, tmp);
+      G2b[0] += tmp[0];
+      G2b[1] += tmp[1];
+      G2b[2] += tmp[2];
+      cross3(Br, Bs, G2c);
 #pragma unroll
-      for (int m = 0; m < n1; ++m) {
-        dr = f4fma(Dri[m], s_q[w][su][m + n1 * j + NQ * k], dr);
-        ds = f4fma(Dsj[m], s_q[w][su][i + n1 * m + NQ * k], ds);
+      for (int k = 0; k < n1; ++k) {
+        const float t = R1[k];
+        float g0[3], g1[3], g2[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          g0[d] = G0a[d] + t * G0b[d];
+          g1[d] = G1a[d] + t * G1b[d];
+          g2[d] = G2a[d] + t * (G2b[d] + t * G2c[d]);
+        }
+        const float J = (Ar[0] + t * Br[0]) * g0[0] + (Ar[1] + t * Br[1]) * g0[1] + (Ar[2] + t * Br[2]) * g0[2];
+        Jn[k] = J;
+        const float iJ = 1.f / J;
+        float4 dr = make_float4(0.f, 0.f, 0.f, 0.f), ds = dr;
+#pragma unroll
+        for (int m = 0; m < n1; ++m) {
+          dr = f4fma(Dri[m], s_q[m + n1 * j + NQ * k], dr);
+          ds = f4fma(Dsj[m], s_q[i + n1 * m + NQ * k], ds);
+        }
+        float dt[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int m = 0; m < n1; ++m) {
+          const float dk = Dm[k * n1 + m];
+#pragma unroll
+          for (int f = 0; f < 4; ++f) dt[f] = fmaf(dk, q[f][m], dt[f]);
+        }
+        const float drf[4] = {dr.x, dr.y, dr.z, dr.w}, dsf[4] = {ds.x, ds.y, ds.z, ds.w};
+        // -div u and -c^2 grad p
+        float div = 0.f;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) div += g0[d] * drf[1 + d] + g1[d] * dsf[1 + d] + g2[d] * dt[1 + d];
+        rhs[0][k] = -div * iJ;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) rhs[1 + d][k] = -c2 * iJ * (g0[d] * drf[0] + g1[d] * dsf[0] + g2[d] * dt[0]);
       }
-      float dt[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int m = 0; m < n1; ++m) {
-        const float dk = Dm[k * n1 + m];
-#pragma unroll
-        for (int f = 0; f < 4; ++f) dt[f] = fmaf(dk, q[f][m], dt[f]);
-      }
-      const float drf[4] = {dr.x, dr.y, dr.z, dr.w}, dsf[4] = {ds.x, ds.y, ds.z, ds.w};
-      // -div u and -c^2 grad p
-      float div = 0.f;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) div += g0[d] * drf[1 + d] + g1[d] * dsf[1 + d] + g2[d] * dt[1 + d];
-      rhs[0][k] = -div * iJ;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) rhs[1 + d][k] = -c2 * iJ * (g0[d] * drf[0] + g1[d] * dsf[0] + g2[d] * dt[0]);
     }
-  }
-  if (MODE != MODE_TRACE) {
-    // ---- fluxes at this lane's point (a,b) = (i,j) of all six faces
     float4 F45[2];
-    if (act) {
+    if (MODE != MODE_TRACE && act) {
+      // inbox offsets: TMA slices start at the 16-byte boundary below the element's first point
+      int oi0 = 0, oi1 = 6 * NQ;
+      const float* sin_ = c_in;
+      if (TMA) {
+        const long long x = (A.side_off + e * 6) * NQ;
+        oi0 = (int)((M.inoff + x) & 3);
+        oi1 = IB + (int)((M.inoff + A.plane + x) & 3);
+        sin_ = t_in;
+      }
+      // ---- fluxes at this lane's point (a,b) = (i,j) of all six faces
 #pragma unroll
       for (int ax = 0; ax < 3; ++ax) {
         float4 tm = make_float4(0.f, 0.f, 0.f, 0.f), tp = tm;
 #pragma unroll
         for (int m = 0; m < n1; ++m) {
           float4 v;
-          if (ax == 0) v = s_q[w][su][m + n1 * i + NQ * j];
-          else if (ax == 1) v = s_q[w][su][i + n1 * m + NQ * j];
+          if (ax == 0) v = s_q[m + n1 * i + NQ * j];
+          else if (ax == 1) v = s_q[i + n1 * m + NQ * j];
           else v = make_float4(q[0][m], q[1][m], q[2][m], q[3][m]);
           tm = f4fma(Vm[m], v, tm);
           tp = f4fma(Vp[m], v, tp);
@@ -500,148 +715,254 @@ __global__ void __launch_bounds__(128, DG_HEXW_MINB) hexw_kernel(Args A) {
           const int f = 2 * ax + sd;
           const float4 tr = sd ? tp : tm;
           float nv[3], Js;
-          hexw_face_geom<N>(g, R1, f, i, j, nv, Js);
-          s_N[w][su][f][col] = make_float4(nv[0], nv[1], nv[2], Js);
+          hexw_face_geom<N>(g_, R1, f, i, j, nv, Js);
+          s_N[f * NQ + col] = make_float4(nv[0], nv[1], nv[2], Js);
           const float unm = nv[0] * tr.y + nv[1] * tr.z + nv[2] * tr.w;
-          const int nb = s_nb[w][su][f];
+          const int nb = s_nb[f];
           float P = 0.f, UN = 0.f;
           if (nb >= 0) {
-            const int64_t gs = A.side_off + e * 6 + f;
-            const int cidx = s_perm[s_code[w][su][f] * NQ + col];
-            P = A.tin[gs * NQ + cidx];
-            UN = A.tin[A.plane + gs * NQ + cidx];
+            const int cidx = s_perm[s_code[f] * NQ + col];
+            P = sin_[oi0 + f * NQ + cidx];
+            UN = sin_[oi1 + f * NQ + cidx];
           }
-          const float ta = s_tau[w][su][f];
+          const float ta = s_tau[f];
           float fp, fu;
           flux(nb < 0, tr.x, unm, P, UN, A.tau_scale * ta, A.tau_scale / ta, false, fp, fu);
           const float wg = W1[i] * W1[j] * Js;
           const float4 Fv = make_float4(wg * fp, wg * fu * nv[0], wg * fu * nv[1], wg * fu * nv[2]);
-          if (ax < 2) s_F[w][su][f][col] = Fv;
+          if (ax < 2) s_F[f * NQ + col] = Fv;
           else F45[sd] = Fv;
         }
       }
     }
     __syncwarp();
-    if (act) {
-      // ---- lift (Alg. hex_surf), M^{-1} = 1/(w w w J), LSRK update
+    stage_in(welem(e_n));   // the inbox buffer is free again
+    if (MODE != MODE_TRACE) {
+      if (act) {
+        // ---- lift (Alg. hex_surf), M^{-1} = 1/(w w w J)
 #pragma unroll
-      for (int k = 0; k < n1; ++k) {
-        const float4 F0 = s_F[w][su][0][j + n1 * k], F1 = s_F[w][su][1][j + n1 * k];
-        const float4 F2 = s_F[w][su][2][i + n1 * k], F3 = s_F[w][su][3][i + n1 * k];
-        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-        sum = f4fma(Vm[i], F0, sum);
-        sum = f4fma(Vp[i], F1, sum);
-        sum = f4fma(Vm[j], F2, sum);
-        sum = f4fma(Vp[j], F3, sum);
-        sum = f4fma(Vm[k], F45[0], sum);
-        sum = f4fma(Vp[k], F45[1], sum);
-        const float iM = 1.f / (W1[i] * W1[j] * W1[k] * Jn[k]);
-        rhs[0][k] += iM * sum.x;
-        rhs[1][k] += c2 * iM * sum.y;
-        rhs[2][k] += c2 * iM * sum.z;
-        rhs[3][k] += c2 * iM * sum.w;
-      }
-      if (MODE == MODE_RHS) {
-#pragma unroll
-        for (int k = 0; k < n1; ++k)
-#pragma unroll
-          for (int f = 0; f < 4; ++f) A.rhs[f * A.ndof + base + col + NQ * k] = rhs[f][k];
-      } else if (MODE == MODE_STAGE) {
-#ifndef DG_HEXW_RES_EARLY
-#pragma unroll
-        for (int k = 0; k < n1; ++k)
-#pragma unroll
-          for (int f = 0; f < 4; ++f) res[f][k] = A.res[f * A.ndof + base + col + NQ * k];
-#endif
-#pragma unroll
-        for (int k = 0; k < n1; ++k)
-#pragma unroll
-          for (int f = 0; f < 4; ++f) {
-            const int64_t id = f * A.ndof + base + col + NQ * k;
-            const float rr = A.a * res[f][k] + A.dt * rhs[f][k];
-            q[f][k] += A.b * rr;
-            A.res[id] = rr;
-            A.qout[id] = q[f][k];
-          }
-      } else {   // MRC / MRF: AB3 update; MRC keeps the new state in res[] and the prediction in q[]
-#pragma unroll
-        for (int k = 0; k < n1; ++k)
-#pragma unroll
-          for (int f = 0; f < 4; ++f) {
-            const int64_t id = f * A.ndof + base + col + NQ * k;
-            const float r0 = rhs[f][k], r1 = A.h1[id], r2 = A.h2[id];
-            A.hw[id] = r0;
-            const float qn = q[f][k] + A.ab0 * r0 + A.ab1 * r1 + A.ab2 * r2;
-            A.qout[id] = qn;
-            if (MODE == MODE_MRC) {
-              res[f][k] = qn;
-              q[f][k] += A.pr0 * r0 + A.pr1 * r1 + A.pr2 * r2;
-            } else {
-              q[f][k] = qn;
-            }
-          }
-      }
-    }
-  }
-  // ---- traces of the state in q[] / s_q into the neighbours' inboxes
-  auto emit = [&](float* tout) {
-    __syncwarp();
-    if (act) {
-#pragma unroll
-      for (int k = 0; k < n1; ++k) s_q[w][su][col + NQ * k] = make_float4(q[0][k], q[1][k], q[2][k], q[3][k]);
-    }
-    __syncwarp();
-    if (!act) return;
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-      float4 tm = make_float4(0.f, 0.f, 0.f, 0.f), tp = tm;
-#pragma unroll
-      for (int m = 0; m < n1; ++m) {
-        float4 v;
-        if (ax == 0) v = s_q[w][su][m + n1 * i + NQ * j];
-        else if (ax == 1) v = s_q[w][su][i + n1 * m + NQ * j];
-        else v = make_float4(q[0][m], q[1][m], q[2][m], q[3][m]);
-        tm = f4fma(Vm[m], v, tm);
-        tp = f4fma(Vp[m], v, tp);
-      }
-#pragma unroll
-      for (int sd = 0; sd < 2; ++sd) {
-        const int f = 2 * ax + sd;
-        const int nb = s_nb[w][su][f];
-        if (nb < 0) continue;
-        float nv[3];
-        if (MODE != MODE_TRACE) {
-          const float4 nn = s_N[w][su][f][col];
-          nv[0] = nn.x; nv[1] = nn.y; nv[2] = nn.z;
-        } else {
-          float Js;
-          hexw_face_geom<N>(g, R1, f, i, j, nv, Js);
+        for (int k = 0; k < n1; ++k) {
+          const float4 F0 = s_F[0 * NQ + j + n1 * k], F1 = s_F[1 * NQ + j + n1 * k];
+          const float4 F2 = s_F[2 * NQ + i + n1 * k], F3 = s_F[3 * NQ + i + n1 * k];
+          float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+          sum = f4fma(Vm[i], F0, sum);
+          sum = f4fma(Vp[i], F1, sum);
+          sum = f4fma(Vm[j], F2, sum);
+          sum = f4fma(Vp[j], F3, sum);
+          sum = f4fma(Vm[k], F45[0], sum);
+          sum = f4fma(Vp[k], F45[1], sum);
+          const float iM = 1.f / (W1[i] * W1[j] * W1[k] * Jn[k]);
+          rhs[0][k] += iM * sum.x;
+          rhs[1][k] += c2 * iM * sum.y;
+          rhs[2][k] += c2 * iM * sum.z;
+          rhs[3][k] += c2 * iM * sum.w;
         }
-        const float4 tr = sd ? tp : tm;
-        const int cidx = s_perm[s_code[w][su][f] * NQ + col];
-        tout[(int64_t)nb * NQ + cidx] = tr.x;
-        tout[A.plane + (int64_t)nb * NQ + cidx] = nv[0] * tr.y + nv[1] * tr.z + nv[2] * tr.w;
+      }
+      cp_async_wait<2>();   // aux(g) has landed
+      if (TMA && H::NAUX > 0 && !wait_bar(3)) {
+        bail = true;
+        break;
+      }
+      __syncwarp();
+      // aux value of field f, node (col, k), slot a
+      int oa[2][4];
+      if (TMA) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          oa[0][f] = (int)((M.a0off + base + f * A.ndof) & 3) + f * QB + col;
+          oa[1][f] = (int)((M.a1off + base + f * A.ndof) & 3) + (4 + f) * QB + col;
+        }
+      }
+      auto auxv = [&](int a, int f, int k) -> float {
+        if (TMA) return t_aux[oa[a][f] + NQ * k];
+        const float* c = reinterpret_cast<const float*>(c_aux + a * NP + col + NQ * k);
+        return c[f];
+      };
+      if (act) {
+        if (MODE == MODE_RHS) {
+#pragma unroll
+          for (int k = 0; k < n1; ++k)
+#pragma unroll
+            for (int f = 0; f < 4; ++f) A.rhs[f * A.ndof + base + col + NQ * k] = rhs[f][k];
+        } else if (MODE == MODE_STAGE) {   // LSRK(5,4) 2N-storage update
+#pragma unroll
+          for (int k = 0; k < n1; ++k)
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+              const int64_t id = f * A.ndof + base + col + NQ * k;
+              const float rr = A.a * auxv(0, f, k) + A.dt * rhs[f][k];
+              q[f][k] += A.b * rr;
+              A.res[id] = rr;
+              A.qout[id] = q[f][k];
+            }
+        } else {   // MRC / MRF: AB3 update; MRC keeps the new state in rhs[] and the prediction in q[]
+#pragma unroll
+          for (int k = 0; k < n1; ++k)
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+              const int64_t id = f * A.ndof + base + col + NQ * k;
+              const float r0 = rhs[f][k], r1 = auxv(0, f, k), r2 = auxv(1, f, k);
+              A.hw[id] = r0;
+              const float qn = q[f][k] + A.ab0 * r0 + A.ab1 * r1 + A.ab2 * r2;
+              A.qout[id] = qn;
+              if (MODE == MODE_MRC) {
+                rhs[f][k] = qn;
+                q[f][k] += A.pr0 * r0 + A.pr1 * r1 + A.pr2 * r2;
+              } else {
+                q[f][k] = qn;
+              }
+            }
+        }
+      }
+      __syncwarp();
+    }
+    stage_aux(welem(e_n));   // the aux buffer is free again
+
+    // ---- traces of the state in q[] into the neighbours' inboxes (MRC: the half-step
+    // prediction into tout, then the new state into tout2)
+    constexpr int NPASS = MODE == MODE_RHS ? 0 : MODE == MODE_MRC ? 2 : 1;
+#pragma unroll 1
+    for (int pass = 0; pass < NPASS; ++pass) {
+      float* tout = pass ? A.tout2 : A.tout;
+      if (act) {
+#pragma unroll
+        for (int k = 0; k < n1; ++k) s_q[col + NQ * k] = make_float4(q[0][k], q[1][k], q[2][k], q[3][k]);
+      }
+      __syncwarp();
+      if (act) {
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+          float4 tm = make_float4(0.f, 0.f, 0.f, 0.f), tp = tm;
+#pragma unroll
+          for (int m = 0; m < n1; ++m) {
+            float4 v;
+            if (ax == 0) v = s_q[m + n1 * i + NQ * j];
+            else if (ax == 1) v = s_q[i + n1 * m + NQ * j];
+            else v = make_float4(q[0][m], q[1][m], q[2][m], q[3][m]);
+            tm = f4fma(Vm[m], v, tm);
+            tp = f4fma(Vp[m], v, tp);
+          }
+#pragma unroll
+          for (int sd = 0; sd < 2; ++sd) {
+            const int f = 2 * ax + sd;
+            const int nb = s_nb[f];
+            if (nb < 0) continue;
+            float nv[3];
+            if (MODE != MODE_TRACE) {
+              const float4 nn = s_N[f * NQ + col];
+              nv[0] = nn.x;
+              nv[1] = nn.y;
+              nv[2] = nn.z;
+            } else {
+              float Js;
+              hexw_face_geom<N>(g_, R1, f, i, j, nv, Js);
+            }
+            const float4 tr = sd ? tp : tm;
+            const int cidx = s_perm[s_code[f] * NQ + col];
+            tout[(int64_t)nb * NQ + cidx] = tr.x;
+            tout[A.plane + (int64_t)nb * NQ + cidx] = nv[0] * tr.y + nv[1] * tr.z + nv[2] * tr.w;
+          }
+        }
+      }
+      __syncwarp();
+      if (MODE == MODE_MRC && act) {
+#pragma unroll
+        for (int k = 0; k < n1; ++k)
+#pragma unroll
+          for (int f = 0; f < 4; ++f) q[f][k] = rhs[f][k];
       }
     }
-  };
-  if (MODE != MODE_RHS) emit(A.tout);
-  if (MODE == MODE_MRC) {
-    if (act) {
-#pragma unroll
-      for (int k = 0; k < n1; ++k)
-#pragma unroll
-        for (int f = 0; f < 4; ++f) q[f][k] = res[f][k];
-    }
-    emit(A.tout2);
+    if (MODE == MODE_RHS) __syncwarp();
+    e_c = e_n;
+    e_n = e_nn;
+  }
+  cp_async_wait<0>();
+  if (TMA && bail) {   // report, then wait (bounded) for this warp's copies still in flight
+    if (lane == 0) atomicOr(A.err, 1);
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k)
+      if (pend & (1u << k)) mbar_wait(bar + k, (phase >> k) & 1u);
   }
 }
 
-template <int N, int MODE>
-static void launch_hexw_n(const Args& A, cudaStream_t s) {
-  using H = HexW<N>;
+template <int N, int MODE, bool TMA>
+static void launch_hexw_n(const Args& A, const HexMaps& M, cudaStream_t s) {
+  using H = HexP<N, MODE, TMA>;
   if (A.K == 0) return;
-  dim3 grid((A.K + H::EPB - 1) / H::EPB);
-  hexw_kernel<N, MODE><<<grid, 32 * H::WPB, 0, s>>>(A);
+  static int blocks = 0;   // persistent grid: resident blocks per SM x SMs (computed once)
+  if (blocks == 0) {
+    cudaFuncSetAttribute(hexw_kernel<N, MODE, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, H::SMEM);
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, hexw_kernel<N, MODE, TMA>, 32 * H::WPB, H::SMEM);
+    blocks = (per < 1 ? 1 : per) * sms;
+  }
+  const int64_t per_block = (int64_t)H::WPB * H::EPW;
+  const int64_t need = ((int64_t)A.K + per_block - 1) / per_block;
+  const int grid = (int)(need < blocks ? need : blocks);
+  hexw_kernel<N, MODE, TMA><<<grid, 32 * H::WPB, H::SMEM, s>>>(A, M);
+}
+
+// ---------------------------------------------------------------------------- TMA descriptors
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return static_cast<EncodeTiledFn>(nullptr);
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// 1D descriptor of n floats at base, box of `box` floats; false where TMA cannot address it.
+bool tma_map_1d(TmaArr& t, const float* base, int64_t n, int box) {
+  t.ok = false;
+  t.base = base;
+  t.n = n;
+  t.box = box;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc || !base || n <= 0 || n >= (1LL << 31) || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+  const cuuint64_t dim[1] = {static_cast<cuuint64_t>(n)};
+  const cuuint64_t stride[1] = {4};
+  const cuuint32_t boxd[1] = {static_cast<cuuint32_t>(box)};
+  const cuuint32_t es[1] = {1};
+  t.ok = enc(&t.map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 1, const_cast<float*>(base), dim, stride, boxd, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return t.ok;
+}
+
+// the registered array holding p (with p's offset in floats), or null
+static const TmaArr* tma_find(const dg_mesh* m, const float* p, long long* off) {
+  for (const TmaArr& t : m->tma)
+    if (t.ok && p >= t.base && p < t.base + t.n) {
+      *off = p - t.base;
+      return &t;
+    }
+  return nullptr;
+}
+
+// TMA operands of a fused hex update launch, or false (then the cp.async kernel runs)
+template <int MODE>
+static bool hex_maps(const dg_mesh* m, const Args& A, HexMaps* M) {
+  if (m->N != 4 || !(MODE == MODE_STAGE || MODE == MODE_MRC || MODE == MODE_MRF)) return false;
+  const TmaArr *q = tma_find(m, A.q, &M->qoff), *in = tma_find(m, A.tin, &M->inoff);
+  const TmaArr* a0 = tma_find(m, MODE == MODE_STAGE ? A.res : A.h1, &M->a0off);
+  const TmaArr* a1 = MODE == MODE_STAGE ? a0 : tma_find(m, A.h2, &M->a1off);
+  if (MODE == MODE_STAGE) M->a1off = M->a0off;
+  if (!q || !in || !a0 || !a1 || q->box != 128 || a0->box != 128 || a1->box != 128 || in->box != 160) return false;
+  M->q = q->map;
+  M->in = in->map;
+  M->a0 = a0->map;
+  M->a1 = a1->map;
+  return true;
 }
 
 // ============================================================================ wedge, pyramid, tet
@@ -966,6 +1287,7 @@ static Args make_args(dg_mesh* m, int t) {
   A.iops2 = td.iops2;
   A.K = td.K;
   A.elist = nullptr;
+  A.err = m->derr;
   A.dof_off = td.dof_off;
   A.ndof = m->ndof;
   A.side_off = td.side_off;
@@ -1001,6 +1323,20 @@ static int ev_take(dg_mesh* m) {
   return (int)m->ev_next++;
 }
 
+// N <= 4 hexahedra: the TMA kernel for the fused N = 4 updates when every staged array has a
+// descriptor, the cp.async kernel otherwise
+template <int N, int MODE>
+static void launch_hex_fast(dg_mesh* m, const Args& A, cudaStream_t s) {
+  HexMaps M{};
+  if constexpr (N == 4 && (MODE == MODE_STAGE || MODE == MODE_MRC || MODE == MODE_MRF)) {
+    if (hex_maps<MODE>(m, A, &M)) {
+      launch_hexw_n<N, MODE, true>(A, M, s);
+      return;
+    }
+  }
+  launch_hexw_n<N, MODE, false>(A, M, s);
+}
+
 template <int MODE>
 static void launch_type(dg_mesh* m, const Args& A, int t) {
   if (A.K == 0) return;
@@ -1014,7 +1350,7 @@ static void launch_type(dg_mesh* m, const Args& A, int t) {
   switch (m->N) {
 #define DG_CASE(NN)                                                   \
   case NN:                                                            \
-    if (t == DG_HEX) { if (NN <= 4) launch_hexw_n<(NN <= 4 ? NN : 4), MODE>(A, s); else launch_hex_n<NN, (MODE > 2 ? 1 : MODE)>(A, s); } \
+    if (t == DG_HEX) { if (NN <= 4) launch_hex_fast<(NN <= 4 ? NN : 4), MODE>(m, A, s); else launch_hex_n<NN, (MODE > 2 ? 1 : MODE)>(A, s); } \
     else if (launch_gen2<MODE>(t, NN, A, s)) {}                       \
     else if (t == DG_WEDGE) launch_gen_n<DG_WEDGE, NN, (MODE > 2 ? 1 : MODE)>(A, s);   \
     else if (t == DG_PYR) launch_gen_n<DG_PYR, NN, (MODE > 2 ? 1 : MODE)>(A, s);       \

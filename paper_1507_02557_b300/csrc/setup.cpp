@@ -1114,6 +1114,14 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
     m->res = alloc_zero<float>(4 * (size_t)m->ndof, owned);
     m->trace = alloc_zero<float>(4 * (size_t)m->nsides * nq, owned);
     m->dacc = alloc_zero<double>(4, owned);
+    m->derr = alloc_zero<int>(1, owned);
+    if (!g_host_only) {   // TMA descriptors of the arrays the fused hex kernels stage
+      dgk::tma_map_1d(m->tma[0], m->q, 4 * m->ndof, 128);
+      dgk::tma_map_1d(m->tma[1], m->res, 4 * m->ndof, 128);
+      if (m->hist) dgk::tma_map_1d(m->tma[2], m->hist, 12 * m->ndof, 128);
+      dgk::tma_map_1d(m->tma[3], m->trace, 4 * m->nsides * nq, 160);
+      if (m->trace3) dgk::tma_map_1d(m->tma[4], m->trace3, 2 * m->nsides * nq, 160);
+    }
     if (!g_host_only && cudaDeviceSynchronize() != cudaSuccess) throw SetupError(DG_ECUDA, cudaGetErrorString(cudaGetLastError()));
     return DG_OK;
   } catch (const SetupError& e) {

@@ -75,9 +75,10 @@ def test_rhs_single_type_meshes(lib):
         assert rel(got, o.rhs(q32.astype(np.float64))) < TOL, L
 
 
-@pytest.mark.parametrize("N", [2, 3])
+@pytest.mark.parametrize("N", [2, 3, 4])
 def test_lsrk_steps_match_oracle(lib, N):
-    """Ten LSRK(5,4) steps at the paper's dt from the projected standing mode."""
+    """Ten LSRK(5,4) steps at the paper's dt from the projected standing mode (N = 4: the
+    hexahedra run the TMA-staged stage kernel)."""
     from oracle.dg import standing_mode
     m = small_hybrid_mesh()
     o = DGOracle(m, N)
