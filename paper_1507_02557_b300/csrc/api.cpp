@@ -325,7 +325,8 @@ extern "C" dg_status dg_step(dg_mesh* m, int nsteps, double dt, double* t_inout)
   if (nsteps == 0) return DG_OK;
   if (m->nlevels == 2) {
     bool fresh = !m->mr_started;
-    cudaError_t e = m->N <= 4 ? mrab3_fused(m, nsteps, dt) : mrab3(m, nsteps, dt);
+    // fused kernels: N <= 4 with lattice exchange on tet / pyramid triangle faces
+    cudaError_t e = m->N <= 4 && m->tri_lat ? mrab3_fused(m, nsteps, dt) : mrab3(m, nsteps, dt);
     if (e != cudaSuccess) return cuda_fail(e);
     if (t_inout) *t_inout += (fresh ? 4 * dt : 0.0) + nsteps * 2 * dt;
     return DG_OK;

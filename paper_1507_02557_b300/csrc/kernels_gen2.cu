@@ -3,12 +3,18 @@
 // Persistent blocks stage the element type's reference operators in shared memory
 // once; each warp then walks over elements.  All operators are independent of the
 // face orientation:
-//   triangle faces  the trace is taken at the equispaced face lattice (a gather for
-//                   the nodal tet, a small matrix for the pyramid and the wedge),
-//                   permuted into the canonical face frame, and interpolated to the
-//                   canonical face quadrature points (matrix E); the lift applies E^T,
-//                   the inverse permutation and the transposed lattice evaluation
-//                   (for polynomial traces this equals the face quadrature of Sec. 2.3);
+//   tet / pyramid triangle faces (affine: n, J^s and tau constant over the face)
+//                   the trace is taken at the equispaced face lattice (a gather for the
+//                   nodal tet, a small matrix for the pyramid) and exchanged there: the
+//                   neighbour's value at local lattice node l sits at its canonical index.
+//                   The flux is linear with constant coefficients, so its values at the
+//                   lattice nodes determine it; the face quadrature of Sec. 2.3 of the
+//                   P_N flux against P_N test traces is then the face mass matrix of the
+//                   lattice basis, folded into the lift operators (Lf, Tn2) at setup;
+//   wedge triangle faces (trace divided by sqrt J, not a polynomial)
+//                   lattice values permuted into the canonical frame, interpolated to
+//                   the canonical face quadrature points (matrix E); the lift applies
+//                   E^T, the inverse permutation and the transposed lattice evaluation;
 //   quad faces      the trace is taken at the local GL points and permuted.
 // The four fields p,u,v,w travel together as float4, so every operator entry read
 // from shared memory feeds four FMAs.
@@ -33,7 +39,10 @@ struct G2 {
   static constexpr int VOL = T == DG_WEDGE ? NQ * NT * 4 + 2 * N1 * N1 + NQ * N1 : NP * NP * 4;
   static constexpr int TN = NTRI * NFN * NP;                            // tet: M^-1 lift; others: lattice evals
   static constexpr int TQ = NQUAD * NQ * NP;
-  static constexpr int OPS = VOL + TN + TQ + NQ * NFN;
+  static constexpr bool LAT = T != DG_WEDGE;                            // lattice-point face exchange
+  static constexpr int TN2 = T == DG_PYR ? NTRI * NFN * NP : 0;         // pyramid: lift of lattice fluxes
+  static constexpr int NFX = LAT ? NTRI * NFN + NQUAD * NQ : NF * NQ;   // face flux points
+  static constexpr int OPS = VOL + TN + TQ + TN2 + NQ * NFN;
   static constexpr int IOPS = 12 * NFN + 8 * NQ + (T == DG_TET ? 4 * NFN : 0);
   static constexpr int OPS_B = ((OPS * 4 + 15) / 16) * 16;
   static constexpr int IOPS_B = ((IOPS * 4 + 15) / 16) * 16;
@@ -85,7 +94,10 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
   const float* wq = D1 + C::N1 * C::N1;                          // wedge weights [NQ][N1]
   const float* Tn = sop + C::VOL;                                // [NTRI][NFN][NP]
   const float* Tq = Tn + C::TN;                                  // [NQUAD][NQ][NP]
-  const float* E = Tq + C::TQ;                                   // [NQ][NFN]
+  const float* Tn2 = Tq + C::TQ;                                 // pyramid [NTRI][NFN][NP]
+  const float* E = Tn2 + C::TN2;                                 // [NQ][NFN]
+  constexpr bool LAT = C::LAT;
+  constexpr int NFX = C::NFX, NLT = NTRI * NFN;
   const int* tperm = sio;                                        // [6][NFN] local lattice -> canonical
   const int* qperm = sio + 12 * NFN;                             // [8][NQ] local GL point -> canonical
   const int* fnode = qperm + 8 * NQ;                             // tet [4][NFN]
@@ -121,7 +133,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
           #pragma unroll 4
         for (int m = 0; m < NP; ++m) f4acc(v, row[m], q4[m]);
         }
-        V4[ti * NFN + tperm[code[face_of_tri<T>(ti)] * NFN + nl]] = v;
+        V4[LAT ? x : ti * NFN + tperm[code[face_of_tri<T>(ti)] * NFN + nl]] = v;
       }
     };
     // trace (p,u,v,w) at point idx of face f (triangle: canonical point; quad: local point)
@@ -143,6 +155,23 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
         tr.x *= is; tr.y *= is; tr.z *= is; tr.w *= is;
       }
       return tr;
+    };
+    // LAT: trace at face-flux point x (lattice node of a triangle face, local order, or local
+    // GL point of a quad face), its face, the inbox index and the face data (n, J^s or w J^s)
+    auto lat_point = [&](int x, int& f, int& ci, float4& tr, float4& sg) {
+      if (x < NLT) {
+        const int ti = x / NFN, nl = x % NFN;
+        f = face_of_tri<T>(ti);
+        tr = T == DG_TET ? q4[fnode[x]] : V4[x];
+        ci = tperm[code[f] * NFN + nl];
+        sg = A.sgeo2[(e * NF + f) * NQ];
+      } else {
+        const int idx = (x - NLT) % NQ;
+        f = T == DG_PYR ? 0 : 2 + (x - NLT) / NQ;
+        tr = trace_at(f, idx);
+        ci = qperm[code[f] * NQ + idx];
+        sg = A.sgeo2[(e * NF + f) * NQ + idx];
+      }
     };
 
     float4 acc[R], pred[R];
@@ -293,14 +322,21 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
         }
       }
       // ---------------------------------------------------------------- face fluxes
-      lattice_values();
+      if (T != DG_TET) lattice_values();
       __syncwarp();
-      for (int fq = lane; fq < NF * NQ; fq += 32) {
-        const int f = fq / NQ, idx = fq % NQ;
-        const float4 tr = trace_at(f, idx);
-        const int ci = tri_of<T>(f) >= 0 ? idx : qperm[code[f] * NQ + idx];
+      for (int fq = lane; fq < NFX; fq += 32) {
+        int f, ci;
+        float4 tr, sg;
+        if (LAT) {
+          lat_point(fq, f, ci, tr, sg);
+        } else {
+          f = fq / NQ;
+          const int idx = fq % NQ;
+          tr = trace_at(f, idx);
+          ci = tri_of<T>(f) >= 0 ? idx : qperm[code[f] * NQ + idx];
+          sg = A.sgeo2[(e * NF + f) * NQ + idx];
+        }
         const int64_t gs = A.side_off + e * NF + f;
-        const float4 sg = A.sgeo2[(e * NF + f) * NQ + idx];
         const float unm = sg.x * tr.y + sg.y * tr.z + sg.z * tr.w;
         const int nb = A.nbr[gs];
         float P = 0.f, UN = 0.f;
@@ -314,33 +350,38 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
         F4[fq] = f4(sg.w * fp, sg.w * fu * sg.x, sg.w * fu * sg.y, sg.w * fu * sg.z);
       }
       __syncwarp();
-      // lattice moments of the triangle-face fluxes, in local lattice order
-      for (int x = lane; x < NTRI * NFN; x += 32) {
-        const int ti = x / NFN, nl = x % NFN;
-        const int f = face_of_tri<T>(ti);
-        const int nc = tperm[code[f] * NFN + nl];
-        float4 gsum = f4(0.f, 0.f, 0.f, 0.f);
-        const float4* fr = F4 + f * NQ;
-        #pragma unroll 4
-        for (int q = 0; q < NQ; ++q) f4acc(gsum, E[q * NFN + nc], fr[q]);
-        G4[x] = gsum;
+      if (!LAT) {
+        // lattice moments of the triangle-face fluxes, in local lattice order
+        for (int x = lane; x < NTRI * NFN; x += 32) {
+          const int ti = x / NFN, nl = x % NFN;
+          const int f = face_of_tri<T>(ti);
+          const int nc = tperm[code[f] * NFN + nl];
+          float4 gsum = f4(0.f, 0.f, 0.f, 0.f);
+          const float4* fr = F4 + f * NQ;
+#pragma unroll 4
+          for (int q = 0; q < NQ; ++q) f4acc(gsum, E[q * NFN + nc], fr[q]);
+          G4[x] = gsum;
+        }
+        __syncwarp();
       }
-      __syncwarp();
       // ---------------------------------------------------------------- lift, M^{-1}, update
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int n = lane + 32 * r;
         if (n >= NP) break;
         float4 sum = f4(0.f, 0.f, 0.f, 0.f);
-        #pragma unroll 4
-        for (int x = 0; x < NTRI * NFN; ++x) f4acc(sum, Tn[x * NP + n], G4[x]);
+        // triangle faces: lattice-point fluxes (LAT: Lf / Tn2 hold the face mass) or moments
+        const float* Lt = T == DG_PYR ? Tn2 : Tn;
+        const float4* Gt = LAT ? F4 : G4;
+#pragma unroll 4
+        for (int x = 0; x < NLT; ++x) f4acc(sum, (LAT ? Lt : Tn)[x * NP + n], Gt[x]);
 #pragma unroll
         for (int qi = 0; qi < NQUAD; ++qi) {
           const int f = T == DG_PYR ? 0 : 2 + qi;
           const float* col = Tq + qi * NQ * NP + n;
-          const float4* fr = F4 + f * NQ;
-          #pragma unroll 4
-        for (int lp = 0; lp < NQ; ++lp) f4acc(sum, col[lp * NP], fr[lp]);
+          const float4* fr = LAT ? F4 + NLT + qi * NQ : F4 + f * NQ;
+#pragma unroll 5
+          for (int lp = 0; lp < NQ; ++lp) f4acc(sum, col[lp * NP], fr[lp]);
         }
         float iM = 1.f;
         if (T == DG_TET) iM = 1.f / A.geo[e * 12 + 9];
@@ -418,16 +459,27 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
     }
     // traces of the state in q4 into the neighbours' inboxes
     auto emit = [&](float* tout) {
-      lattice_values();
+      if (T != DG_TET) lattice_values();
       __syncwarp();
-      for (int fq = lane; fq < NF * NQ; fq += 32) {
-        const int f = fq / NQ, idx = fq % NQ;
+      for (int fq = lane; fq < NFX; fq += 32) {
+        int f, ci;
+        float4 tr, sg;
+        if (LAT) {
+          f = fq < NLT ? face_of_tri<T>(fq / NFN) : (T == DG_PYR ? 0 : 2 + (fq - NLT) / NQ);
+        } else {
+          f = fq / NQ;
+        }
         const int64_t gs = A.side_off + e * NF + f;
         const int nb = A.nbr[gs];
         if (nb < 0) continue;
-        const float4 tr = trace_at(f, idx);
-        const int ci = tri_of<T>(f) >= 0 ? idx : qperm[code[f] * NQ + idx];
-        const float4 sg = A.sgeo2[(e * NF + f) * NQ + idx];
+        if (LAT) {
+          lat_point(fq, f, ci, tr, sg);
+        } else {
+          const int idx = fq % NQ;
+          tr = trace_at(f, idx);
+          ci = tri_of<T>(f) >= 0 ? idx : qperm[code[f] * NQ + idx];
+          sg = A.sgeo2[(e * NF + f) * NQ + idx];
+        }
         tout[(int64_t)nb * NQ + ci] = tr.x;
         tout[A.plane + (int64_t)nb * NQ + ci] = sg.x * tr.y + sg.y * tr.z + sg.z * tr.w;
       }

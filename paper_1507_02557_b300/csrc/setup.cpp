@@ -520,6 +520,18 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
       e = r / nfc[t];
       f = (int)(r % nfc[t]);
     };
+    // triangle faces exchange lattice values (tet, pyramid) unless a wedge's triangle face meets
+    // a tet or pyramid: the wedge's trace is not a polynomial there, so the whole mesh then keeps
+    // the quadrature-point exchange of the older kernels for tets and pyramids
+    m->tri_lat = true;
+    for (int64_t s = 0; s < side; ++s) {
+      int t, f, t2, f2;
+      int64_t e, e2;
+      if (nbr[s] < 0) continue;
+      side_elem(s, t, e, f);
+      side_elem(nbr[s], t2, e2, f2);
+      if (face_nverts(t, f) == 3 && (t == WEDGE) != (t2 == WEDGE)) m->tri_lat = false;
+    }
     for (int64_t s = 0; s < side; ++s) {
       int t, f, t2, f2;
       int64_t e, e2;
@@ -643,6 +655,7 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
       // face geometry (non-hex: stored; all types: time-step data)
       std::vector<float4> sgeo, sgeo2;
       std::vector<float> sisq, sisq2;
+      double js0 = 0.0;
       for (int64_t e = 0; e < K; ++e) {
         load_xv(e);
         for (int f = 0; f < nf; ++f) {
@@ -686,6 +699,14 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
             if (t != HEX) {
               double wj = w[q] * Js;
               if (t == WEDGE) wj /= std::sqrt(J);
+              if (pass == 1 && fnv == 3 && t != WEDGE) {
+                // lattice exchange: the face is affine, n and J^s are constant over it; the
+                // quadrature weights live in the face mass matrix folded into the lift
+                wj = Js;
+                if (q == 0) js0 = Js;
+                else if (std::fabs(Js - js0) > 1e-9 * js0)
+                  throw SetupError(DG_EMESH, "triangle face of a tet or pyramid is not affine");
+              }
               float4 gv = make_float4((float)(nn[0] / nl), (float)(nn[1] / nl), (float)(nn[2] / nl), (float)wj);
               (pass == 0 ? sgeo : sgeo2).push_back(gv);
               if (t == WEDGE) (pass == 0 ? sisq : sisq2).push_back((float)(1.0 / std::sqrt(J)));
@@ -887,14 +908,21 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
         td.ops = upload(ops, owned);
 
         // ---- orientation-free operators (kernels_gen2.cu); float layout:
-        //  tet:   DV4[Np][Np] (D^r,D^s,D^t,0) | Lf[4][nfn][Np] = Mhat^{-1}[i][fnode] | E[nq][nfn]
-        //  pyr:   DV4[Np][Np] | Tn[4][nfn][Np] (tri faces 1..4) | Tq[nq][Np] (base) | E[nq][nfn]
+        //  tet:   DV4[Np][Np] (D^r,D^s,D^t,0) | Lf[4][nfn][Np] = Mhat^{-1} face-node columns x Mf | E[nq][nfn]
+        //  pyr:   DV4[Np][Np] | Tn[4][nfn][Np] (tri faces 1..4) | Tq[nq][Np] (base) | Tn2[4][nfn][Np] = Mf Tn |
+        //         E[nq][nfn]
         //  wedge: VV4[nc][Np] (V,V_r,V_s,V_t) | wq[nc] | Tn[2][nfn][Np] | Tq[3][nq][Np] | E[nq][nfn]
         //  int layout: tperm[6][nfn] | tinv[6][nfn] | qperm[8][nq] | (tet) fnode[4][nfn]
         const int nfn = (N + 1) * (N + 2) / 2;
         std::vector<int> tperm, tinv;
         std::vector<double> E;
         lattice_tables(N, tperm, tinv, E, tpts);
+        // face mass matrix of the lattice basis, Mf[m][n] = sum_q w_q l_m(x_q) l_n(x_q); it is
+        // invariant under the six vertex permutations of the (symmetric) lattice
+        std::vector<double> Mf(nfn * nfn, 0.0);
+        for (int a = 0; a < nfn; ++a)
+          for (int b2 = 0; b2 < nfn; ++b2)
+            for (int q = 0; q < nq; ++q) Mf[a * nfn + b2] += tw[q] * E[q * nfn + a] * E[q * nfn + b2];
         std::vector<float> o2;
         std::vector<int> i2(tperm.begin(), tperm.end());
         i2.insert(i2.end(), tinv.begin(), tinv.end());
@@ -958,9 +986,14 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
               }
           for (int v : fnode)
             if (v < 0) throw SetupError(DG_EINVAL, "tet face lattice not found among the nodes");
+          // lift of lattice-point fluxes: Lf[f][n][i] = sum_m Mhat^{-1}[i][fnode[f][m]] Mf[m][n]
           for (int f = 0; f < 4; ++f)
             for (int n = 0; n < nfn; ++n)
-              for (int i = 0; i < Np; ++i) o2.push_back((float)Minv[i * Np + fnode[f * nfn + n]]);
+              for (int i = 0; i < Np; ++i) {
+                double v = 0.0;
+                for (int mm = 0; mm < nfn; ++mm) v += Minv[i * Np + fnode[f * nfn + mm]] * Mf[mm * nfn + n];
+                o2.push_back((float)v);
+              }
           i2.insert(i2.end(), fnode.begin(), fnode.end());
         } else {
           if (t == WEDGE) {
@@ -1034,6 +1067,26 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
               face_point(t, f, ident, qpts[2 * q], qpts[2 * q + 1], rst, d1, d2);
               B[t].eval(rst, phi.data(), nullptr);
               for (int i = 0; i < Np; ++i) o2.push_back((float)phi[i]);
+            }
+          }
+          if (t == PYR) {
+            // lift of lattice-point fluxes on the triangle faces: Tn2[f][n][i] = sum_m Mf[n][m] phi_i(lattice_m)
+            std::vector<double> tn(nfn * Np);
+            for (int f = 0; f < nf; ++f) {
+              if (face_nverts(t, f) != 3) continue;
+              for (int l2 = 0; l2 <= N; ++l2)
+                for (int l1 = 0; l1 + l2 <= N; ++l1) {
+                  double rst[3];
+                  lattice_rst(f, l1, l2, rst);
+                  B[t].eval(rst, phi.data(), nullptr);
+                  for (int i = 0; i < Np; ++i) tn[lattice_index(N, l1, l2) * Np + i] = phi[i];
+                }
+              for (int n = 0; n < nfn; ++n)
+                for (int i = 0; i < Np; ++i) {
+                  double v = 0.0;
+                  for (int mm = 0; mm < nfn; ++mm) v += Mf[n * nfn + mm] * tn[mm * Np + i];
+                  o2.push_back((float)v);
+                }
             }
           }
         }
