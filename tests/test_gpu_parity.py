@@ -157,3 +157,43 @@ def test_multirate_ab3_matches_oracle(lib, N):
         q, hist = mr.step(q, hist, h)
     assert abs(t - 14 * h) < 1e-12
     assert rel(got, q) < TOL, per_type_rel(o, got, q)
+
+
+def wedge_tet_mesh():
+    """One wedge and one tet sharing a triangle face, c^2 = 1 and 2.25: a wedge triangle face
+    against a tet selects the quadrature-point face exchange for tets and pyramids."""
+    from paper_1507_02557_b300.inputs import HybridMesh
+    xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 0, 1], [0, 1, 0], [1, 1, 0], [0, 1, 1], [0, -1, 0]], float)
+    conn = [np.zeros((0, 8), np.int32), np.array([[0, 1, 2, 3, 4, 5]], np.int32),
+            np.zeros((0, 5), np.int32), np.array([[0, 1, 2, 6]], np.int32)]
+    c2 = [np.zeros(0), np.array([1.0]), np.zeros(0), np.array([2.25])]
+    return HybridMesh(xyz=xyz, conn=conn, c2=c2)
+
+
+@pytest.mark.parametrize("N", [2, 4])
+def test_wedge_tet_triangle_face_rhs(lib, N):
+    m = wedge_tet_mesh()
+    o = DGOracle(m, N)
+    q32 = random_state(o.ndof, 3).astype(np.float32)
+    got, _ = gpu_rhs(lib, m, N, q32)
+    assert rel(got, o.rhs(q32.astype(np.float64))) < TOL
+
+
+def test_wedge_tet_triangle_face_multirate(lib):
+    """Start-up + 3 coarse MRAB3 steps through the unfused schedule of this mesh."""
+    from oracle.constants import trace_constant
+    from oracle.dg import MRAB3, mr_levels, standing_mode
+    m, N = wedge_tet_mesh(), 3
+    o = DGOracle(m, N)
+    lev, dmin = mr_levels(o, [trace_constant(t, N) for t in range(4)], 2)
+    g = lib.Mesh(m, N, nlevels=2)
+    h = g.timestep()
+    q0 = o.project(standing_mode, 0.0).astype(np.float32)
+    g.set_state(q0, on_device=False)
+    g.step(3, h)
+    got = g.get_state(np.zeros_like(q0), on_device=False).astype(np.float64)
+    mr = MRAB3(o, lev)
+    q, hist = mr.start(q0.astype(np.float64), h)
+    for _ in range(3):
+        q, hist = mr.step(q, hist, h)
+    assert rel(got, q) < TOL
