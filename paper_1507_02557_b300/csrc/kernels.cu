@@ -1319,6 +1319,11 @@ static void launch_gen_n(const Args& A, cudaStream_t s) {
 
 template <int MODE>
 bool launch_gen2(int t, int N, const Args& A, cudaStream_t s);   // kernels_gen2.cu
+template <int MODE>
+bool launch_tet_tc(int N, const Args& A, cudaStream_t s);        // kernels_tc.cu
+#ifndef DG_TET_TC
+#define DG_TET_TC 1
+#endif
 
 // Event pair around one type's launch when dg_profile is on.
 static int ev_take(dg_mesh* m) {
@@ -1358,6 +1363,7 @@ static void launch_type(dg_mesh* m, const Args& A, int t) {
 #define DG_CASE(NN)                                                   \
   case NN:                                                            \
     if (t == DG_HEX) { if (NN <= 4) launch_hex_fast<(NN <= 4 ? NN : 4), MODE>(m, A, s); else launch_hex_n<NN, (MODE > 2 ? 1 : MODE)>(A, s); } \
+    else if (DG_TET_TC && t == DG_TET && m->tri_lat && launch_tet_tc<MODE>(NN, A, s)) {}   \
     else if ((t == DG_WEDGE || m->tri_lat) && launch_gen2<MODE>(t, NN, A, s)) {}   \
     else if (t == DG_WEDGE) launch_gen_n<DG_WEDGE, NN, (MODE > 2 ? 1 : MODE)>(A, s);   \
     else if (t == DG_PYR) launch_gen_n<DG_PYR, NN, (MODE > 2 ? 1 : MODE)>(A, s);       \
