@@ -34,11 +34,13 @@ struct G2 {
   static constexpr int NTRI = T == DG_WEDGE ? 2 : 4;
   static constexpr int NQUAD = NF - NTRI;
   static constexpr int NC = T == DG_WEDGE ? (N + 1) * (N + 1) * (N + 1) : 0;
-  static constexpr int NW = T == DG_WEDGE ? 12 : 16;                   // warps per block
+  static constexpr int NW = 16;                                        // warps per block
   static constexpr int N1 = N + 1, NT = NFN;                            // wedge: 1D points, triangle modes
   static constexpr int VOL = T == DG_WEDGE ? NQ * NT * 4 + 2 * N1 * N1 + NQ * N1 : NP * NP * 4;
-  static constexpr int TN = NTRI * NFN * NP;                            // tet: M^-1 lift; others: lattice evals
-  static constexpr int TQ = NQUAD * NQ * NP;
+  // tet: lattice lift; pyramid: lattice evals; wedge: Vtl [2][NFN][NT]
+  static constexpr int TN = T == DG_WEDGE ? NTRI * NFN * NT : NTRI * NFN * NP;
+  // pyramid: GL evals of the base; wedge: Ve [3][N1][NT] | V1e [2][N1]
+  static constexpr int TQ = T == DG_WEDGE ? NQUAD * N1 * NT + 2 * N1 : NQUAD * NQ * NP;
   static constexpr bool LAT = T != DG_WEDGE;                            // lattice-point face exchange
   static constexpr int TN2 = T == DG_PYR ? NTRI * NFN * NP : 0;         // pyramid: lift of lattice fluxes
   static constexpr int NFX = LAT ? NTRI * NFN + NQUAD * NQ : NF * NQ;   // face flux points
@@ -98,6 +100,9 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
   const float* E = Tn2 + C::TN2;                                 // [NQ][NFN]
   constexpr bool LAT = C::LAT;
   constexpr int NFX = C::NFX, NLT = NTRI * NFN;
+  const float* Vtl = Tn;                                         // wedge [2][NFN][NT]
+  const float* Ve = Tq;                                          // wedge [3][N1][NT]
+  const float* V1e = Tq + NQUAD * C::N1 * C::NT;                 // wedge [2][N1]
   const int* tperm = sio;                                        // [6][NFN] local lattice -> canonical
   const int* qperm = sio + 12 * NFN;                             // [8][NQ] local GL point -> canonical
   const int* fnode = qperm + 8 * NQ;                             // tet [4][NFN]
@@ -120,20 +125,65 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
       q4[n] = f4(A.q[base + n], A.q[A.ndof + base + n], A.q[2 * A.ndof + base + n], A.q[3 * A.ndof + base + n]);
     __syncwarp();
 
-    // canonical lattice values of the triangle faces (V4) from q4
-    auto lattice_values = [&]() {
-      for (int x = lane; x < NTRI * NFN; x += 32) {
-        const int ti = x / NFN, nl = x % NFN;
-        float4 v;
-        if (T == DG_TET) {
-          v = q4[fnode[ti * NFN + nl]];
+    // wedge, factorised over triangle x 1D: lattice values of the two triangle faces (V4,
+    // canonical order) and traces at the local GL points of the three quad faces (TQ), with
+    // Z_f[mt] = sum_j phi_1D_j(s_f) q[mt, j] and Y_qf[ia][j] = sum_mt phi_tri_mt(edge_ia) q[mt, j]
+    // staged in the (then free) volume scratch
+    constexpr int WN1 = C::N1, WNT = C::NT;
+    float4* ZB = W4;
+    float4* YB = W4 + 2 * WNT;
+    float4* TQB = YB + 3 * WN1 * WN1;
+    auto wedge_face_values = [&]() {
+      for (int x = lane; x < 2 * WNT + 3 * WN1 * WN1; x += 32) {
+        float4 v = f4(0.f, 0.f, 0.f, 0.f);
+        if (x < 2 * WNT) {
+          const int f = x / WNT, mt = x % WNT;
+#pragma unroll
+          for (int j = 0; j < WN1; ++j) f4acc(v, V1e[f * WN1 + j], q4[mt + WNT * j]);
+          ZB[x] = v;
         } else {
-          v = f4(0.f, 0.f, 0.f, 0.f);
-          const float* row = Tn + (ti * NFN + nl) * NP;
-          #pragma unroll 4
-        for (int m = 0; m < NP; ++m) f4acc(v, row[m], q4[m]);
+          const int y = x - 2 * WNT, qf = y / (WN1 * WN1), ia = (y / WN1) % WN1, j = y % WN1;
+          const float* ve = Ve + (qf * WN1 + ia) * WNT;
+#pragma unroll 5
+          for (int mt = 0; mt < WNT; ++mt) f4acc(v, ve[mt], q4[mt + WNT * j]);
+          YB[y] = v;
         }
-        V4[LAT ? x : ti * NFN + tperm[code[face_of_tri<T>(ti)] * NFN + nl]] = v;
+      }
+      __syncwarp();
+      for (int x = lane; x < 2 * NFN + 3 * NQ; x += 32) {
+        float4 v = f4(0.f, 0.f, 0.f, 0.f);
+        if (x < 2 * NFN) {
+          const int ti = x / NFN, nl = x % NFN;
+          const float* vt = Vtl + (ti * NFN + nl) * WNT;
+#pragma unroll 5
+          for (int mt = 0; mt < WNT; ++mt) f4acc(v, vt[mt], ZB[ti * WNT + mt]);
+          V4[ti * NFN + tperm[code[ti] * NFN + nl]] = v;
+        } else {
+          const int y = x - 2 * NFN, qf = y / NQ, idx = y % NQ, ia = idx % WN1, ib = idx / WN1;
+#pragma unroll
+          for (int j = 0; j < WN1; ++j) f4acc(v, V1[ib * WN1 + j], YB[(qf * WN1 + ia) * WN1 + j]);
+          TQB[y] = v;
+        }
+      }
+    };
+    // canonical lattice values of the triangle faces (V4) from q4
+    // (tet, pyramid: local order; the wedge also fills the quad-face traces)
+    auto lattice_values = [&]() {
+      if constexpr (T == DG_WEDGE) {
+        wedge_face_values();
+      } else {
+        for (int x = lane; x < NTRI * NFN; x += 32) {
+          float4 v;
+          if (T == DG_TET) {
+            v = q4[fnode[x]];
+          } else {
+            v = f4(0.f, 0.f, 0.f, 0.f);
+            const float* row = Tn + x * NP;
+#pragma unroll 4
+            for (int m = 0; m < NP; ++m) f4acc(v, row[m], q4[m]);
+          }
+          V4[x] = v;
+        }
       }
     };
     // trace (p,u,v,w) at point idx of face f (triangle: canonical point; quad: local point)
@@ -145,6 +195,8 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
         const float4* vc = V4 + ti * NFN;
         #pragma unroll 4
         for (int n = 0; n < NFN; ++n) f4acc(tr, er[n], vc[n]);
+      } else if (T == DG_WEDGE) {
+        tr = TQB[quad_of<T>(f) * NQ + idx];
       } else {
         const float* row = Tq + (quad_of<T>(f) * NQ + idx) * NP;
         #pragma unroll 4
@@ -365,23 +417,51 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
         __syncwarp();
       }
       // ---------------------------------------------------------------- lift, M^{-1}, update
+      float4* HB = W4;              // wedge: H_f[mt] = sum_nl phi_tri_mt(lattice_nl) G_f[nl]
+      float4* PB = W4 + 2 * WNT;    // wedge: P_qf[ia][j] = sum_ib phi_1D_j(x_ib) F_qf[ia, ib]
+      if (T == DG_WEDGE) {
+        for (int x = lane; x < 2 * WNT + 3 * WN1 * WN1; x += 32) {
+          float4 v = f4(0.f, 0.f, 0.f, 0.f);
+          if (x < 2 * WNT) {
+            const int f = x / WNT, mt = x % WNT;
+#pragma unroll 5
+            for (int nl = 0; nl < NFN; ++nl) f4acc(v, Vtl[(f * NFN + nl) * WNT + mt], G4[f * NFN + nl]);
+            HB[x] = v;
+          } else {
+            const int y = x - 2 * WNT, qf = y / (WN1 * WN1), ia = (y / WN1) % WN1, j = y % WN1;
+#pragma unroll
+            for (int ib = 0; ib < WN1; ++ib) f4acc(v, V1[ib * WN1 + j], F4[(2 + qf) * NQ + ia + WN1 * ib]);
+            PB[y] = v;
+          }
+        }
+        __syncwarp();
+      }
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int n = lane + 32 * r;
         if (n >= NP) break;
         float4 sum = f4(0.f, 0.f, 0.f, 0.f);
-        // triangle faces: lattice-point fluxes (LAT: Lf / Tn2 hold the face mass) or moments
-        const float* Lt = T == DG_PYR ? Tn2 : Tn;
-        const float4* Gt = LAT ? F4 : G4;
-#pragma unroll 4
-        for (int x = 0; x < NLT; ++x) f4acc(sum, (LAT ? Lt : Tn)[x * NP + n], Gt[x]);
+        if (T == DG_WEDGE) {   // node (mt, j): triangle faces, then quad faces (edge x 1D)
+          const int mt = n % WNT, j = n / WNT;
+          f4acc(sum, V1e[j], HB[mt]);
+          f4acc(sum, V1e[WN1 + j], HB[WNT + mt]);
 #pragma unroll
-        for (int qi = 0; qi < NQUAD; ++qi) {
-          const int f = T == DG_PYR ? 0 : 2 + qi;
-          const float* col = Tq + qi * NQ * NP + n;
-          const float4* fr = LAT ? F4 + NLT + qi * NQ : F4 + f * NQ;
+          for (int qf = 0; qf < 3; ++qf)
+#pragma unroll
+            for (int ia = 0; ia < WN1; ++ia)
+              f4acc(sum, Ve[(qf * WN1 + ia) * WNT + mt], PB[(qf * WN1 + ia) * WN1 + j]);
+        } else {
+          // triangle faces: lattice-point fluxes (LAT: Lf / Tn2 hold the face mass)
+          const float* Lt = T == DG_PYR ? Tn2 : Tn;
+#pragma unroll 4
+          for (int x = 0; x < NLT; ++x) f4acc(sum, Lt[x * NP + n], F4[x]);
+#pragma unroll
+          for (int qi = 0; qi < NQUAD; ++qi) {
+            const float* col = Tq + qi * NQ * NP + n;
+            const float4* fr = F4 + NLT + qi * NQ;
 #pragma unroll 5
-          for (int lp = 0; lp < NQ; ++lp) f4acc(sum, col[lp * NP], fr[lp]);
+            for (int lp = 0; lp < NQ; ++lp) f4acc(sum, col[lp * NP], fr[lp]);
+          }
         }
         float iM = 1.f;
         if (T == DG_TET) iM = 1.f / A.geo[e * 12 + 9];

@@ -911,7 +911,8 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
         //  tet:   DV4[Np][Np] (D^r,D^s,D^t,0) | Lf[4][nfn][Np] = Mhat^{-1} face-node columns x Mf | E[nq][nfn]
         //  pyr:   DV4[Np][Np] | Tn[4][nfn][Np] (tri faces 1..4) | Tq[nq][Np] (base) | Tn2[4][nfn][Np] = Mf Tn |
         //         E[nq][nfn]
-        //  wedge: VV4[nc][Np] (V,V_r,V_s,V_t) | wq[nc] | Tn[2][nfn][Np] | Tq[3][nq][Np] | E[nq][nfn]
+        //  wedge: Vt4[nq][ntri] | V1[n1][n1] | D1[n1][n1] | w[nq][n1] | Vtl[2][nfn][ntri] | Ve[3][n1][ntri] |
+        //         V1e[2][n1] | E[nq][nfn]
         //  int layout: tperm[6][nfn] | tinv[6][nfn] | qperm[8][nq] | (tet) fnode[4][nfn]
         const int nfn = (N + 1) * (N + 2) / 2;
         std::vector<int> tperm, tinv;
@@ -1049,7 +1050,36 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
           // triangle-face lattice evaluations, then quad-face local GL evaluations
           std::vector<double> gx, gw;
           gauss_jacobi(n1, 0, 0, gx, gw);
-          for (int f = 0; f < nf; ++f) {
+          if (t == WEDGE) {
+            // factorised face evaluations of phi_(mt,j) = phi_tri_mt(r,t) phi_1D_j(s):
+            //   Vtl[2][nfn][ntri]  phi_tri at the lattice of the triangle faces (s = -1, +1)
+            //   Ve[3][n1][ntri]    phi_tri at the GL points along the edge of each quad face
+            //                      (local u; local v runs along s)
+            //   V1e[2][n1]         phi_1D_j(-1), phi_1D_j(+1)
+            const int ntri = Np / n1;
+            for (int f = 0; f < 2; ++f)
+              for (int l2 = 0; l2 <= N; ++l2)
+                for (int l1 = 0; l1 + l2 <= N; ++l1) {
+                  double rst[3];
+                  lattice_rst(f, l1, l2, rst);
+                  const double rt[3] = {rst[0], 0.0, rst[2]};
+                  B[t].eval(rt, phi.data(), nullptr);
+                  for (int mt = 0; mt < ntri; ++mt) o2.push_back((float)(phi[mt] * std::sqrt(2.0)));
+                }
+            static const int ident4[4] = {0, 1, 2, 3};
+            for (int f = 2; f < 5; ++f)
+              for (int ia = 0; ia < n1; ++ia) {
+                double rst[3], d1[3], d2[3];
+                face_point(t, f, ident4, gx[ia], -1.0, rst, d1, d2);
+                const double rt[3] = {rst[0], 0.0, rst[2]};
+                B[t].eval(rt, phi.data(), nullptr);
+                for (int mt = 0; mt < ntri; ++mt) o2.push_back((float)(phi[mt] * std::sqrt(2.0)));
+              }
+            for (int f = 0; f < 2; ++f)
+              for (int j = 0; j < n1; ++j)
+                o2.push_back((float)(std::sqrt((2.0 * j + 1) / 2) * jacobi(j, 0, 0, f == 0 ? -1.0 : 1.0)));
+          }
+          for (int f = 0; f < nf && t != WEDGE; ++f) {
             if (face_nverts(t, f) != 3) continue;
             for (int l2 = 0; l2 <= N; ++l2)
               for (int l1 = 0; l1 + l2 <= N; ++l1) {
@@ -1060,7 +1090,7 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
               }
           }
           static const int ident[4] = {0, 1, 2, 3};
-          for (int f = 0; f < nf; ++f) {
+          for (int f = 0; f < nf && t != WEDGE; ++f) {
             if (face_nverts(t, f) != 4) continue;
             for (int q = 0; q < nq; ++q) {
               double rst[3], d1[3], d2[3];
