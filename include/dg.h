@@ -154,6 +154,18 @@ dg_status dg_energy_noalloc(dg_mesh *mesh, const float *q_dev, double *E);
  * (enable = 1) or off (enable = 0).  Launch counts are kept even when off. */
 dg_status dg_profile(dg_mesh *mesh, int enable, double *ms, int64_t *launches);
 
+/* Self-test of the device watchdog.  Kernels that wait on the GPU (the
+ * mbarrier waits of the TMA-staged hex kernel and of the tensor-core tet
+ * kernel) bound every wait; a wait that runs out sets bit 0 of the mesh's
+ * device error word, and the next synchronising call (dg_get_state to the host,
+ * dg_energy) returns DG_ETIMEOUT and clears the word.  This call launches one
+ * kernel whose bounded wait is on an mbarrier that no thread arrives on, so it
+ * runs out after limit_cycles SM clocks (1 .. 2^32) and records the timeout the
+ * same way; the call then synchronises and returns that status (DG_ETIMEOUT when
+ * the watchdog works; the word is cleared).  No counterpart in the paper.
+ * DG_EINVAL for a null mesh or a limit out of range. */
+dg_status dg_watchdog_selftest(dg_mesh *mesh, int64_t limit_cycles);
+
 /* Adjoint of dg_step (gradient w.r.t. c^2 and source amplitude): not built,
  * returns DG_ENOTSUP. */
 dg_status dg_adjoint_step(dg_mesh *mesh, int nsteps, float *lambda_dev, double *grad_c2_dev,

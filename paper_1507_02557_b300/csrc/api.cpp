@@ -319,6 +319,18 @@ cudaError_t mrab3_fused(dg_mesh* m, int nsteps, double h) {
 
 }  // namespace
 
+namespace dgk {
+cudaError_t launch_watchdog(int* err, long long limit, cudaStream_t s);   // kernels_tc.cu
+}
+
+extern "C" dg_status dg_watchdog_selftest(dg_mesh* m, int64_t limit_cycles) {
+  if (!m || !m->derr || limit_cycles < 1 || limit_cycles > (1LL << 32)) return DG_EINVAL;
+  cudaError_t e = dgk::launch_watchdog(m->derr, (long long)limit_cycles, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return device_flags(m);
+}
+
 extern "C" dg_status dg_step(dg_mesh* m, int nsteps, double dt, double* t_inout) {
   if (!m || nsteps < 0) return DG_EINVAL;
   if (!(dt > 0)) dt = m->dt_min;

@@ -439,6 +439,33 @@ bool launch_tet_tc(int N, const Args& A, cudaStream_t s) {
   }
 }
 
+// Watchdog self-test: a bounded wait on an mbarrier that nothing arrives on; the timeout is
+// recorded in the device error word as in the production kernels.
+__global__ void watchdog_kernel(int* err, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const unsigned a = su32(&bar);
+  const long long t0 = clock64();
+  unsigned done = 0;
+  while (!done && clock64() - t0 < limit)
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a)
+        : "memory");
+  if (!__syncthreads_or(done == 0) || threadIdx.x != 0) return;
+  atomicOr(err, 1);
+}
+
+cudaError_t launch_watchdog(int* err, long long limit, cudaStream_t s) {
+  watchdog_kernel<<<1, 32, 0, s>>>(err, limit);
+  return cudaGetLastError();
+}
+
 template bool launch_tet_tc<MODE_TRACE>(int, const Args&, cudaStream_t);
 template bool launch_tet_tc<MODE_RHS>(int, const Args&, cudaStream_t);
 template bool launch_tet_tc<MODE_STAGE>(int, const Args&, cudaStream_t);

@@ -20,7 +20,8 @@ _lib = C.CDLL(LIB_PATH)
 HEX, WEDGE, PYR, TET = 0, 1, 2, 3
 EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_host_check", "dg_layout", "dg_ndof", "dg_level_counts",
            "dg_set_state", "dg_get_state", "dg_rhs", "dg_timestep", "dg_step", "dg_state_ptr",
-           "dg_energy", "dg_energy_noalloc", "dg_profile", "dg_adjoint_step", "dg_status_string", "dg_last_error")
+           "dg_energy", "dg_energy_noalloc", "dg_profile", "dg_watchdog_selftest", "dg_adjoint_step",
+           "dg_status_string", "dg_last_error")
 
 
 class Desc(C.Structure):
@@ -47,6 +48,7 @@ _lib.dg_step.argtypes = [_vp, C.c_int, C.c_double, C.POINTER(C.c_double)]
 _lib.dg_state_ptr.argtypes = [_vp, C.POINTER(_vp)]
 _lib.dg_energy.argtypes = [_vp, _vp, C.POINTER(C.c_double)]
 _lib.dg_energy_noalloc.argtypes = [_vp, _vp, C.POINTER(C.c_double)]
+_lib.dg_watchdog_selftest.argtypes = [_vp, C.c_int64]
 _lib.dg_profile.argtypes = [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
 _lib.dg_status_string.restype = C.c_char_p
 _lib.dg_status_string.argtypes = [C.c_int]
@@ -172,6 +174,10 @@ class Mesh:
         E = C.c_double()
         _check(_lib.dg_energy_noalloc(self._h, _ptr(q_dev) if q_dev is not None else None, C.byref(E)))
         return E.value
+
+    def watchdog_selftest(self, limit_cycles):
+        """dg_watchdog_selftest: the status (an int) a bounded device wait that runs out reports."""
+        return int(_lib.dg_watchdog_selftest(self._h, int(limit_cycles)))
 
     def profile(self, enable):
         """Per-type kernel ms and launch counts since the last call; then (re)arm timing."""

@@ -197,3 +197,14 @@ def test_wedge_tet_triangle_face_multirate(lib):
     for _ in range(3):
         q, hist = mr.step(q, hist, h)
     assert rel(got, q) < TOL
+
+
+def test_watchdog_reports_timeout(lib):
+    """A bounded device wait that runs out (on an mbarrier nothing arrives on) is reported as
+    DG_ETIMEOUT by the synchronizing call; the word is cleared and the mesh stays usable."""
+    m = small_hybrid_mesh()
+    g = lib.Mesh(m, 2)
+    assert g.watchdog_selftest(1 << 20) == -5
+    g.set_state(random_state(g.ndof, 1).astype(np.float32), on_device=False)
+    g.step(1)
+    assert np.isfinite(g.energy())
