@@ -37,12 +37,14 @@ struct G2 {
   static constexpr int NW = 16;                                        // warps per block
   static constexpr int N1 = N + 1, NT = NFN;                            // wedge: 1D points, triangle modes
   static constexpr int VOL = T == DG_WEDGE ? NQ * NT * 4 + 2 * N1 * N1 + NQ * N1 : NP * NP * 4;
-  // tet: lattice lift; pyramid: lattice evals; wedge: Vtl [2][NFN][NT]
-  static constexpr int TN = T == DG_WEDGE ? NTRI * NFN * NT : NTRI * NFN * NP;
-  // pyramid: GL evals of the base; wedge: Ve [3][N1][NT] | V1e [2][N1]
-  static constexpr int TQ = T == DG_WEDGE ? NQUAD * N1 * NT + 2 * N1 : NQUAD * NQ * NP;
+  static constexpr int NKL = (N + 1) * (N + 2) / 2;                   // pyramid (level k, index l <= k)
+  // tet: lattice lift; pyramid: EF [4][NKL] | PF [4][NFN][NKL] | PF2 [4][NFN][NKL]; wedge: Vtl [2][NFN][NT]
+  static constexpr int TN = T == DG_WEDGE ? NTRI * NFN * NT
+                            : T == DG_PYR ? NTRI * NKL + 2 * NTRI * NFN * NKL : NTRI * NFN * NP;
+  // pyramid: LA [N1][NKL] | GC [N1]; wedge: Ve [3][N1][NT] | V1e [2][N1]
+  static constexpr int TQ = T == DG_WEDGE ? NQUAD * N1 * NT + 2 * N1 : T == DG_PYR ? N1 * NKL + N1 : 0;
   static constexpr bool LAT = T != DG_WEDGE;                            // lattice-point face exchange
-  static constexpr int TN2 = T == DG_PYR ? NTRI * NFN * NP : 0;         // pyramid: lift of lattice fluxes
+  static constexpr int TN2 = 0;
   static constexpr int NFX = LAT ? NTRI * NFN + NQUAD * NQ : NF * NQ;   // face flux points
   static constexpr int OPS = VOL + TN + TQ + TN2 + NQ * NFN;
   static constexpr int IOPS = 12 * NFN + 8 * NQ + (T == DG_TET ? 4 * NFN : 0);
@@ -50,7 +52,8 @@ struct G2 {
   static constexpr int IOPS_B = ((IOPS * 4 + 15) / 16) * 16;
   // per-warp float4 buffers: q4, W4 (wedge: Y/Z pair + X1,X2), F4, G4 (local-order moments),
   // V4 (canonical lattice values)
-  static constexpr int WB = NP + (T == DG_WEDGE ? 2 * NT * N1 + 2 * NC : NP) + NF * NQ + 2 * NTRI * NFN;
+  static constexpr int WB = NP + (T == DG_WEDGE ? 2 * NT * N1 + 2 * NC : NP) + NF * NQ + 2 * NTRI * NFN +
+                            (T == DG_PYR ? NKL * N1 + NQ : 0);
   static constexpr int SMEM = OPS_B + IOPS_B + NW * WB * 16;
   static constexpr int R = (NP + 31) / 32;
 };
@@ -96,13 +99,18 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
   const float* wq = D1 + C::N1 * C::N1;                          // wedge weights [NQ][N1]
   const float* Tn = sop + C::VOL;                                // [NTRI][NFN][NP]
   const float* Tq = Tn + C::TN;                                  // [NQUAD][NQ][NP]
-  const float* Tn2 = Tq + C::TQ;                                 // pyramid [NTRI][NFN][NP]
-  const float* E = Tn2 + C::TN2;                                 // [NQ][NFN]
+  const float* E = Tq + C::TQ;                                   // [NQ][NFN]
   constexpr bool LAT = C::LAT;
   constexpr int NFX = C::NFX, NLT = NTRI * NFN;
   const float* Vtl = Tn;                                         // wedge [2][NFN][NT]
   const float* Ve = Tq;                                          // wedge [3][N1][NT]
   const float* V1e = Tq + NQUAD * C::N1 * C::NT;                 // wedge [2][N1]
+  constexpr int NKL = C::NKL;
+  const float* EF = Tn;                                          // pyramid [4][NKL]
+  const float* PF = Tn + NTRI * NKL;                             // pyramid [4][NFN][NKL]
+  const float* PF2 = PF + NTRI * NFN * NKL;                      // pyramid [4][NFN][NKL]
+  const float* LA = Tq;                                          // pyramid [N1][NKL]
+  const float* GC = Tq + C::N1 * NKL;                            // pyramid [N1]
   const int* tperm = sio;                                        // [6][NFN] local lattice -> canonical
   const int* qperm = sio + 12 * NFN;                             // [8][NQ] local GL point -> canonical
   const int* fnode = qperm + 8 * NQ;                             // tet [4][NFN]
@@ -115,6 +123,8 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
   float4* F4 = W4 + (T == DG_WEDGE ? 2 * C::NT * C::N1 + 2 * NC : NP);
   float4* G4 = F4 + NF * NQ;
   float4* V4 = G4 + NTRI * NFN;
+  float4* PZB = V4 + NTRI * NFN;                                 // pyramid [NKL][N1]
+  float4* PTQB = PZB + NKL * C::N1;                              // pyramid [NQ] base traces
 
   for (int64_t li = (int64_t)blockIdx.x * NW + warp; li < A.K; li += (int64_t)gridDim.x * NW) {
     const int64_t e = A.elist ? (int64_t)A.elist[li] : li;
@@ -167,10 +177,59 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
       }
     };
     // canonical lattice values of the triangle faces (V4) from q4
+    // pyramid, factorised over the levels of the semi-nodal basis: triangle face ti fixes
+    // b (ti even) or a (ti odd); Y_ti[k][l] = sum over the fixed direction of its factor times q
+    // (into G4), then lattice values (local order) = sum_kl PF[x][kl] Y_ti[kl]; base:
+    // Z[k][i][q] = GC_k sum_j LA[q][k][j] q_kji (PZB), traces = sum_kl LA[p][kl] Z[kl][q] (PTQB)
+    auto pyr_face_values = [&]() {
+      constexpr int PN1 = C::N1;
+      for (int x = lane; x < NTRI * NKL + NKL * PN1; x += 32) {
+        const bool face = x < NTRI * NKL;
+        const int kl = face ? x % NKL : (x - NTRI * NKL) / PN1;
+        int k = 0;
+        while ((k + 1) * (k + 2) / 2 <= kl) ++k;
+        const int l = kl - k * (k + 1) / 2, k1 = k + 1, off = k * (k + 1) * (2 * k + 1) / 6, kb = k * (k + 1) / 2;
+        float4 v = f4(0.f, 0.f, 0.f, 0.f);
+        if (face) {
+          const int ti = x / NKL;
+          const float* ef = EF + ti * NKL + kb;
+          if (ti & 1) {
+            for (int i = 0; i < k1; ++i) f4acc(v, ef[i], q4[off + l * k1 + i]);
+          } else {
+            for (int j = 0; j < k1; ++j) f4acc(v, ef[j], q4[off + j * k1 + l]);
+          }
+          G4[x] = v;
+        } else {
+          const float* la = LA + ((x - NTRI * NKL) % PN1) * NKL + kb;
+          for (int j = 0; j < k1; ++j) f4acc(v, la[j], q4[off + j * k1 + l]);
+          const float g = GC[k];
+          PZB[x - NTRI * NKL] = f4(g * v.x, g * v.y, g * v.z, g * v.w);
+        }
+      }
+      __syncwarp();
+      for (int x = lane; x < NTRI * NFN + NQ; x += 32) {
+        float4 v = f4(0.f, 0.f, 0.f, 0.f);
+        if (x < NTRI * NFN) {
+          const float* pf = PF + x * NKL;
+          const float4* y = G4 + (x / NFN) * NKL;
+#pragma unroll 5
+          for (int kl = 0; kl < NKL; ++kl) f4acc(v, pf[kl], y[kl]);
+          V4[x] = v;
+        } else {
+          const int idx = x - NTRI * NFN, pp = idx % PN1, qq = idx / PN1;
+          const float* la = LA + pp * NKL;
+#pragma unroll 5
+          for (int kl = 0; kl < NKL; ++kl) f4acc(v, la[kl], PZB[kl * PN1 + qq]);
+          PTQB[idx] = v;
+        }
+      }
+    };
     // (tet, pyramid: local order; the wedge also fills the quad-face traces)
     auto lattice_values = [&]() {
       if constexpr (T == DG_WEDGE) {
         wedge_face_values();
+      } else if constexpr (T == DG_PYR) {
+        pyr_face_values();
       } else {
         for (int x = lane; x < NTRI * NFN; x += 32) {
           float4 v;
@@ -197,6 +256,8 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
         for (int n = 0; n < NFN; ++n) f4acc(tr, er[n], vc[n]);
       } else if (T == DG_WEDGE) {
         tr = TQB[quad_of<T>(f) * NQ + idx];
+      } else if (T == DG_PYR) {
+        tr = PTQB[idx];
       } else {
         const float* row = Tq + (quad_of<T>(f) * NQ + idx) * NP;
         #pragma unroll 4
@@ -436,12 +497,46 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
         }
         __syncwarp();
       }
+      if (T == DG_PYR) {
+        // H_ti[kl] = sum_n PF2[ti][n][kl] F_ti[n] (G4); Wb[(k,j)][p] = sum_q LA[q][(k,j)] F_base[p, q] (PZB)
+        constexpr int PN1 = C::N1;
+        for (int x = lane; x < NTRI * NKL + NKL * PN1; x += 32) {
+          float4 v = f4(0.f, 0.f, 0.f, 0.f);
+          if (x < NTRI * NKL) {
+            const int ti = x / NKL, kl = x % NKL;
+            const float* pf2 = PF2 + ti * NFN * NKL + kl;
+#pragma unroll 5
+            for (int n = 0; n < NFN; ++n) f4acc(v, pf2[n * NKL], F4[ti * NFN + n]);
+            G4[x] = v;
+          } else {
+            const int y = x - NTRI * NKL, kl = y / PN1, pp = y % PN1;
+#pragma unroll
+            for (int qq = 0; qq < PN1; ++qq) f4acc(v, LA[qq * NKL + kl], F4[NLT + pp + PN1 * qq]);
+            PZB[y] = v;
+          }
+        }
+        __syncwarp();
+      }
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int n = lane + 32 * r;
         if (n >= NP) break;
         float4 sum = f4(0.f, 0.f, 0.f, 0.f);
-        if (T == DG_WEDGE) {   // node (mt, j): triangle faces, then quad faces (edge x 1D)
+        if (T == DG_PYR) {   // node (k, j, i): four triangle faces, then the base
+          constexpr int PN1 = C::N1;
+          int k = 0;
+          while ((k + 1) * (k + 2) * (2 * k + 3) / 6 <= n) ++k;
+          const int r0 = n - k * (k + 1) * (2 * k + 1) / 6, j = r0 / (k + 1), i = r0 % (k + 1);
+          const int kb = k * (k + 1) / 2;
+          f4acc(sum, EF[0 * NKL + kb + j], G4[0 * NKL + kb + i]);
+          f4acc(sum, EF[1 * NKL + kb + i], G4[1 * NKL + kb + j]);
+          f4acc(sum, EF[2 * NKL + kb + j], G4[2 * NKL + kb + i]);
+          f4acc(sum, EF[3 * NKL + kb + i], G4[3 * NKL + kb + j]);
+          float4 bsum = f4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int pp = 0; pp < PN1; ++pp) f4acc(bsum, LA[pp * NKL + kb + i], PZB[(kb + j) * PN1 + pp]);
+          f4acc(sum, GC[k], bsum);
+        } else if (T == DG_WEDGE) {   // node (mt, j): triangle faces, then quad faces (edge x 1D)
           const int mt = n % WNT, j = n / WNT;
           f4acc(sum, V1e[j], HB[mt]);
           f4acc(sum, V1e[WN1 + j], HB[WNT + mt]);
@@ -450,18 +545,9 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
 #pragma unroll
             for (int ia = 0; ia < WN1; ++ia)
               f4acc(sum, Ve[(qf * WN1 + ia) * WNT + mt], PB[(qf * WN1 + ia) * WN1 + j]);
-        } else {
-          // triangle faces: lattice-point fluxes (LAT: Lf / Tn2 hold the face mass)
-          const float* Lt = T == DG_PYR ? Tn2 : Tn;
+        } else {   // tet: lattice-point fluxes (Lf holds the face mass)
 #pragma unroll 4
-          for (int x = 0; x < NLT; ++x) f4acc(sum, Lt[x * NP + n], F4[x]);
-#pragma unroll
-          for (int qi = 0; qi < NQUAD; ++qi) {
-            const float* col = Tq + qi * NQ * NP + n;
-            const float4* fr = F4 + NLT + qi * NQ;
-#pragma unroll 5
-            for (int lp = 0; lp < NQ; ++lp) f4acc(sum, col[lp * NP], fr[lp]);
-          }
+          for (int x = 0; x < NLT; ++x) f4acc(sum, Tn[x * NP + n], F4[x]);
         }
         float iM = 1.f;
         if (T == DG_TET) iM = 1.f / A.geo[e * 12 + 9];

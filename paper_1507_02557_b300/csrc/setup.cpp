@@ -909,8 +909,8 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
 
         // ---- orientation-free operators (kernels_gen2.cu); float layout:
         //  tet:   DV4[Np][Np] (D^r,D^s,D^t,0) | Lf[4][nfn][Np] = Mhat^{-1} face-node columns x Mf | E[nq][nfn]
-        //  pyr:   DV4[Np][Np] | Tn[4][nfn][Np] (tri faces 1..4) | Tq[nq][Np] (base) | Tn2[4][nfn][Np] = Mf Tn |
-        //         E[nq][nfn]
+        //  pyr:   DV4[Np][Np] | EF[4][nkl] | PF[4][nfn][nkl] | PF2[4][nfn][nkl] | LA[n1][nkl] | GC[n1] | E[nq][nfn]
+        //         (nkl = (N+1)(N+2)/2 level-index pairs (k, l <= k))
         //  wedge: Vt4[nq][ntri] | V1[n1][n1] | D1[n1][n1] | w[nq][n1] | Vtl[2][nfn][ntri] | Ve[3][n1][ntri] |
         //         V1e[2][n1] | E[nq][nfn]
         //  int layout: tperm[6][nfn] | tinv[6][nfn] | qperm[8][nq] | (tet) fnode[4][nfn]
@@ -1079,45 +1079,57 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
               for (int j = 0; j < n1; ++j)
                 o2.push_back((float)(std::sqrt((2.0 * j + 1) / 2) * jacobi(j, 0, 0, f == 0 ? -1.0 : 1.0)));
           }
-          for (int f = 0; f < nf && t != WEDGE; ++f) {
-            if (face_nverts(t, f) != 3) continue;
-            for (int l2 = 0; l2 <= N; ++l2)
-              for (int l1 = 0; l1 + l2 <= N; ++l1) {
-                double rst[3];
-                lattice_rst(f, l1, l2, rst);
-                B[t].eval(rst, phi.data(), nullptr);
-                for (int i = 0; i < Np; ++i) o2.push_back((float)phi[i]);
-              }
-          }
-          static const int ident[4] = {0, 1, 2, 3};
-          for (int f = 0; f < nf && t != WEDGE; ++f) {
-            if (face_nverts(t, f) != 4) continue;
-            for (int q = 0; q < nq; ++q) {
-              double rst[3], d1[3], d2[3];
-              face_point(t, f, ident, qpts[2 * q], qpts[2 * q + 1], rst, d1, d2);
-              B[t].eval(rst, phi.data(), nullptr);
-              for (int i = 0; i < Np; ++i) o2.push_back((float)phi[i]);
-            }
-          }
           if (t == PYR) {
-            // lift of lattice-point fluxes on the triangle faces: Tn2[f][n][i] = sum_m Mf[n][m] phi_i(lattice_m)
-            std::vector<double> tn(nfn * Np);
-            for (int f = 0; f < nf; ++f) {
-              if (face_nverts(t, f) != 3) continue;
+            // factorised face evaluations of the semi-nodal basis
+            //   phi_kji = [l^k_i(a)/sqrt(w^k_i)] [l^k_j(b)/sqrt(w^k_j)] [h^k P^{(2k+3,0)}_{N-k}(t)/sqrt(gamma_k)]:
+            // triangle face f = 1..4 fixes b = -1, a = +1, b = +1, a = -1; per (k, l), l <= k:
+            //   EF[4][nkl]        the fixed coordinate's factor
+            //   PF[4][nfn][nkl]   at lattice node x of the face: the free coordinate's factor times the t factor
+            //   PF2[4][nfn][nkl]  = Mf PF (lift of lattice-point fluxes)
+            // base (t = -1, h = 1, local GL points (a_p, b_q)):
+            //   LA[n1][nkl]       l^k_l(x_p)/sqrt(w^k_l);   GC[n1]  P^{(2k+3,0)}_{N-k}(-1)/sqrt(gamma_k)
+            const int nkl = n1 * (n1 + 1) / 2;
+            std::vector<double> tmp(n1);
+            auto lag = [&](int k, double x) {
+              lagrange(B[t].lev_x[k], x, tmp.data(), nullptr);
+              for (int l = 0; l <= k; ++l) tmp[l] /= std::sqrt(B[t].lev_w[k][l]);
+            };
+            const bool fixa[4] = {false, true, false, true};
+            const double fixv[4] = {-1.0, 1.0, 1.0, -1.0};
+            for (int ti = 0; ti < 4; ++ti)
+              for (int k = 0; k <= N; ++k) {
+                lag(k, fixv[ti]);
+                for (int l = 0; l <= k; ++l) o2.push_back((float)tmp[l]);
+              }
+            std::vector<double> pf(4 * nfn * nkl);
+            for (int ti = 0; ti < 4; ++ti)
               for (int l2 = 0; l2 <= N; ++l2)
                 for (int l1 = 0; l1 + l2 <= N; ++l1) {
                   double rst[3];
-                  lattice_rst(f, l1, l2, rst);
-                  B[t].eval(rst, phi.data(), nullptr);
-                  for (int i = 0; i < Np; ++i) tn[lattice_index(N, l1, l2) * Np + i] = phi[i];
+                  lattice_rst(ti + 1, l1, l2, rst);
+                  const double h = 0.5 * (1 - rst[2]);
+                  const double a = h > 1e-14 ? (1 + rst[0]) / h - 1 : 0.0, b = h > 1e-14 ? (1 + rst[1]) / h - 1 : 0.0;
+                  const int x = lattice_index(N, l1, l2);
+                  for (int k = 0; k <= N; ++k) {
+                    const double tk = std::pow(h, k) * jacobi(N - k, 2 * k + 3, 0, rst[2]) / std::sqrt(B[t].gam[k]);
+                    lag(k, fixa[ti] ? b : a);
+                    for (int l = 0; l <= k; ++l) pf[(ti * nfn + x) * nkl + k * (k + 1) / 2 + l] = tmp[l] * tk;
+                  }
                 }
+            for (double v : pf) o2.push_back((float)v);
+            for (int ti = 0; ti < 4; ++ti)
               for (int n = 0; n < nfn; ++n)
-                for (int i = 0; i < Np; ++i) {
+                for (int kl = 0; kl < nkl; ++kl) {
                   double v = 0.0;
-                  for (int mm = 0; mm < nfn; ++mm) v += Mf[n * nfn + mm] * tn[mm * Np + i];
+                  for (int mm = 0; mm < nfn; ++mm) v += Mf[n * nfn + mm] * pf[(ti * nfn + mm) * nkl + kl];
                   o2.push_back((float)v);
                 }
-            }
+            for (int pp = 0; pp < n1; ++pp)
+              for (int k = 0; k <= N; ++k) {
+                lag(k, gx[pp]);
+                for (int l = 0; l <= k; ++l) o2.push_back((float)tmp[l]);
+              }
+            for (int k = 0; k <= N; ++k) o2.push_back((float)(jacobi(N - k, 2 * k + 3, 0, -1.0) / std::sqrt(B[t].gam[k])));
           }
         }
         for (double v : E) o2.push_back((float)v);
