@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
 // t-face traces come from registers; r/s-derivatives and r/s-face traces read the
 // element's nodes as float4 (p,u,v,w) from shared memory.  Only warp-level
 // synchronisation after the start of the block.
-__constant__ float c_hexw[5][64];   // per N: D1[n1*n1] (row = node), Vm[n1], Vp[n1], w[n1], r[n1]
+__constant__ float c_hexw[5][64];   // per N: D1[n1*n1] (row = node), Vm[n1], Vp[n1], w[n1], r[n1], 1/w[n1]
 
 cudaError_t upload_hex_constants(int N, const float* hc, int count) {
   if (N < 1 || N > 4 || count > 64) return cudaSuccess;
@@ -314,7 +314,7 @@ __device__ __forceinline__ void hexw_face_geom(const float* g, const float* rr, 
   }
   cross3(u, v, nv);
   Js = sqrtf(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
-  const float inv = sg / Js;
+  const float inv = sg * __frcp_rn(Js);
   nv[0] *= inv;
   nv[1] *= inv;
   nv[2] *= inv;
@@ -459,6 +459,7 @@ __global__ void __launch_bounds__(128, DG_HEXP_MINB) hexw_kernel(Args A, const _
   const float* Vp = Vm + n1;
   const float* W1 = Vp + n1;
   const float* R1 = W1 + n1;
+  const float* iW = R1 + n1;
 
   for (int x = threadIdx.x; x < 8 * NQ; x += blockDim.x) s_perm[x] = A.perm[x];
   if (TMA && lane == 0) {
@@ -618,7 +619,7 @@ __global__ void __launch_bounds__(128, DG_HEXP_MINB) hexw_kernel(Args A, const _
       }
     }
     float rhs[4][n1];
-    float Jn[n1];
+    float iJn[n1];   // 1/J at the column's nodes
 
     if (MODE != MODE_TRACE && act) {
       // ---- volume: collocated strong form (Alg. hex_vol), metrics built along the column
@@ -661,8 +662,8 @@ __global__ void __launch_bounds__(128, DG_HEXP_MINB) hexw_kernel(Args A, const _
           g2[d] = G2a[d] + t * (G2b[d] + t * G2c[d]);
         }
         const float J = (Ar[0] + t * Br[0]) * g0[0] + (Ar[1] + t * Br[1]) * g0[1] + (Ar[2] + t * Br[2]) * g0[2];
-        Jn[k] = J;
-        const float iJ = 1.f / J;
+        const float iJ = __frcp_rn(J);
+        iJn[k] = iJ;
         float4 dr = make_float4(0.f, 0.f, 0.f, 0.f), ds = dr;
 #pragma unroll
         for (int m = 0; m < n1; ++m) {
@@ -727,7 +728,7 @@ __global__ void __launch_bounds__(128, DG_HEXP_MINB) hexw_kernel(Args A, const _
           }
           const float ta = s_tau[f];
           float fp, fu;
-          flux(nb < 0, tr.x, unm, P, UN, A.tau_scale * ta, A.tau_scale / ta, false, fp, fu);
+          flux(nb < 0, tr.x, unm, P, UN, A.tau_scale * ta, A.tau_scale * __frcp_rn(ta), false, fp, fu);
           const float wg = W1[i] * W1[j] * Js;
           const float4 Fv = make_float4(wg * fp, wg * fu * nv[0], wg * fu * nv[1], wg * fu * nv[2]);
           if (ax < 2) s_F[f * NQ + col] = Fv;
@@ -751,7 +752,7 @@ __global__ void __launch_bounds__(128, DG_HEXP_MINB) hexw_kernel(Args A, const _
           sum = f4fma(Vp[j], F3, sum);
           sum = f4fma(Vm[k], F45[0], sum);
           sum = f4fma(Vp[k], F45[1], sum);
-          const float iM = 1.f / (W1[i] * W1[j] * W1[k] * Jn[k]);
+          const float iM = iW[i] * iW[j] * iW[k] * iJn[k];
           rhs[0][k] += iM * sum.x;
           rhs[1][k] += c2 * iM * sum.y;
           rhs[2][k] += c2 * iM * sum.z;

@@ -737,6 +737,7 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
         for (int i = 0; i < n1; ++i) hc.push_back((float)l[i]);
         for (int i = 0; i < n1; ++i) hc.push_back((float)B[t].w1[i]);
         for (int i = 0; i < n1; ++i) hc.push_back((float)B[t].r1[i]);
+        for (int i = 0; i < n1; ++i) hc.push_back((float)(1.0 / B[t].w1[i]));
         m->hexc = upload(hc, owned);
         if (!g_host_only && dgk::upload_hex_constants(N, hc.data(), (int)hc.size()) != cudaSuccess)
           throw SetupError(DG_ECUDA, "constant upload failed");
