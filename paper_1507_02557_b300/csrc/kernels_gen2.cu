@@ -34,7 +34,8 @@ struct G2 {
   static constexpr int NTRI = T == DG_WEDGE ? 2 : 4;
   static constexpr int NQUAD = NF - NTRI;
   static constexpr int NC = T == DG_WEDGE ? (N + 1) * (N + 1) * (N + 1) : 0;
-  static constexpr int NW = 16;                                        // warps per block
+  // warps per block (one block per SM): the pyramid's 22 fill the shared memory at N = 4
+  static constexpr int NW = T == DG_PYR ? 22 : 16;
   static constexpr int N1 = N + 1, NT = NFN;                            // wedge: 1D points, triangle modes
   static constexpr int VOL = T == DG_WEDGE ? NQ * NT * 4 + 2 * N1 * N1 + NQ * N1 : NP * NP * 4;
   static constexpr int NKL = (N + 1) * (N + 2) / 2;                   // pyramid (level k, index l <= k)
