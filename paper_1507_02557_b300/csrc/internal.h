@@ -75,6 +75,7 @@ struct dg_mesh {
   std::vector<double> dtK[4];
   std::vector<double> tet_mhat;  // host copy of the reference tet mass (energy)
   float* tet_mhat_dev = nullptr;
+  float* tet_chol_dev = nullptr;   // R with M_hat = R^T R (upper triangular), energy
   // multi-rate (nlevels = 2): per-level element lists, RHS history, start-up flag
   int nlevels = 1;
   dgk::Sel all, lev[2];           // lev[0] = coarse (level 1), lev[1] = fine (level 2)

@@ -1194,59 +1194,54 @@ __global__ void __launch_bounds__(128) gen_kernel(Args A) {
 }
 
 // ============================================================================ energy
-// E_K = 1/2 (p^T M p + (1/c^2) sum_d u_d^T M u_d), FP64.  Grid-stride blocks: the element's
-// state (and the tet reference mass) in shared memory, one atomic per block.
+// E = 1/2 sum_K (p^T M p + (1/c^2) sum_d u_d^T M u_d).  Flat grid-stride loop over (element,
+// node): FP32 per-node terms (hex w J, pyramid J, wedge 1; tet: row n of R q with M_hat = R^T R,
+// so p^T M p = J |R p|^2), FP64 accumulation, one atomic per block.
 template <int T, int N>
-__global__ void __launch_bounds__(128) energy_kernel(Args A, const float* mhat, double* acc) {
+__global__ void __launch_bounds__(256) energy_kernel(Args A, const float* chol, double* acc) {
   constexpr int NP = T == DG_HEX ? (N + 1) * (N + 1) * (N + 1) : np_of(T, N);
   constexpr int n1 = N + 1;
-  __shared__ double s_red[128];
-  __shared__ float s_geo[24];
-  __shared__ float s_q[4][NP];
-  constexpr bool MSH = T == DG_TET && NP * NP * 8 <= 32768;   // tet reference mass in shared memory
-  __shared__ double s_m[MSH ? NP * NP : 1];
+  __shared__ double s_red[256];
   const int tid = threadIdx.x;
-  if (MSH)
-    for (int x = tid; x < NP * NP; x += blockDim.x) s_m[x] = mhat[x];
-  const double* Mh = MSH ? s_m : nullptr;
   double loc = 0.0;
-  for (int64_t e = blockIdx.x; e < A.K; e += gridDim.x) {
-    const int64_t base = A.dof_off + e * NP;
-    __syncthreads();   // previous element's reads of s_q / s_geo are done
-    if (T == DG_HEX && tid < 24) s_geo[tid] = A.geo[e * 24 + tid];
-    for (int x = tid; x < 4 * NP; x += blockDim.x) s_q[x / NP][x % NP] = A.q[(x / NP) * A.ndof + base + x % NP];
-    __syncthreads();
-    const double ic2 = 1.0 / (double)A.c2[e];
-    for (int n = tid; n < NP; n += blockDim.x) {
-      const double qv[4] = {s_q[0][n], s_q[1][n], s_q[2][n], s_q[3][n]};
-      const double wsq = qv[0] * qv[0] + ic2 * (qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]);
+  const int64_t total = (int64_t)A.K * NP;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + tid; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = x / NP;
+    const int n = (int)(x % NP);
+    const int64_t b = A.dof_off + e * NP;
+    const float ic2 = 1.f / A.c2[e];
+    float term;
+    if (T == DG_TET) {
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int m = n; m < NP; ++m) {
+        const float r = __ldg(chol + n * NP + m);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) c[f] = fmaf(r, A.q[f * A.ndof + b + m], c[f]);
+      }
+      term = A.geo[e * 12 + 9] * (c[0] * c[0] + ic2 * (c[1] * c[1] + c[2] * c[2] + c[3] * c[3]));
+    } else {
+      const float qv[4] = {A.q[b + n], A.q[A.ndof + b + n], A.q[2 * A.ndof + b + n], A.q[3 * A.ndof + b + n]};
+      const float wsq = qv[0] * qv[0] + ic2 * (qv[1] * qv[1] + qv[2] * qv[2] + qv[3] * qv[3]);
       if (T == DG_HEX) {
+        const float* g = A.geo + e * 24;
         const float* hc = A.hexc;
         const int i = n % n1, j = (n / n1) % n1, k = n / (n1 * n1);
         float xr[3], xs[3], xt[3], g0[3];
-        hex_jac(s_geo, hc[n1 * n1 + 3 * n1 + i], hc[n1 * n1 + 3 * n1 + j], hc[n1 * n1 + 3 * n1 + k], xr, xs, xt);
+        hex_jac(g, hc[n1 * n1 + 3 * n1 + i], hc[n1 * n1 + 3 * n1 + j], hc[n1 * n1 + 3 * n1 + k], xr, xs, xt);
         cross3(xs, xt, g0);
-        const double J = (double)xr[0] * g0[0] + (double)xr[1] * g0[1] + (double)xr[2] * g0[2];
-        const double w = (double)hc[n1 * n1 + 2 * n1 + i] * hc[n1 * n1 + 2 * n1 + j] * hc[n1 * n1 + 2 * n1 + k];
-        loc += w * J * wsq;
+        const float J = xr[0] * g0[0] + xr[1] * g0[1] + xr[2] * g0[2];
+        term = hc[n1 * n1 + 2 * n1 + i] * hc[n1 * n1 + 2 * n1 + j] * hc[n1 * n1 + 2 * n1 + k] * J * wsq;
       } else if (T == DG_WEDGE) {
-        loc += wsq;
-      } else if (T == DG_PYR) {
-        loc += (double)A.geo[(e * NP + n) * 10 + 9] * wsq;
+        term = wsq;
       } else {
-        double sm = 0.0;
-        for (int m = 0; m < NP; ++m) {
-          double o = (double)s_q[0][m] * qv[0];
-          for (int f = 1; f < 4; ++f) o += ic2 * (double)s_q[f][m] * qv[f];
-          sm += (MSH ? Mh[n * NP + m] : (double)__ldg(mhat + n * NP + m)) * o;
-        }
-        loc += (double)A.geo[e * 12 + 9] * sm;
+        term = A.geo[(e * NP + n) * 10 + 9] * wsq;
       }
     }
+    loc += (double)term;
   }
   s_red[tid] = loc;
   __syncthreads();
-  for (int st = 64; st > 0; st >>= 1) {
+  for (int st = 128; st > 0; st >>= 1) {
     if (tid < st) s_red[tid] += s_red[tid + st];
     __syncthreads();
   }
@@ -1500,14 +1495,17 @@ cudaError_t launch_energy(dg_mesh* m, const float* q, double* acc) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  auto egrid = [&](int K) { return (unsigned)(K < 8 * sms ? K : 8 * sms); };   // 8 blocks per SM
+  auto egrid = [&](int t) {   // blocks of 256 (element, node) pairs, at most 8 per SM
+    const int64_t need = ((int64_t)A[t].K * m->td[t].Np + 255) / 256;
+    return (unsigned)(need < 8 * sms ? need : 8 * sms);
+  };
   switch (m->N) {
 #define DG_CASE(NN)                                                                                  \
   case NN:                                                                                           \
-    if (A[0].K) energy_kernel<DG_HEX, NN><<<egrid(A[0].K), 128, 0, s>>>(A[0], nullptr, acc);         \
-    if (A[1].K) energy_kernel<DG_WEDGE, NN><<<egrid(A[1].K), 128, 0, s>>>(A[1], nullptr, acc);       \
-    if (A[2].K) energy_kernel<DG_PYR, NN><<<egrid(A[2].K), 128, 0, s>>>(A[2], nullptr, acc);         \
-    if (A[3].K) energy_kernel<DG_TET, NN><<<egrid(A[3].K), 128, 0, s>>>(A[3], m->tet_mhat_dev, acc); \
+    if (A[0].K) energy_kernel<DG_HEX, NN><<<egrid(0), 256, 0, s>>>(A[0], nullptr, acc);              \
+    if (A[1].K) energy_kernel<DG_WEDGE, NN><<<egrid(1), 256, 0, s>>>(A[1], nullptr, acc);            \
+    if (A[2].K) energy_kernel<DG_PYR, NN><<<egrid(2), 256, 0, s>>>(A[2], nullptr, acc);              \
+    if (A[3].K) energy_kernel<DG_TET, NN><<<egrid(3), 256, 0, s>>>(A[3], m->tet_chol_dev, acc);      \
     break;
     DG_CASE(1) DG_CASE(2) DG_CASE(3) DG_CASE(4) DG_CASE(5) DG_CASE(6)
 #undef DG_CASE

@@ -800,6 +800,21 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
           Minv = I;
           std::vector<float> mh(M.begin(), M.end());
           m->tet_mhat_dev = upload(mh, owned);
+          // Cholesky factor M = R^T R (R upper triangular): the energy kernel takes p^T M p = |R p|^2
+          std::vector<double> R(Np * Np, 0.0);
+          for (int i = 0; i < Np; ++i) {
+            double d = M[i * Np + i];
+            for (int k = 0; k < i; ++k) d -= R[k * Np + i] * R[k * Np + i];
+            if (!(d > 0)) throw SetupError(DG_EINVAL, "tet reference mass not positive definite");
+            R[i * Np + i] = std::sqrt(d);
+            for (int j = i + 1; j < Np; ++j) {
+              double v = M[i * Np + j];
+              for (int k = 0; k < i; ++k) v -= R[k * Np + i] * R[k * Np + j];
+              R[i * Np + j] = v / R[i * Np + i];
+            }
+          }
+          std::vector<float> rf(R.begin(), R.end());
+          m->tet_chol_dev = upload(rf, owned);
         }
         for (int f = 0; f < nf; ++f) {
           int fnv = face_nverts(t, f);
