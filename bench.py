@@ -143,7 +143,7 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-HEX_MRC_DRAM_BYTES_PER_ELEMENT = 969425408 / 73728   # 550,659,072 read + 418,766,336 written
+HEX_MRC_DRAM_BYTES_PER_ELEMENT = 969658880 / 73728   # 550,616,064 read + 419,042,816 written
 
 
 def hex_alg_bytes(N):
