@@ -128,6 +128,16 @@ class Clocks:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The largest value over all ranks (the job's time is its slowest replica's)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -222,11 +232,7 @@ def main():
         torch.cuda.synchronize()
 
     def max_ms(ms):
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-        return ms
+        return max_over_ranks(ms, dist, "cuda")
 
     # ---- single-rate LSRK(5,4): fused stage kernels
     g1 = dg.Mesh(mesh, ORDER, stream=stream.cuda_stream, nlevels=1)
