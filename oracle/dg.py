@@ -41,14 +41,17 @@ class DGOracle:
 
     ``tau_scale`` multiplies both penalties (1 = upwind, 0 = central flux).
     ``pyr_form`` is ``"skew"`` (Alg. pyr_vol, default) or ``"strong"``.
+    ``hex_basis`` is ``"gl"`` (default) or ``"gll"``: the SEM hexahedron of Sec. 2.1.1 (nodes
+    and collocated mass at the GLL points), with GLL points on every quadrilateral face.
     """
 
-    def __init__(self, mesh, N, tau_scale=1.0, pyr_form="skew"):
+    def __init__(self, mesh, N, tau_scale=1.0, pyr_form="skew", hex_basis="gl"):
         self.mesh = mesh
         self.N = N
         self.tau_scale = float(tau_scale)
         self.pyr_form = pyr_form
-        self.geo = MeshGeometry(mesh, N)
+        self.hex_basis = hex_basis
+        self.geo = MeshGeometry(mesh, N, lobatto=hex_basis == "gll")
         self.els = self.geo.els
         self.K = mesh.nelem
         self.Np = [el.Np for el in self.els]

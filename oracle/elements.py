@@ -216,8 +216,11 @@ class Wedge:
 
     @staticmethod
     def _abc(rst):
+        # collapsed coordinate of the triangle (r, t); at its collapsed vertex t = 1 every mode
+        # with i >= 1 carries ((1 - t)/2)^i, so the limit is taken at a = 0 there (values only)
         r, s, t = rst.T
-        a = 2 * (1 + r) / (1 - t) - 1
+        h = 1 - t
+        a = np.where(h > 1e-14, 2 * (1 + r) / np.where(h > 1e-14, h, 1.0) - 1, 0.0)
         return a, s, t
 
     def _raw(self, rst):

@@ -208,3 +208,26 @@ def test_watchdog_reports_timeout(lib):
     g.set_state(random_state(g.ndof, 1).astype(np.float32), on_device=False)
     g.step(1)
     assert np.isfinite(g.energy())
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_error_against_exact_mode_matches_oracle(lib, N):
+    """FP32 state with the tensor-core (TF32x3) tets and FP32 SIMT kernels elsewhere: the L2
+    error against the exact standing mode after LSRK steps to t = 0.02 equals the FP64 oracle's
+    (the discretisation error dominates; rounding stays far below it)."""
+    from oracle.dg import standing_mode
+    m = small_hybrid_mesh()
+    o = DGOracle(m, N)
+    q0 = o.project(standing_mode, 0.0)
+    g = lib.Mesh(m, N)
+    T = 0.02
+    n = int(np.ceil(T / g.timestep()))
+    dt = T / n
+    g.set_state(q0.astype(np.float32), on_device=False)
+    g.step(n, dt)
+    got = g.get_state(np.zeros(q0.shape, np.float32), on_device=False).astype(np.float64)
+    q = q0.copy()
+    for _ in range(n):
+        q = o.lsrk_step(q, dt)
+    e_gpu, e_orc = o.l2_error(got, standing_mode, T), o.l2_error(q, standing_mode, T)
+    assert abs(e_gpu - e_orc) <= 0.01 * e_orc + 1e-6, (e_gpu, e_orc)

@@ -22,13 +22,22 @@ def energy_rate(dg, q):
     return float(np.sum(q * dg.mass_apply(dg.rhs(q)) * dg.material_weights()))
 
 
+@pytest.fixture(scope="module")
+def mesh_affine_c():
+    """Undisplaced (affine) hybrid mesh with a wave-speed jump: the SEM hexahedron's GLL
+    collocation integrates its (constant) metric terms exactly there."""
+    return layered_mesh(3, 3, 5, "HWHTK", seed=3, amp=0.0, c_of_layer=lambda k: 1.0 if k % 2 == 0 else 1.5)
+
+
 @pytest.mark.parametrize("N", [1, 2, 3])
-@pytest.mark.parametrize("which", ["mesh", "mesh_c"])
-def test_energy_identity(N, which, request):
-    """Eq. (sym): U^T A U = 0 for central flux and = -1/2 sum int (tau_p[p]^2 + tau_u[u_n]^2) for upwind."""
+@pytest.mark.parametrize("which,hex_basis", [("mesh", "gl"), ("mesh_c", "gl"), ("mesh_affine_c", "gll")])
+def test_energy_identity(N, which, hex_basis, request):
+    """Eq. (sym): U^T A U = 0 for central flux and = -1/2 sum int (tau_p[p]^2 + tau_u[u_n]^2) for
+    upwind.  SEM hexahedra (GLL collocation, GLL points on every quad face) satisfy it exactly on
+    affine hexahedra; on trilinear ones the GLL rule (exact to 2N-1) misses the metric terms."""
     m = request.getfixturevalue(which)
     for ts in (0.0, 1.0):
-        dg = DGOracle(m, N, tau_scale=ts)
+        dg = DGOracle(m, N, tau_scale=ts, hex_basis=hex_basis)
         q = random_state(dg.ndof, 7)
         rate = energy_rate(dg, q)
         diss = dg.jump_dissipation(q)
@@ -91,14 +100,15 @@ def test_faces_conform_and_walls_on_cube(mesh):
     assert nb > 0
 
 
-@pytest.mark.parametrize("N", [1, 3])
-def test_linear_fields_are_reproduced(N):
+@pytest.mark.parametrize("N,hex_basis", [(1, "gl"), (3, "gl"), (2, "gll"), (3, "gll")])
+def test_linear_fields_are_reproduced(N, hex_basis):
     """Continuous linear fields: zero jumps, and -div u, -grad p exact at interior elements.
 
-    Affine mesh (amp = 0), so that the LSC wedge space contains the linear fields.
+    Affine mesh (amp = 0), so that the LSC wedge space contains the linear fields.  SEM: from
+    N = 2 on, the GLL-lumped projection of a linear field is its interpolant.
     """
     m = layered_mesh(3, 3, 5, "HWHTK", seed=0, amp=0.0)
-    dg = DGOracle(m, N)
+    dg = DGOracle(m, N, hex_basis=hex_basis)
     f = lambda x, t: np.stack([1 + 2 * x[:, 0] - x[:, 1] + 0.5 * x[:, 2],
                                0.3 * x[:, 0], -0.7 * x[:, 1] + 0.1, 0.2 * x[:, 2] + 0.4 * x[:, 0]])
     q = dg.project(f)

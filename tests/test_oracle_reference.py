@@ -103,6 +103,15 @@ def test_trace_constants_table(name):
         assert abs(trace_constant(TYPES[name], N) - tab[N - 1]) < 0.006, (name, N)
 
 
+@pytest.mark.parametrize("name", ["hex", "wedge", "pyramid"])
+def test_sem_trace_constants_table(name):
+    """Table computedTraceSEM: GLL nodes for the hexahedron and GLL points on every quadrilateral
+    face (also those of wedges and pyramids) reproduce the printed SEM constants."""
+    tab = read_table("trace_constants_sem.txt")[name]
+    for N in range(1, 7):
+        assert abs(trace_constant(TYPES[name], N, lobatto=True) - tab[N - 1]) < 0.006 * max(1, tab[N - 1] / 100), (name, N)
+
+
 @pytest.mark.parametrize("name", ["wedge", "pyramid", "tet"])
 def test_markov_constants_table(name):
     """Table markovConsts: pins the reference gradients of each basis."""
