@@ -65,7 +65,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* d, void* stream, dg_mesh** out) {
     g_err = "N must be in 1..6";
     return DG_ENOTSUP;
   }
-  if (d->hex_basis != 0 || d->nlevels > 2 || d->precision != 0) {
+  if ((d->hex_basis != 0 && d->hex_basis != 1) || d->nlevels > 2 || d->precision != 0) {
     g_err = "only GL hexahedra, one or two time-step levels and FP32 are built";
     return DG_ENOTSUP;
   }

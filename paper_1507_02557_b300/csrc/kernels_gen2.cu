@@ -42,8 +42,8 @@ struct G2 {
   // tet: lattice lift; pyramid: EF [4][NKL] | PF [4][NFN][NKL] | PF2 [4][NFN][NKL]; wedge: Vtl [2][NFN][NT]
   static constexpr int TN = T == DG_WEDGE ? NTRI * NFN * NT
                             : T == DG_PYR ? NTRI * NKL + 2 * NTRI * NFN * NKL : NTRI * NFN * NP;
-  // pyramid: LA [N1][NKL] | GC [N1]; wedge: Ve [3][N1][NT] | V1e [2][N1]
-  static constexpr int TQ = T == DG_WEDGE ? NQUAD * N1 * NT + 2 * N1 : T == DG_PYR ? N1 * NKL + N1 : 0;
+  // pyramid: LA [N1][NKL] | GC [N1]; wedge: Ve [3][N1][NT] | V1e [2][N1] | V1q [N1][N1]
+  static constexpr int TQ = T == DG_WEDGE ? NQUAD * N1 * NT + 2 * N1 + N1 * N1 : T == DG_PYR ? N1 * NKL + N1 : 0;
   static constexpr bool LAT = T != DG_WEDGE;                            // lattice-point face exchange
   static constexpr int TN2 = 0;
   static constexpr int NFX = LAT ? NTRI * NFN + NQUAD * NQ : NF * NQ;   // face flux points
@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
   const float* Vtl = Tn;                                         // wedge [2][NFN][NT]
   const float* Ve = Tq;                                          // wedge [3][N1][NT]
   const float* V1e = Tq + NQUAD * C::N1 * C::NT;                 // wedge [2][N1]
+  const float* V1q = V1e + 2 * C::N1;                            // wedge [N1][N1]: 1D basis at quad-face s points
   constexpr int NKL = C::NKL;
   const float* EF = Tn;                                          // pyramid [4][NKL]
   const float* PF = Tn + NTRI * NKL;                             // pyramid [4][NFN][NKL]
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
         } else {
           const int y = x - 2 * NFN, qf = y / NQ, idx = y % NQ, ia = idx % WN1, ib = idx / WN1;
 #pragma unroll
-          for (int j = 0; j < WN1; ++j) f4acc(v, V1[ib * WN1 + j], YB[(qf * WN1 + ia) * WN1 + j]);
+          for (int j = 0; j < WN1; ++j) f4acc(v, V1q[ib * WN1 + j], YB[(qf * WN1 + ia) * WN1 + j]);
           TQB[y] = v;
         }
       }
@@ -492,7 +493,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
           } else {
             const int y = x - 2 * WNT, qf = y / (WN1 * WN1), ia = (y / WN1) % WN1, j = y % WN1;
 #pragma unroll
-            for (int ib = 0; ib < WN1; ++ib) f4acc(v, V1[ib * WN1 + j], F4[(2 + qf) * NQ + ia + WN1 * ib]);
+            for (int ib = 0; ib < WN1; ++ib) f4acc(v, V1q[ib * WN1 + j], F4[(2 + qf) * NQ + ia + WN1 * ib]);
             PB[y] = v;
           }
         }

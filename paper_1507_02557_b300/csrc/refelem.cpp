@@ -57,6 +57,25 @@ void gauss_jacobi(int n, double a, double b, std::vector<double>& x, std::vector
   }
 }
 
+void gauss_lobatto(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  std::vector<double> xi, wi;
+  if (n > 2) gauss_jacobi(n - 2, 1, 1, xi, wi);   // interior nodes: zeros of P'_{n-1}
+  x[0] = -1.0;
+  x[n - 1] = 1.0;
+  for (int i = 1; i + 1 < n; ++i) x[i] = xi[i - 1];
+  for (int i = 0; i < n; ++i) {
+    const double p = jacobi(n - 1, 0, 0, x[i]);
+    w[i] = 2.0 / (n * (n - 1.0) * p * p);
+  }
+}
+
+void face_rule_1d(int N, bool lobatto, std::vector<double>& x, std::vector<double>& w) {
+  if (lobatto) gauss_lobatto(N + 1, x, w);
+  else gauss_jacobi(N + 1, 0, 0, x, w);
+}
+
 void lagrange(const std::vector<double>& nodes, double x, double* l, double* dl) {
   int n = (int)nodes.size();
   for (int i = 0; i < n; ++i) {
@@ -128,9 +147,9 @@ void face_code_key(int nv, int code, int key[4]) {
 }
 
 // ----------------------------------------------------------------------------- face rules
-void quad_rule(int N, std::vector<double>& pts, std::vector<double>& w) {
+void quad_rule(int N, std::vector<double>& pts, std::vector<double>& w, bool lobatto) {
   std::vector<double> x, wx;
-  gauss_jacobi(N + 1, 0, 0, x, wx);
+  face_rule_1d(N, lobatto, x, wx);
   int n = N + 1;
   pts.resize(2 * n * n);
   w.resize(n * n);
@@ -243,12 +262,12 @@ static void invert(std::vector<double>& A, int n) {
   A.swap(I);
 }
 
-void Basis::init(int type_, int N_) {
+void Basis::init(int type_, int N_, bool lobatto) {
   type = type_;
   N = N_;
   Np = num_nodes(type, N);
   if (type == HEX) {
-    gauss_jacobi(N + 1, 0, 0, r1, w1);
+    face_rule_1d(N, lobatto, r1, w1);
     int n = N + 1;
     nodes.resize(3 * Np);
     for (int k = 0; k < n; ++k)

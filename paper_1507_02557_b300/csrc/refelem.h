@@ -1,11 +1,11 @@
 // Reference-element data for the hybrid DG method, built on the host in FP64.
 //
 // Bases (Sec. 2.1 of arxiv 1507.02557):
-//   hex      nodal Lagrange at tensor Gauss-Legendre nodes (Sec. 2.1.1)
+//   hex      nodal Lagrange at tensor Gauss-Legendre nodes, or Gauss-Lobatto (SEM) (Sec. 2.1.1)
 //   tet      nodal Lagrange at the equispaced lattice of the bi-unit tet (Sec. 2.1.2)
 //   wedge    orthonormal modal basis, LSC-DG numerator (Sec. 2.1.3)
 //   pyramid  semi-nodal orthogonal basis of the rational space B_N (Sec. 2.1.4)
-// Face rules: tensor GL (N+1)^2 on quadrilaterals; collapsed GL x Gauss-Jacobi(1,0)
+// Face rules: tensor GL (or GLL with SEM hexahedra) (N+1)^2 on quadrilaterals; collapsed GL x Gauss-Jacobi(1,0)
 // with (N+1)^2 points on triangles, given in a canonical face frame (see setup.cpp).
 #pragma once
 #include <vector>
@@ -18,6 +18,10 @@ enum { HEX = 0, WEDGE = 1, PYR = 2, TET = 3 };
 double jacobi(int n, double a, double b, double x);
 double jacobi_deriv(int n, double a, double b, double x);
 void gauss_jacobi(int n, double a, double b, std::vector<double>& x, std::vector<double>& w);
+// n-point Gauss-Lobatto-Legendre rule: +-1 and the zeros of P'_{n-1}, w = 2 / (n (n-1) P_{n-1}(x)^2)
+void gauss_lobatto(int n, std::vector<double>& x, std::vector<double>& w);
+// the (N+1)-point quadrilateral-face rule in 1D: GL, or GLL with SEM hexahedra
+void face_rule_1d(int N, bool lobatto, std::vector<double>& x, std::vector<double>& w);
 void lagrange(const std::vector<double>& nodes, double x, double* l, double* dl);
 
 // Reference element geometry --------------------------------------------------
@@ -46,13 +50,13 @@ struct Basis {
   std::vector<std::vector<double>> lev_x, lev_w; // GL nodes/weights of each level k (k+1 points)
   std::vector<int> mi, mj, mk;                   // mode indices
   std::vector<double> gam;                       // pyramid c-normalisation per level
-  void init(int type, int N);
+  void init(int type, int N, bool lobatto = false);   // lobatto: SEM hexahedron (GLL nodes)
   void eval(const double* rst, double* phi, double* g) const;
 };
 
 // Face cubature in canonical coordinates: pts[nq*2], w[nq] (tri: (xi,eta); quad: (alpha,beta)).
 void tri_rule(int N, std::vector<double>& pts, std::vector<double>& w);
-void quad_rule(int N, std::vector<double>& pts, std::vector<double>& w);
+void quad_rule(int N, std::vector<double>& pts, std::vector<double>& w, bool lobatto = false);
 // Reference point (rst) and tangents of canonical face point (u,v) for (type, face, key).
 void face_point(int type, int f, const int key[4], double u, double v, double rst[3],
                 double d1[3], double d2[3]);

@@ -234,10 +234,12 @@ double max_gen_eig(std::vector<double> A, std::vector<double> B, int n) {
   return mx;
 }
 
-// Reference trace constant C_T(N) (Appendix B), Euclidean face measure of the reference element.
-double trace_constant(const Basis& B) {
+// Reference trace constant C_T(N) (Appendix B), Euclidean face measure of the reference element;
+// lobatto: SEM (GLL points on the quadrilateral faces, GLL-collocated hex mass), Table
+// computedTraceSEM.
+double trace_constant(const Basis& B, bool lobatto = false) {
   int t = B.type, N = B.N, Np = B.Np;
-  if (t == HEX) return 1.5 * (N + 1) * (N + 2);
+  if (t == HEX) return lobatto ? 1.5 * N * (N + 1) : 1.5 * (N + 1) * (N + 2);
   std::vector<double> P, W;
   volume_rule(t, N + 2, P, W);
   std::vector<double> M(Np * Np, 0.0), Ms(Np * Np, 0.0), phi(Np);
@@ -250,7 +252,7 @@ double trace_constant(const Basis& B) {
     int nv = face_nverts(t, f);
     int key[4] = {0, 1, 2, 3};
     std::vector<double> pts, w;
-    if (nv == 3) tri_rule(N, pts, w); else quad_rule(N, pts, w);
+    if (nv == 3) tri_rule(N, pts, w); else quad_rule(N, pts, w, lobatto);
     for (size_t q = 0; q < w.size(); ++q) {
       double rst[3], d1[3], d2[3];
       face_point(t, f, key, pts[2 * q], pts[2 * q + 1], rst, d1, d2);
@@ -414,8 +416,8 @@ dg_status dg_setup_host_only(dg_mesh* m, const dg_mesh_desc* d, std::string& err
   if (st == DG_OK && ct) {
     for (int t = 0; t < 4; ++t) {
       Basis B;
-      B.init(t, d->N);
-      ct[t] = trace_constant(B);
+      B.init(t, d->N, d->hex_basis == 1 && t == HEX);
+      ct[t] = trace_constant(B, d->hex_basis == 1);
     }
   }
   dg_free(m);
@@ -445,8 +447,9 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
     m->tau_scale = d->tau_scale;
     m->cfl = d->cfl > 0 ? d->cfl : 0.5;
     m->pyr_form = d->pyr_form;
+    const bool sem = d->hex_basis == 1;   // SEM hexahedra: GLL nodes, GLL points on quad faces
     Basis B[4];
-    for (int t = 0; t < 4; ++t) B[t].init(t, N);
+    for (int t = 0; t < 4; ++t) B[t].init(t, N, sem && t == HEX);
     const int nfc[4] = {6, 5, 5, 4};
 
     // --- offsets
@@ -550,11 +553,11 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
     // --- face rules in canonical coordinates
     std::vector<double> tpts, tw, qpts, qw;
     tri_rule(N, tpts, tw);
-    quad_rule(N, qpts, qw);
+    quad_rule(N, qpts, qw, sem);
 
     // --- per-type geometry, operators and time-step data
     double CT[4];
-    for (int t = 0; t < 4; ++t) CT[t] = trace_constant(B[t]);
+    for (int t = 0; t < 4; ++t) CT[t] = trace_constant(B[t], sem);
     std::vector<double> jsmax[4], jinvmax[4], jsj[4], taup[4], tauu[4];
     for (int t = 0; t < 4; ++t) {
       int K = m->td[t].K;
@@ -928,7 +931,7 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
         //  pyr:   DV4[Np][Np] | EF[4][nkl] | PF[4][nfn][nkl] | PF2[4][nfn][nkl] | LA[n1][nkl] | GC[n1] | E[nq][nfn]
         //         (nkl = (N+1)(N+2)/2 level-index pairs (k, l <= k))
         //  wedge: Vt4[nq][ntri] | V1[n1][n1] | D1[n1][n1] | w[nq][n1] | Vtl[2][nfn][ntri] | Ve[3][n1][ntri] |
-        //         V1e[2][n1] | E[nq][nfn]
+        //         V1e[2][n1] | V1q[n1][n1] | E[nq][nfn]
         //  int layout: tperm[6][nfn] | tinv[6][nfn] | qperm[8][nq] | (tet) fnode[4][nfn]
         const int nfn = (N + 1) * (N + 2) / 2;
         std::vector<int> tperm, tinv;
@@ -1063,9 +1066,9 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
             for (int qt = 0; qt < nqt; ++qt)
               for (int l = 0; l < n1; ++l) o2.push_back((float)(tww[qt] * sw[l]));
           }
-          // triangle-face lattice evaluations, then quad-face local GL evaluations
+          // triangle-face lattice evaluations, then evaluations at the quad faces' local points
           std::vector<double> gx, gw;
-          gauss_jacobi(n1, 0, 0, gx, gw);
+          face_rule_1d(N, sem, gx, gw);
           if (t == WEDGE) {
             // factorised face evaluations of phi_(mt,j) = phi_tri_mt(r,t) phi_1D_j(s):
             //   Vtl[2][nfn][ntri]  phi_tri at the lattice of the triangle faces (s = -1, +1)
@@ -1094,6 +1097,9 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
             for (int f = 0; f < 2; ++f)
               for (int j = 0; j < n1; ++j)
                 o2.push_back((float)(std::sqrt((2.0 * j + 1) / 2) * jacobi(j, 0, 0, f == 0 ? -1.0 : 1.0)));
+            //   V1q[n1][n1]        phi_1D_j at the quad faces' points along s (GL, or GLL with SEM)
+            for (int l = 0; l < n1; ++l)
+              for (int j = 0; j < n1; ++j) o2.push_back((float)(std::sqrt((2.0 * j + 1) / 2) * jacobi(j, 0, 0, gx[l])));
           }
           if (t == PYR) {
             // factorised face evaluations of the semi-nodal basis

@@ -73,7 +73,7 @@ def _ptr(x):
     return x.ctypes.data_as(_vp)
 
 
-def _desc(mesh, N, tau_scale, pyr_form, cfl, keep, nlevels=1):
+def _desc(mesh, N, tau_scale, pyr_form, cfl, keep, nlevels=1, hex_basis=0):
     d = Desc()
     xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
     keep.append(xyz)
@@ -86,15 +86,16 @@ def _desc(mesh, N, tau_scale, pyr_form, cfl, keep, nlevels=1):
         d.nelem[t] = cn.shape[0]
         d.conn[t] = cn.ctypes.data_as(C.POINTER(C.c_int32))
         d.c2[t] = c2.ctypes.data_as(C.POINTER(C.c_double))
-    d.N, d.hex_basis, d.pyr_form = N, 0, pyr_form
+    d.N, d.hex_basis, d.pyr_form = N, hex_basis, pyr_form
     d.tau_scale, d.nlevels, d.cfl, d.precision = tau_scale, nlevels, cfl, 0
     return d
 
 
-def host_check(mesh, N, tau_scale=1.0, pyr_form=0, cfl=0.5, nlevels=1, levels=False):
-    """dg_host_check: (dt_min, [C_T hex, wedge, pyr, tet][, level counts]) from the host setup alone."""
+def host_check(mesh, N, tau_scale=1.0, pyr_form=0, cfl=0.5, nlevels=1, levels=False, hex_basis=0):
+    """dg_host_check: (dt_min, [C_T hex, wedge, pyr, tet][, level counts]) from the host setup alone.
+    hex_basis 1 = SEM hexahedra (GLL nodes, GLL points on every quadrilateral face)."""
     keep = []
-    d = _desc(mesh, N, tau_scale, pyr_form, cfl, keep, nlevels)
+    d = _desc(mesh, N, tau_scale, pyr_form, cfl, keep, nlevels, hex_basis)
     dt = C.c_double()
     ct = (C.c_double * 4)()
     lc = (C.c_int64 * 2)()
@@ -107,9 +108,9 @@ def host_check(mesh, N, tau_scale=1.0, pyr_form=0, cfl=0.5, nlevels=1, levels=Fa
 class Mesh:
     """A dg_mesh on the current CUDA device (see include/dg.h)."""
 
-    def __init__(self, mesh, N, tau_scale=1.0, pyr_form=0, cfl=0.5, stream=None, nlevels=1):
+    def __init__(self, mesh, N, tau_scale=1.0, pyr_form=0, cfl=0.5, stream=None, nlevels=1, hex_basis=0):
         keep = []
-        d = _desc(mesh, N, tau_scale, pyr_form, cfl, keep, nlevels)
+        d = _desc(mesh, N, tau_scale, pyr_form, cfl, keep, nlevels, hex_basis)
         h = _vp()
         _check(_lib.dg_mesh_create(C.byref(d), _vp(stream or 0), C.byref(h)))
         self._h = h

@@ -231,3 +231,49 @@ def test_error_against_exact_mode_matches_oracle(lib, N):
         q = o.lsrk_step(q, dt)
     e_gpu, e_orc = o.l2_error(got, standing_mode, T), o.l2_error(q, standing_mode, T)
     assert abs(e_gpu - e_orc) <= 0.01 * e_orc + 1e-6, (e_gpu, e_orc)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_sem_rhs_matches_oracle(lib, N):
+    """SEM hexahedra (GLL nodes, GLL points on every quadrilateral face, also those of wedges and
+    pyramids): rhs against the oracle with the same rules."""
+    for name in ("hybrid", "cjump"):
+        m = MESHES[name]()
+        o = DGOracle(m, N, hex_basis="gll")
+        q32 = random_state(o.ndof, 13).astype(np.float32)
+        got, _ = gpu_rhs(lib, m, N, q32, hex_basis=1)
+        want = o.rhs(q32.astype(np.float64))
+        errs = per_type_rel(o, got, want)
+        assert rel(got, want) < TOL and max(errs) < TOL, (name, errs)
+
+
+@pytest.mark.parametrize("N", [3, 4])
+def test_sem_steps_match_oracle(lib, N):
+    """SEM: ten LSRK(5,4) steps, and the multi-rate start-up + 3 coarse steps, against the oracle
+    (N = 4: TMA-staged hex stage and fused multi-rate kernels with the GLL tables)."""
+    from oracle.constants import trace_constant
+    from oracle.dg import MRAB3, mr_levels, standing_mode
+    m = MESHES["cjump"]()
+    o = DGOracle(m, N, hex_basis="gll")
+    q0 = o.project(standing_mode, 0.0).astype(np.float32)
+    g = lib.Mesh(m, N, hex_basis=1)
+    dt = g.timestep()
+    g.set_state(q0, on_device=False)
+    g.step(10, dt)
+    got = g.get_state(np.zeros_like(q0), on_device=False).astype(np.float64)
+    q = q0.astype(np.float64)
+    for _ in range(10):
+        q = o.lsrk_step(q, dt)
+    assert rel(got, q) < TOL, per_type_rel(o, got, q)
+    lev, dmin = mr_levels(o, [trace_constant(t, N, lobatto=True) for t in range(4)], 2)
+    gm = lib.Mesh(m, N, nlevels=2, hex_basis=1)
+    h = gm.timestep()
+    assert abs(h - dmin) < 1e-12 * dmin
+    gm.set_state(q0, on_device=False)
+    gm.step(3, h)
+    got = gm.get_state(np.zeros_like(q0), on_device=False).astype(np.float64)
+    mr = MRAB3(o, lev)
+    q, hist = mr.start(q0.astype(np.float64), h)
+    for _ in range(3):
+        q, hist = mr.step(q, hist, h)
+    assert rel(got, q) < TOL, per_type_rel(o, got, q)

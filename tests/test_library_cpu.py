@@ -49,6 +49,20 @@ def test_host_trace_constants_against_paper_table():
         assert np.allclose(ct, row, atol=0.006)
 
 
+@pytest.mark.parametrize("N", [1, 2, 4])
+def test_host_setup_sem_matches_oracle_and_table(N):
+    """SEM hexahedra (hex_basis 1): C_SEM(N) of the printed Table computedTraceSEM for hex, wedge
+    and pyramid, and dt equal to the oracle's with the same rules."""
+    m = small_hybrid_mesh()
+    dt, ct = dg.host_check(m, N, hex_basis=1)
+    tab = {1: [3, 46.46, 31.58], 2: [9, 51.70, 37.12], 4: [30, 83.32, 60.95]}[N]
+    assert np.allclose(ct[:3], tab, atol=0.006)
+    o = DGOracle(m, N, hex_basis="gll")
+    cto = [trace_constant(t, N, lobatto=True) for t in range(4)]
+    assert np.allclose(ct, cto, rtol=1e-12)
+    assert abs(dt - o.global_dt(cto)) < 1e-12 * dt
+
+
 def test_host_setup_rejects_bad_meshes():
     m = small_hybrid_mesh()
     with pytest.raises(dg.DGError, match="not supported"):
