@@ -13,6 +13,9 @@ actually performed.  Beside it ("single_rate"): one step = one LSRK(5,4) step
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
 
+Beside them ("sem_hex"): the multi-rate workload with SEM hexahedra (GLL nodes, GLL points on
+every quadrilateral face) and the ratio of its hex kernel time per step to the GL one.
+
 Under torchrun (N > 1) every rank advances its own replica of the mesh (no
 exchange): value = sum over ranks, time = max over ranks ("replicas only").
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
@@ -309,6 +312,26 @@ def main():
                                      "h2d_bytes_per_step": 4 * ndof * 4, "d2h_bytes_per_step": 8}
     del g1
 
+    # ---- SEM hexahedra (GLL nodes, GLL points on quad faces): the same multi-rate workload, for
+    # the cost comparison of the two hex bases (per-DOF time of the hex kernels)
+    del g
+    torch.cuda.synchronize()
+    gs = dg.Mesh(mesh, ORDER, stream=stream.cuda_stream, nlevels=2, hex_basis=1)
+    gs.set_state(q0, on_device=False)
+    hs = gs.timestep()
+    fs = gs.level_type_counts(2)
+    ndof_fine_s = sum(c * n for c, n in zip(fs, npe))
+    s_steps = max(3, min(args.steps, 20))
+    gs.step(args.warmup, hs)
+    ms_s, kms_s, _, _ = timed_run(gs, torch, stream, s_steps, hs, barrier)
+    ms_s = max_ms(ms_s)
+    sem = {"value": (ndof + ndof_fine_s) * s_steps * world / (ms_s / 1e3) / 1e9, "unit": METRIC,
+           "steps": s_steps, "ms_per_step": ms_s / s_steps, "h_fine": hs, "fine_elements": fs,
+           "kernel_ms": dict(zip(["hex", "wedge", "pyramid", "tet"], kms_s)),
+           "hex_time_sem_over_gl": (kms_s[0] / s_steps) / (kms[0] / args.steps)}
+    del gs
+    torch.cuda.synchronize()
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -322,7 +345,7 @@ def main():
                              "traffic": traffic, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
                 "kernel_ms": dict(zip(["hex", "wedge", "pyramid", "tet"], kms)),
                 "gpu_launches": int(sum(launches)) + 2 * 4 * args.steps,
-                "single_rate": single, "e2e": e2e, "clocks": clk}
+                "single_rate": single, "sem_hex": sem, "e2e": e2e, "clocks": clk}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

@@ -84,6 +84,7 @@ struct dg_mesh {
   float* trace3 = nullptr;        // third trace buffer of the fused multi-rate schedule
   int cslot[3] = {0, 1, 2}, fslot[3] = {2, 0, 1};   // slots of r^n, r^{n-1}, r^{n-2} per level
   bool mr_started = false;
+  bool hex_sem = false;           // SEM hexahedra (GLL nodes)
   bool tri_lat = true;            // tet / pyramid triangle faces exchange lattice values (gen2)
   int* derr = nullptr;            // device error word: bit 0 = a bounded device wait timed out
   dgk::TmaArr tma[5];             // q, res, hist, trace, trace3 (hex TMA staging)

@@ -427,7 +427,9 @@ struct HexMaps {
   long long qoff, a0off, a1off, inoff;
 };
 
-template <int N, int MODE, bool TMA>
+// SEM = true: GLL nodes, the faces carry the end nodes; traces are node values and the lift only
+// touches the boundary nodes (the cost advantage of the SEM hexahedron, Sec. 2.1.1)
+template <int N, int MODE, bool TMA, bool SEM>
 __global__ void __launch_bounds__(128, DG_HEXP_MINB) hexw_kernel(Args A, const __grid_constant__ HexMaps M) {
   using H = HexP<N, MODE, TMA>;
   constexpr int n1 = H::n1, NP = H::NP, NQ = H::NQ, EPW = H::EPW, WPB = H::WPB, SD = H::SD;
@@ -702,14 +704,21 @@ __global__ void __launch_bounds__(128, DG_HEXP_MINB) hexw_kernel(Args A, const _
 #pragma unroll
       for (int ax = 0; ax < 3; ++ax) {
         float4 tm = make_float4(0.f, 0.f, 0.f, 0.f), tp = tm;
+        auto node = [&](int m) {
+          if (ax == 0) return s_q[m + n1 * i + NQ * j];
+          if (ax == 1) return s_q[i + n1 * m + NQ * j];
+          return make_float4(q[0][m], q[1][m], q[2][m], q[3][m]);
+        };
+        if constexpr (SEM) {
+          tm = node(0);
+          tp = node(N);
+        } else {
 #pragma unroll
-        for (int m = 0; m < n1; ++m) {
-          float4 v;
-          if (ax == 0) v = s_q[m + n1 * i + NQ * j];
-          else if (ax == 1) v = s_q[i + n1 * m + NQ * j];
-          else v = make_float4(q[0][m], q[1][m], q[2][m], q[3][m]);
-          tm = f4fma(Vm[m], v, tm);
-          tp = f4fma(Vp[m], v, tp);
+          for (int m = 0; m < n1; ++m) {
+            const float4 v = node(m);
+            tm = f4fma(Vm[m], v, tm);
+            tp = f4fma(Vp[m], v, tp);
+          }
         }
 #pragma unroll
         for (int sd = 0; sd < 2; ++sd) {
@@ -743,15 +752,24 @@ __global__ void __launch_bounds__(128, DG_HEXP_MINB) hexw_kernel(Args A, const _
         // ---- lift (Alg. hex_surf), M^{-1} = 1/(w w w J)
 #pragma unroll
         for (int k = 0; k < n1; ++k) {
-          const float4 F0 = s_F[0 * NQ + j + n1 * k], F1 = s_F[1 * NQ + j + n1 * k];
-          const float4 F2 = s_F[2 * NQ + i + n1 * k], F3 = s_F[3 * NQ + i + n1 * k];
           float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-          sum = f4fma(Vm[i], F0, sum);
-          sum = f4fma(Vp[i], F1, sum);
-          sum = f4fma(Vm[j], F2, sum);
-          sum = f4fma(Vp[j], F3, sum);
-          sum = f4fma(Vm[k], F45[0], sum);
-          sum = f4fma(Vp[k], F45[1], sum);
+          if constexpr (SEM) {   // l_m(-1) = delta_{m0}, l_m(+1) = delta_{mN}
+            if (i == 0) sum = f4fma(1.f, s_F[0 * NQ + j + n1 * k], sum);
+            if (i == N) sum = f4fma(1.f, s_F[1 * NQ + j + n1 * k], sum);
+            if (j == 0) sum = f4fma(1.f, s_F[2 * NQ + i + n1 * k], sum);
+            if (j == N) sum = f4fma(1.f, s_F[3 * NQ + i + n1 * k], sum);
+            if (k == 0) sum = f4fma(1.f, F45[0], sum);
+            if (k == N) sum = f4fma(1.f, F45[1], sum);
+          } else {
+            const float4 F0 = s_F[0 * NQ + j + n1 * k], F1 = s_F[1 * NQ + j + n1 * k];
+            const float4 F2 = s_F[2 * NQ + i + n1 * k], F3 = s_F[3 * NQ + i + n1 * k];
+            sum = f4fma(Vm[i], F0, sum);
+            sum = f4fma(Vp[i], F1, sum);
+            sum = f4fma(Vm[j], F2, sum);
+            sum = f4fma(Vp[j], F3, sum);
+            sum = f4fma(Vm[k], F45[0], sum);
+            sum = f4fma(Vp[k], F45[1], sum);
+          }
           const float iM = iW[i] * iW[j] * iW[k] * iJn[k];
           rhs[0][k] += iM * sum.x;
           rhs[1][k] += c2 * iM * sum.y;
@@ -834,14 +852,21 @@ __global__ void __launch_bounds__(128, DG_HEXP_MINB) hexw_kernel(Args A, const _
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
           float4 tm = make_float4(0.f, 0.f, 0.f, 0.f), tp = tm;
+          auto node = [&](int m) {
+            if (ax == 0) return s_q[m + n1 * i + NQ * j];
+            if (ax == 1) return s_q[i + n1 * m + NQ * j];
+            return make_float4(q[0][m], q[1][m], q[2][m], q[3][m]);
+          };
+          if constexpr (SEM) {
+            tm = node(0);
+            tp = node(N);
+          } else {
 #pragma unroll
-          for (int m = 0; m < n1; ++m) {
-            float4 v;
-            if (ax == 0) v = s_q[m + n1 * i + NQ * j];
-            else if (ax == 1) v = s_q[i + n1 * m + NQ * j];
-            else v = make_float4(q[0][m], q[1][m], q[2][m], q[3][m]);
-            tm = f4fma(Vm[m], v, tm);
-            tp = f4fma(Vp[m], v, tp);
+            for (int m = 0; m < n1; ++m) {
+              const float4 v = node(m);
+              tm = f4fma(Vm[m], v, tm);
+              tp = f4fma(Vp[m], v, tp);
+            }
           }
 #pragma unroll
           for (int sd = 0; sd < 2; ++sd) {
@@ -886,23 +911,23 @@ __global__ void __launch_bounds__(128, DG_HEXP_MINB) hexw_kernel(Args A, const _
   }
 }
 
-template <int N, int MODE, bool TMA>
+template <int N, int MODE, bool TMA, bool SEM>
 static void launch_hexw_n(const Args& A, const HexMaps& M, cudaStream_t s) {
   using H = HexP<N, MODE, TMA>;
   if (A.K == 0) return;
   static int blocks = 0;   // persistent grid: resident blocks per SM x SMs (computed once)
   if (blocks == 0) {
-    cudaFuncSetAttribute(hexw_kernel<N, MODE, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, H::SMEM);
+    cudaFuncSetAttribute(hexw_kernel<N, MODE, TMA, SEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, H::SMEM);
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, hexw_kernel<N, MODE, TMA>, 32 * H::WPB, H::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, hexw_kernel<N, MODE, TMA, SEM>, 32 * H::WPB, H::SMEM);
     blocks = (per < 1 ? 1 : per) * sms;
   }
   const int64_t per_block = (int64_t)H::WPB * H::EPW;
   const int64_t need = ((int64_t)A.K + per_block - 1) / per_block;
   const int grid = (int)(need < blocks ? need : blocks);
-  hexw_kernel<N, MODE, TMA><<<grid, 32 * H::WPB, H::SMEM, s>>>(A, M);
+  hexw_kernel<N, MODE, TMA, SEM><<<grid, 32 * H::WPB, H::SMEM, s>>>(A, M);
 }
 
 // ---------------------------------------------------------------------------- TMA descriptors
@@ -1333,16 +1358,21 @@ static int ev_take(dg_mesh* m) {
 
 // N <= 4 hexahedra: the TMA kernel for the fused N = 4 updates when every staged array has a
 // descriptor, the cp.async kernel otherwise
-template <int N, int MODE>
-static void launch_hex_fast(dg_mesh* m, const Args& A, cudaStream_t s) {
+template <int N, int MODE, bool SEM>
+static void launch_hex_fast_b(dg_mesh* m, const Args& A, cudaStream_t s) {
   HexMaps M{};
   if constexpr (N == 4 && (MODE == MODE_STAGE || MODE == MODE_MRC || MODE == MODE_MRF)) {
     if (hex_maps<MODE>(m, A, &M)) {
-      launch_hexw_n<N, MODE, true>(A, M, s);
+      launch_hexw_n<N, MODE, true, SEM>(A, M, s);
       return;
     }
   }
-  launch_hexw_n<N, MODE, false>(A, M, s);
+  launch_hexw_n<N, MODE, false, SEM>(A, M, s);
+}
+template <int N, int MODE>
+static void launch_hex_fast(dg_mesh* m, const Args& A, cudaStream_t s) {
+  if (m->hex_sem) launch_hex_fast_b<N, MODE, true>(m, A, s);
+  else launch_hex_fast_b<N, MODE, false>(m, A, s);
 }
 
 template <int MODE>

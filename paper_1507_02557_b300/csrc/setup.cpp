@@ -448,6 +448,7 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
     m->cfl = d->cfl > 0 ? d->cfl : 0.5;
     m->pyr_form = d->pyr_form;
     const bool sem = d->hex_basis == 1;   // SEM hexahedra: GLL nodes, GLL points on quad faces
+    m->hex_sem = sem;
     Basis B[4];
     for (int t = 0; t < 4; ++t) B[t].init(t, N, sem && t == HEX);
     const int nfc[4] = {6, 5, 5, 4};
