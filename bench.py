@@ -16,6 +16,11 @@ actually performed.  Beside it ("single_rate"): one step = one LSRK(5,4) step
 Beside them ("sem_hex"): the multi-rate workload with SEM hexahedra (GLL nodes, GLL points on
 every quadrilateral face) and the ratio of its hex kernel time per step to the GL one.
 
+Beside them ("batch"): 256 seeded meshes of n^3 cells (n log-uniform in [6, 40], N uniform in
+2..6, c uniform in [1, 3] per layer, layers H*a | W | H*b | T | K*k) advanced by LSRK(5,4), once
+mesh after mesh through dg_step and once through one dg_batch (a captured CUDA graph with one
+branch per mesh); also the subset of the meshes with n <= 12.
+
 Under torchrun (N > 1) every rank advances its own replica of the mesh (no
 exchange): value = sum over ranks, time = max over ranks ("replicas only").
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
@@ -191,6 +196,49 @@ def timed_run(g, torch, stream, steps, dt, barrier):
     return ev0.elapsed_time(ev1), kms, launches, clk.summary()
 
 
+def batch_run(dg, torch, stream, barrier, world, steps=6):
+    """The many-mesh workload: GDOF-stage/s of per-mesh dg_step calls (eager) and of one dg_batch
+    (graph), wall clock between device synchronisations, all meshes' states resident."""
+    from paper_1507_02557_b300.inputs import batch_mesh, batch_specs, random_state
+    specs = batch_specs()
+    t0 = time.perf_counter()
+    meshes = [dg.Mesh(batch_mesh(sp), sp[1], stream=stream.cuda_stream) for sp in specs]
+    barrier()
+    setup_s = time.perf_counter() - t0
+    for i, g in enumerate(meshes):
+        g.set_state((1e-3 * random_state(g.ndof, 100 + i)).astype(np.float32), on_device=False)
+    out = {"workload": "256 meshes of n^3 cells, n log-uniform in [6,40], N uniform in 2..6, "
+                       "c uniform in [1,3] per layer; LSRK(5,4)",
+           "steps": steps, "setup_s": setup_s, "unit": METRIC}
+    for name, sel in (("all", [True] * len(specs)), ("n_le_12", [sp[0] <= 12 for sp in specs])):
+        ms = [g for g, k in zip(meshes, sel) if k]
+        units = sum(g.ndof for g in ms) * 5 * steps * world
+        b = dg.Batch(ms, stream=stream.cuda_stream)
+
+        def eager():
+            for g in ms:
+                g.step(steps)
+
+        def graph():
+            b.step(steps)
+
+        res = {"meshes": len(ms), "dof": sum(g.ndof for g in ms)}
+        for arm, f in (("eager", eager), ("graph", graph)):
+            f()
+            barrier()
+            t1 = time.perf_counter()
+            f()
+            barrier()
+            res[arm] = units / (time.perf_counter() - t1) / 1e9
+        res["graph_over_eager"] = res["graph"] / res["eager"]
+        res["graph_replays_captures"] = list(b.stats())
+        b.close()
+        out[name] = res
+    del meshes
+    torch.cuda.synchronize()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -199,6 +247,7 @@ def main():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--cells", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -331,6 +380,7 @@ def main():
            "hex_time_sem_over_gl": (kms_s[0] / s_steps) / (kms[0] / args.steps)}
     del gs
     torch.cuda.synchronize()
+    batch = None if args.no_batch else batch_run(dg, torch, stream, barrier, world)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -346,6 +396,8 @@ def main():
                 "kernel_ms": dict(zip(["hex", "wedge", "pyramid", "tet"], kms)),
                 "gpu_launches": int(sum(launches)) + 2 * 4 * args.steps,
                 "single_rate": single, "sem_hex": sem, "e2e": e2e, "clocks": clk}
+        if batch:
+            line["batch"] = batch
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

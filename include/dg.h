@@ -166,6 +166,42 @@ dg_status dg_profile(dg_mesh *mesh, int enable, double *ms, int64_t *launches);
  * DG_EINVAL for a null mesh or a limit out of range. */
 dg_status dg_watchdog_selftest(dg_mesh *mesh, int64_t limit_cycles);
 
+/* ---- batches: many meshes stepped together ---------------------------------
+ * Sec. 4.3 (Figure perDofTimes) measures the time per degree of freedom rising
+ * for small meshes, whose kernels cannot fill the GPU.  A batch steps several
+ * meshes (any mix of N, element types, sizes and time-step levels) through one
+ * CUDA graph in which each mesh is an independent branch, so the kernels of
+ * different meshes run concurrently and a chunk of steps costs one graph launch.
+ *
+ * dg_batch_create: meshes[count] are borrowed and must outlive the batch; a mesh
+ *   belongs to at most one batch; every mesh must be on the current device.
+ *   Work is enqueued on cuda_stream (NULL = the legacy default stream is not
+ *   capturable, so the batch then creates and owns a stream).  Allocates per-mesh
+ *   branch streams and events.  DG_EINVAL on a NULL or repeated mesh or count < 1.
+ * dg_batch_step: the same as dg_step(meshes[i], nsteps, dt[i], &t_inout[i]) for
+ *   every i (dt NULL or dt[i] <= 0: that mesh's dt_min; t_inout NULL: not
+ *   reported), with the same results bit for bit as, per mesh, one dg_step call
+ *   of nsteps mod DG_BATCH_CHUNK steps followed by nsteps / DG_BATCH_CHUNK calls
+ *   of DG_BATCH_CHUNK steps (the multi-rate history slots rotate with that
+ *   period).  The batch stream first waits for each mesh's own stream, and
+ *   each mesh's stream then waits for the batch, so per-mesh calls before and
+ *   after stay ordered.  Steps: the multi-rate start-ups and nsteps mod
+ *   DG_BATCH_CHUNK steps are enqueued directly, mesh after mesh; the rest are
+ *   replays of a graph of DG_BATCH_CHUNK steps of every mesh.  The graph is
+ *   captured on first use and cached (up to 4 graphs, keyed by the dt values and
+ *   the meshes' history-slot phases; a mesh stepped on its own between batch
+ *   calls may change its phase and cost one re-capture).  Asynchronous: errors
+ *   of the kernels are reported by the next synchronising call on a mesh.
+ * dg_batch_destroy: synchronises the batch stream and frees the batch's graphs,
+ *   streams and events (not the meshes). */
+#define DG_BATCH_CHUNK 3
+typedef struct dg_batch dg_batch;
+dg_status dg_batch_create(dg_mesh *const *meshes, int count, void *cuda_stream, dg_batch **out);
+dg_status dg_batch_step(dg_batch *batch, int nsteps, const double *dt, double *t_inout);
+/* Graph replays and captures since creation (for tests and measurements). */
+dg_status dg_batch_stats(const dg_batch *batch, int64_t *replays, int64_t *captures);
+void dg_batch_destroy(dg_batch *batch);
+
 /* Adjoint of dg_step (gradient w.r.t. c^2 and source amplitude): not built,
  * returns DG_ENOTSUP. */
 dg_status dg_adjoint_step(dg_mesh *mesh, int nsteps, float *lambda_dev, double *grad_c2_dev,

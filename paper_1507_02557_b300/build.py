@@ -10,7 +10,7 @@ OUT = os.path.join(HERE, "libdg.so")
 BUILD = os.environ.get("DG_BUILD_DIR", os.path.join(ROOT, "_build"))
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 EXTRA = os.environ.get("DG_NVCC_FLAGS", "").split()   # extra nvcc flags (variant builds)
-SOURCES = ["refelem.cpp", "setup.cpp", "api.cpp", "kernels.cu", "kernels_gen2.cu", "kernels_tc.cu", "noalloc.cu"]
+SOURCES = ["refelem.cpp", "setup.cpp", "api.cpp", "kernels.cu", "kernels_gen2.cu", "kernels_tc.cu", "noalloc.cu", "batch.cpp"]
 
 
 def nvcc():
@@ -27,13 +27,13 @@ def build(verbose=False):
         deps = [src] + [os.path.join(SRC, h) for h in os.listdir(SRC) if h.endswith((".h", ".cuh"))]
         deps.append(os.path.join(ROOT, "include", "dg.h"))
         if not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(d) for d in deps):
-            cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2"] + EXTRA + [
+            cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-fopenmp"] + EXTRA + [
                    "-I", os.path.join(ROOT, "include"), "-I", SRC, "-c", src, "-o", obj]
             if verbose:
                 print(" ".join(cmd), flush=True)
             subprocess.run(cmd, check=True)
         objs.append(obj)
-    cmd = [nvcc(), ARCH, "-shared", "-o", OUT] + objs + ["-lcudart"]
+    cmd = [nvcc(), ARCH, "-shared", "-o", OUT] + objs + ["-lcudart", "-lgomp"]
     subprocess.run(cmd, check=True)
     return OUT
 

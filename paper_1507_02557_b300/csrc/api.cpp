@@ -331,21 +331,25 @@ extern "C" dg_status dg_watchdog_selftest(dg_mesh* m, int64_t limit_cycles) {
   return device_flags(m);
 }
 
+cudaError_t dg_enqueue_steps(dg_mesh* m, int nsteps, double dt) {
+  if (m->nlevels == 2)   // fused kernels: N <= 4 with lattice exchange on tet / pyramid triangle faces
+    return m->N <= 4 && m->tri_lat ? mrab3_fused(m, nsteps, dt) : mrab3(m, nsteps, dt);
+  return nsteps > 0 ? lsrk_steps(m, nsteps, dt) : cudaSuccess;
+}
+
+double dg_step_time(const dg_mesh* m, int nsteps, double dt, bool fresh) {
+  if (m->nlevels == 2) return (fresh ? 4 * dt : 0.0) + nsteps * 2 * dt;
+  return nsteps * dt;
+}
+
 extern "C" dg_status dg_step(dg_mesh* m, int nsteps, double dt, double* t_inout) {
   if (!m || nsteps < 0) return DG_EINVAL;
   if (!(dt > 0)) dt = m->dt_min;
   if (nsteps == 0) return DG_OK;
-  if (m->nlevels == 2) {
-    bool fresh = !m->mr_started;
-    // fused kernels: N <= 4 with lattice exchange on tet / pyramid triangle faces
-    cudaError_t e = m->N <= 4 && m->tri_lat ? mrab3_fused(m, nsteps, dt) : mrab3(m, nsteps, dt);
-    if (e != cudaSuccess) return cuda_fail(e);
-    if (t_inout) *t_inout += (fresh ? 4 * dt : 0.0) + nsteps * 2 * dt;
-    return DG_OK;
-  }
-  cudaError_t e = lsrk_steps(m, nsteps, dt);
+  const bool fresh = m->nlevels == 2 && !m->mr_started;
+  cudaError_t e = dg_enqueue_steps(m, nsteps, dt);
   if (e != cudaSuccess) return cuda_fail(e);
-  if (t_inout) *t_inout += nsteps * dt;
+  if (t_inout) *t_inout += dg_step_time(m, nsteps, dt, fresh);
   return DG_OK;
 }
 

@@ -114,11 +114,17 @@ cudaError_t launch_mr(dg_mesh* m, bool coarse, const Sel& sel, float* q, const f
 cudaError_t launch_ab(dg_mesh* m, const Sel& sel, const float* qin, float* qout, const float* r0,
                       const float* r1, const float* r2, float h0, float h1, float h2);
 // Hex constants (1D D, V^f, GL weights and nodes) of order N <= 4 into constant memory.
-cudaError_t upload_hex_constants(int N, const float* hc, int count);
+cudaError_t upload_hex_constants(int N, bool sem, const float* hc, int count);
 }  // namespace dgk
 
 // Message returned by dg_last_error() on this thread (api.cpp).
 void dg_set_last_error(const std::string& msg);
+
+// nsteps time steps of m on m->stream: LSRK(5,4), or multi-rate AB3 whose first call also runs the
+// start-up (nsteps = 0 runs the start-up alone).  No synchronization (api.cpp).
+cudaError_t dg_enqueue_steps(dg_mesh* m, int nsteps, double dt);
+// Simulated time that dg_enqueue_steps(m, nsteps, dt) advances; fresh = the start-up runs too.
+double dg_step_time(const dg_mesh* m, int nsteps, double dt, bool fresh);
 
 // Host setup (setup.cpp).
 dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err);

@@ -260,11 +260,12 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
 // t-face traces come from registers; r/s-derivatives and r/s-face traces read the
 // element's nodes as float4 (p,u,v,w) from shared memory.  Only warp-level
 // synchronisation after the start of the block.
-__constant__ float c_hexw[5][64];   // per N: D1[n1*n1] (row = node), Vm[n1], Vp[n1], w[n1], r[n1], 1/w[n1]
+// per node set (0 = GL, 1 = GLL) and N: D1[n1*n1] (row = node), Vm[n1], Vp[n1], w[n1], r[n1], 1/w[n1]
+__constant__ float c_hexw[2][5][64];
 
-cudaError_t upload_hex_constants(int N, const float* hc, int count) {
+cudaError_t upload_hex_constants(int N, bool sem, const float* hc, int count) {
   if (N < 1 || N > 4 || count > 64) return cudaSuccess;
-  return cudaMemcpyToSymbol(c_hexw, hc, count * sizeof(float), N * 64 * sizeof(float));
+  return cudaMemcpyToSymbol(c_hexw, hc, count * sizeof(float), ((sem ? 5 : 0) + N) * 64 * sizeof(float));
 }
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
@@ -456,7 +457,7 @@ __global__ void __launch_bounds__(128, DG_HEXP_MINB) hexw_kernel(Args A, const _
   float4* s_N = reinterpret_cast<float4*>(pw + (TMA ? H::T_N : H::C_N)) + su * 6 * NQ;
   auto SDp = [&](int b) { return reinterpret_cast<float*>(pw + (TMA ? H::T_SD : H::C_SD)) + (b * EPW + su) * SD; };
 
-  const float* Dm = c_hexw[N];
+  const float* Dm = c_hexw[SEM ? 1 : 0][N];
   const float* Vm = Dm + n1 * n1;
   const float* Vp = Vm + n1;
   const float* W1 = Vp + n1;

@@ -10,8 +10,11 @@
 // Face points: collapsed rule (N+1)^2 on triangles, GL (N+1)^2 on quads.
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <stdexcept>
 
@@ -237,9 +240,8 @@ double max_gen_eig(std::vector<double> A, std::vector<double> B, int n) {
 // Reference trace constant C_T(N) (Appendix B), Euclidean face measure of the reference element;
 // lobatto: SEM (GLL points on the quadrilateral faces, GLL-collocated hex mass), Table
 // computedTraceSEM.
-double trace_constant(const Basis& B, bool lobatto = false) {
+double trace_constant_eval(const Basis& B, bool lobatto) {
   int t = B.type, N = B.N, Np = B.Np;
-  if (t == HEX) return lobatto ? 1.5 * N * (N + 1) : 1.5 * (N + 1) * (N + 2);
   std::vector<double> P, W;
   volume_rule(t, N + 2, P, W);
   std::vector<double> M(Np * Np, 0.0), Ms(Np * Np, 0.0), phi(Np);
@@ -265,6 +267,23 @@ double trace_constant(const Basis& B, bool lobatto = false) {
     }
   }
   return max_gen_eig(Ms, M, Np);
+}
+
+// C_T depends on the reference element alone: computed once per (type, N, node set) and process.
+double trace_constant(const Basis& B, bool lobatto = false) {
+  if (B.type == HEX) return lobatto ? 1.5 * B.N * (B.N + 1) : 1.5 * (B.N + 1) * (B.N + 2);
+  static std::mutex mu;
+  static std::map<std::array<int, 3>, double> cache;
+  const std::array<int, 3> key{B.type, B.N, lobatto ? 1 : 0};
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  const double v = trace_constant_eval(B, lobatto);
+  std::lock_guard<std::mutex> lk(mu);
+  cache[key] = v;
+  return v;
 }
 
 // Canonical corner order (positions within the local corner list) of a face.
@@ -576,14 +595,19 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
       std::vector<float> c2f(K);
       for (int e = 0; e < K; ++e) c2f[e] = (float)d->c2[t][e];
       td.c2 = upload(c2f, owned);
-      std::vector<double> xv(3 * nv);
-      auto load_xv = [&](int64_t e) {
+      auto load_xv = [&](int64_t e, double* xv) {
         const int32_t* cv = d->conn[t] + e * nv;
         for (int v = 0; v < nv; ++v)
           for (int c = 0; c < 3; ++c) xv[3 * v + c] = d->xyz[3 * (int64_t)cv[v] + c];
       };
+      // the element loops below run in parallel: each writes its own slices, errors are
+      // collected and raised after the loop
+      std::atomic<const char*> bad{nullptr};
+      auto flag = [&](const char* msg) {
+        const char* none = nullptr;
+        bad.compare_exchange_strong(none, msg);
+      };
       // volume geometry
-      std::vector<float> geo;
       std::vector<double> wedge_pts, wedge_w;
       if (t == WEDGE) {
         std::vector<double> tp, tww, sx, sw;
@@ -596,8 +620,13 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
           }
         td.nc = (int)wedge_w.size();
       }
+      const int gstride = t == HEX ? 24 : t == TET ? 12 : t == PYR ? 10 * Np : 12 * td.nc;
+      std::vector<float> geo((size_t)K * gstride, 0.f);
+#pragma omp parallel for schedule(dynamic, 256)
       for (int64_t e = 0; e < K; ++e) {
-        load_xv(e);
+        double xv[24];
+        load_xv(e, xv);
+        float* ge = geo.data() + (size_t)e * gstride;
         double F[9], G[9];
         if (t == HEX) {
           // x = c0 + c1 r + c2 s + c3 t + c4 rs + c5 rt + c6 st + c7 rst (coefficients c1..c7)
@@ -610,58 +639,60 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
               for (int dd = 0; dd < 3; ++dd) cf[mm][dd] += 0.125 * mon[mm] * xv[3 * v + dd];
           }
           for (int mm = 1; mm < 8; ++mm)
-            for (int dd = 0; dd < 3; ++dd) geo.push_back((float)cf[mm][dd]);
-          geo.insert(geo.end(), {0.f, 0.f, 0.f});
+            for (int dd = 0; dd < 3; ++dd) ge[3 * (mm - 1) + dd] = (float)cf[mm][dd];
           double jmin = 1e300;
           for (int n = 0; n < Np; ++n) {
-            map_jacobian(HEX, xv.data(), &B[t].nodes[3 * n], F);
+            map_jacobian(HEX, xv, &B[t].nodes[3 * n], F);
             double J = det3(F);
             jmin = std::min(jmin, J);
             jinvmax[t][e] = std::max(jinvmax[t][e], 1.0 / J);
           }
-          if (!(jmin > 0)) throw SetupError(DG_EMESH, "hexahedron with J <= 0");
+          if (!(jmin > 0)) flag("hexahedron with J <= 0");
         } else if (t == TET) {
           double rst0[3] = {-1, -1, -1};
-          map_jacobian(TET, xv.data(), rst0, F);
+          map_jacobian(TET, xv, rst0, F);
           double J = inverse_metric(F, G);
-          if (!(J > 0)) throw SetupError(DG_EMESH, "tetrahedron with J <= 0");
-          for (int i = 0; i < 9; ++i) geo.push_back((float)G[i]);
-          geo.insert(geo.end(), {(float)J, 0.f, 0.f});
+          if (!(J > 0)) flag("tetrahedron with J <= 0");
+          for (int i = 0; i < 9; ++i) ge[i] = (float)G[i];
+          ge[9] = (float)J;
           jinvmax[t][e] = 1.0 / J;
         } else if (t == PYR) {
           for (int n = 0; n < Np; ++n) {
             double a = B[t].lev_x[B[t].mk[n]][B[t].mi[n]], b = B[t].lev_x[B[t].mk[n]][B[t].mj[n]];
             double rst[3] = {0.5 * (a - 1), 0.5 * (b - 1), 0.0};
-            map_jacobian(PYR, xv.data(), rst, F);
+            map_jacobian(PYR, xv, rst, F);
             double J = inverse_metric(F, G);
-            if (!(J > 0)) throw SetupError(DG_EMESH, "pyramid with J <= 0");
-            for (int i = 0; i < 9; ++i) geo.push_back((float)G[i]);
-            geo.push_back((float)J);
+            if (!(J > 0)) flag("pyramid with J <= 0");
+            for (int i = 0; i < 9; ++i) ge[10 * n + i] = (float)G[i];
+            ge[10 * n + 9] = (float)J;
             jinvmax[t][e] = std::max(jinvmax[t][e], 1.0 / J);
           }
         } else {  // wedge
           for (int q = 0; q < td.nc; ++q) {
-            map_jacobian(WEDGE, xv.data(), &wedge_pts[3 * q], F);
+            map_jacobian(WEDGE, xv, &wedge_pts[3 * q], F);
             double J = inverse_metric(F, G);
-            if (!(J > 0)) throw SetupError(DG_EMESH, "wedge with J <= 0");
+            if (!(J > 0)) flag("wedge with J <= 0");
             double gJ[3];
-            wedge_grad_J(xv.data(), &wedge_pts[3 * q], gJ);
-            for (int i = 0; i < 9; ++i) geo.push_back((float)G[i]);
+            wedge_grad_J(xv, &wedge_pts[3 * q], gJ);
+            for (int i = 0; i < 9; ++i) ge[12 * q + i] = (float)G[i];
             for (int dd = 0; dd < 3; ++dd) {
               double gx = G[0 + dd] * gJ[0] + G[3 + dd] * gJ[1] + G[6 + dd] * gJ[2];
-              geo.push_back((float)(gx / (2.0 * J)));
+              ge[12 * q + 9 + dd] = (float)(gx / (2.0 * J));
             }
           }
         }
       }
+      if (bad.load()) throw SetupError(DG_EMESH, bad.load());
       td.geo = upload(geo, owned);
 
       // face geometry (non-hex: stored; all types: time-step data)
-      std::vector<float4> sgeo, sgeo2;
-      std::vector<float> sisq, sisq2;
-      double js0 = 0.0;
+      const size_t nfq = (size_t)K * nf * nq;
+      std::vector<float4> sgeo(t == HEX ? 0 : nfq), sgeo2(t == HEX ? 0 : nfq);
+      std::vector<float> sisq(t == WEDGE ? nfq : 0), sisq2(t == WEDGE ? nfq : 0);
+#pragma omp parallel for schedule(dynamic, 256)
       for (int64_t e = 0; e < K; ++e) {
-        load_xv(e);
+        double xv[24];
+        load_xv(e, xv);
         for (int f = 0; f < nf; ++f) {
           int64_t s = td.side_off + e * nf + f;
           int fnv = face_nverts(t, f);
@@ -672,6 +703,7 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
           const double* og = face_outward(t, f);
           taup[t][e] = std::max(taup[t][e], taud[s]);
           tauu[t][e] = std::max(tauu[t][e], 1.0 / taud[s]);
+          double js0 = 0.0;
           for (int pass = 0; pass < (t == HEX ? 1 : 2); ++pass)
           for (int q = 0; q < nq; ++q) {
             double rst[3], d1[3], d2[3], F[9], G[9];
@@ -680,7 +712,7 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
             static const int ident[4] = {0, 1, 2, 3};
             const int* kk = (pass == 1 && fnv == 4) ? ident : key;
             face_point(t, f, kk, pts[2 * q], pts[2 * q + 1], rst, d1, d2);
-            map_jacobian(t, xv.data(), rst, F);
+            map_jacobian(t, xv, rst, F);
             double J = inverse_metric(F, G);
             double x1[3], x2[3], nn[3];
             for (int dd = 0; dd < 3; ++dd) {
@@ -699,7 +731,7 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
               jsmax[t][e] = std::max(jsmax[t][e], Js / Jsref);
               jsj[t][e] = std::max(jsj[t][e], Js / Jsref / J);
             }
-            if (!(J > 0)) throw SetupError(DG_EMESH, "J <= 0 at a face point");
+            if (!(J > 0)) flag("J <= 0 at a face point");
             if (t != HEX) {
               double wj = w[q] * Js;
               if (t == WEDGE) wj /= std::sqrt(J);
@@ -709,15 +741,17 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
                 wj = Js;
                 if (q == 0) js0 = Js;
                 else if (std::fabs(Js - js0) > 1e-9 * js0)
-                  throw SetupError(DG_EMESH, "triangle face of a tet or pyramid is not affine");
+                  flag("triangle face of a tet or pyramid is not affine");
               }
+              const size_t at = ((size_t)e * nf + f) * nq + q;
               float4 gv = make_float4((float)(nn[0] / nl), (float)(nn[1] / nl), (float)(nn[2] / nl), (float)wj);
-              (pass == 0 ? sgeo : sgeo2).push_back(gv);
-              if (t == WEDGE) (pass == 0 ? sisq : sisq2).push_back((float)(1.0 / std::sqrt(J)));
+              (pass == 0 ? sgeo : sgeo2)[at] = gv;
+              if (t == WEDGE) (pass == 0 ? sisq : sisq2)[at] = (float)(1.0 / std::sqrt(J));
             }
           }
         }
       }
+      if (bad.load()) throw SetupError(DG_EMESH, bad.load());
       if (t != HEX) {
         td.sgeo = upload(sgeo, owned);
         td.sgeo2 = upload(sgeo2, owned);
@@ -743,7 +777,7 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
         for (int i = 0; i < n1; ++i) hc.push_back((float)B[t].r1[i]);
         for (int i = 0; i < n1; ++i) hc.push_back((float)(1.0 / B[t].w1[i]));
         m->hexc = upload(hc, owned);
-        if (!g_host_only && dgk::upload_hex_constants(N, hc.data(), (int)hc.size()) != cudaSuccess)
+        if (!g_host_only && dgk::upload_hex_constants(N, sem, hc.data(), (int)hc.size()) != cudaSuccess)
           throw SetupError(DG_ECUDA, "constant upload failed");
         // local face point (iu + n1 iv) -> canonical index, per code
         std::vector<int> perm(dgk::NCODES * nq, 0);

@@ -21,6 +21,7 @@ HEX, WEDGE, PYR, TET = 0, 1, 2, 3
 EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_host_check", "dg_layout", "dg_ndof", "dg_level_counts",
            "dg_set_state", "dg_get_state", "dg_rhs", "dg_timestep", "dg_step", "dg_state_ptr",
            "dg_energy", "dg_energy_noalloc", "dg_profile", "dg_watchdog_selftest", "dg_adjoint_step",
+           "dg_batch_create", "dg_batch_step", "dg_batch_stats", "dg_batch_destroy",
            "dg_status_string", "dg_last_error")
 
 
@@ -50,6 +51,12 @@ _lib.dg_energy.argtypes = [_vp, _vp, C.POINTER(C.c_double)]
 _lib.dg_energy_noalloc.argtypes = [_vp, _vp, C.POINTER(C.c_double)]
 _lib.dg_watchdog_selftest.argtypes = [_vp, C.c_int64]
 _lib.dg_profile.argtypes = [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+_lib.dg_batch_create.argtypes = [C.POINTER(_vp), C.c_int, _vp, C.POINTER(_vp)]
+_lib.dg_batch_step.argtypes = [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+_lib.dg_batch_stats.argtypes = [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+_lib.dg_batch_destroy.argtypes = [_vp]
+_lib.dg_batch_destroy.restype = None
+BATCH_CHUNK = 3   # DG_BATCH_CHUNK
 _lib.dg_status_string.restype = C.c_char_p
 _lib.dg_status_string.argtypes = [C.c_int]
 _lib.dg_last_error.restype = C.c_char_p
@@ -191,3 +198,37 @@ class Mesh:
         E = C.c_double()
         _check(_lib.dg_energy(self._h, _ptr(q_dev) if q_dev is not None else None, C.byref(E)))
         return E.value
+
+
+class Batch:
+    """A dg_batch: several Mesh objects stepped through one captured CUDA graph (include/dg.h).
+    The meshes must outlive the batch."""
+
+    def __init__(self, meshes, stream=None):
+        self.meshes = list(meshes)
+        arr = (_vp * len(self.meshes))(*[g._h for g in self.meshes])
+        h = _vp()
+        _check(_lib.dg_batch_create(arr, len(self.meshes), _vp(stream or 0), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.dg_batch_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def step(self, nsteps, dt=None, t=None):
+        """dg_batch_step; dt, t: per-mesh sequences (None = each mesh's dt_min / not reported).
+        Returns the updated times."""
+        n = len(self.meshes)
+        dta = (C.c_double * n)(*(dt if dt is not None else [0.0] * n))
+        ta = (C.c_double * n)(*(t if t is not None else [0.0] * n))
+        _check(_lib.dg_batch_step(self._h, int(nsteps), dta, ta))
+        return list(ta)
+
+    def stats(self):
+        """(graph replays, graph captures) since creation."""
+        r, c = C.c_int64(), C.c_int64()
+        _check(_lib.dg_batch_stats(self._h, C.byref(r), C.byref(c)))
+        return r.value, c.value

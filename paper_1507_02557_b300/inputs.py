@@ -218,3 +218,28 @@ def scale_mesh(nx=64, ny=64, seed=0):
 def random_state(ndof, seed=0):
     """(4, ndof) float64 standard-normal state: p, u, v, w."""
     return np.random.default_rng(seed).standard_normal((4, ndof))
+
+
+def batch_specs(count=256, seed=0, nmin=6, nmax=40):
+    """Seeded recipe of the many-mesh workload, one (n, N, layers, c per layer) per mesh:
+    n log-uniform in [nmin, nmax] (an n x n x n cell grid), N uniform in {2..6}, layer codes
+    H*a | W | H*b | T | K*k with k = max(1, round(0.05 n)), a = (n - 2 - k) // 2,
+    b = n - 2 - k - a, and c uniform in [1, 3] per layer."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(round(float(np.exp(rng.uniform(np.log(nmin), np.log(nmax))))))
+        N = int(rng.integers(2, 7))
+        k = max(1, int(round(0.05 * n)))
+        a = (n - 2 - k) // 2
+        b = n - 2 - k - a
+        layers = "H" * a + "W" + "H" * b + "T" + "K" * k
+        c = rng.uniform(1.0, 3.0, size=len(layers))
+        out.append((n, N, layers, c))
+    return out
+
+
+def batch_mesh(spec, seed=0):
+    """The layered mesh of one batch_specs entry (c^2 from its per-layer wave speeds)."""
+    n, _, layers, c = spec
+    return layered_mesh(n, n, n, layers, seed=seed, c_of_layer=lambda k: float(c[k]))

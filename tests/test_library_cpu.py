@@ -94,3 +94,15 @@ def test_host_setup_multirate_levels_match_oracle():
     lev, _ = mr_levels(o, [trace_constant(t, N) for t in range(4)], 2)
     want = [sum(int(np.sum(l == L)) for l in lev) for L in (1, 2)]
     assert lc == want and lc[1] > 0
+
+
+def test_batch_calls_reject_bad_arguments_without_a_device():
+    """dg_batch_* argument checks come before any CUDA call."""
+    import ctypes as C
+    h = C.c_void_p()
+    assert dg._lib.dg_batch_create(None, 0, None, C.byref(h)) == -1 and not h.value
+    arr = (C.c_void_p * 2)(None, None)
+    assert dg._lib.dg_batch_create(arr, 2, None, C.byref(h)) == -1
+    assert dg._lib.dg_batch_step(None, 3, None, None) == -1
+    assert dg._lib.dg_batch_stats(None, None, None) == -1
+    dg._lib.dg_batch_destroy(None)
