@@ -66,7 +66,7 @@ typedef struct {
                               pyramid base (r,s) lexicographic at t=-1, apex (-1,-1,1);
                               tet (-1,-1,-1),(1,-1,-1),(-1,1,-1),(-1,-1,1) */
   const double *c2[4];     /* host, [nelem] squared wave speed per element (> 0) */
-  int N;                   /* polynomial order, 1..6 */
+  int N;                   /* polynomial order, 1..7 */
   int hex_basis;           /* 0 = GL nodes; 1 = SEM: GLL nodes and GLL points on every quad face */
   int pyr_form;            /* 0 = skew-symmetric, 1 = strong (identical results, Sec. 2.2) */
   double tau_scale;        /* 1 = upwind, 0 = central flux */

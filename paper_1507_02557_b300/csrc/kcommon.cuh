@@ -36,6 +36,7 @@ struct Args {
   const float* sisq2;
   const float* ops2;
   const int* iops2;
+  int nops2;          // floats in ops2 (layout check of the orientation-free kernels)
   int* err;           // device error word (bit 0: a bounded wait timed out)
   const int* elist;   // optional element list (multi-rate levels); NULL = elements 0..K-1
   int K;              // number of elements processed

@@ -1314,6 +1314,7 @@ static Args make_args(dg_mesh* m, int t) {
   A.sisq2 = td.sisq2;
   A.ops2 = td.ops2;
   A.iops2 = td.iops2;
+  A.nops2 = td.nops2;
   A.K = td.K;
   A.elist = nullptr;
   A.err = m->derr;
@@ -1396,7 +1397,7 @@ static void launch_type(dg_mesh* m, const Args& A, int t) {
     else if (t == DG_PYR) launch_gen_n<DG_PYR, NN, (MODE > 2 ? 1 : MODE)>(A, s);       \
     else launch_gen_n<DG_TET, NN, (MODE > 2 ? 1 : MODE)>(A, s);                        \
     break;
-    DG_CASE(1) DG_CASE(2) DG_CASE(3) DG_CASE(4) DG_CASE(5) DG_CASE(6)
+    DG_CASE(1) DG_CASE(2) DG_CASE(3) DG_CASE(4) DG_CASE(5) DG_CASE(6) DG_CASE(7)
 #undef DG_CASE
     default: break;
   }
@@ -1538,7 +1539,7 @@ cudaError_t launch_energy(dg_mesh* m, const float* q, double* acc) {
     if (A[2].K) energy_kernel<DG_PYR, NN><<<egrid(2), 256, 0, s>>>(A[2], nullptr, acc);              \
     if (A[3].K) energy_kernel<DG_TET, NN><<<egrid(3), 256, 0, s>>>(A[3], m->tet_chol_dev, acc);      \
     break;
-    DG_CASE(1) DG_CASE(2) DG_CASE(3) DG_CASE(4) DG_CASE(5) DG_CASE(6)
+    DG_CASE(1) DG_CASE(2) DG_CASE(3) DG_CASE(4) DG_CASE(5) DG_CASE(6) DG_CASE(7)
 #undef DG_CASE
     default: break;
   }

@@ -34,8 +34,6 @@ struct G2 {
   static constexpr int NTRI = T == DG_WEDGE ? 2 : 4;
   static constexpr int NQUAD = NF - NTRI;
   static constexpr int NC = T == DG_WEDGE ? (N + 1) * (N + 1) * (N + 1) : 0;
-  // warps per block (one block per SM): the pyramid's 22 fill the shared memory at N = 4
-  static constexpr int NW = T == DG_PYR ? 22 : 16;
   static constexpr int N1 = N + 1, NT = NFN;                            // wedge: 1D points, triangle modes
   static constexpr int VOL = T == DG_WEDGE ? NQ * NT * 4 + 2 * N1 * N1 + NQ * N1 : NP * NP * 4;
   static constexpr int NKL = (N + 1) * (N + 2) / 2;                   // pyramid (level k, index l <= k)
@@ -55,8 +53,26 @@ struct G2 {
   // V4 (canonical lattice values)
   static constexpr int WB = NP + (T == DG_WEDGE ? 2 * NT * N1 + 2 * NC : NP) + NF * NQ + 2 * NTRI * NFN +
                             (T == DG_PYR ? NKL * N1 + NQ : 0);
-  static constexpr int SMEM = OPS_B + IOPS_B + NW * WB * 16;
+  // tet / pyramid: the volume operator transposed, (D^T)[m][n] = D[n][m] as float4, follows the
+  // operators in global memory at float offset OPS_T (host layout size NOPS)
+  static constexpr int OPS_T = ((OPS + 3) / 4) * 4;
+  static constexpr int NOPS = OPS_T + (T == DG_WEDGE ? 0 : VOL);
+  // one block per SM.  Warps per block: 16 (pyramid 22, which fill the shared memory at N = 4),
+  // fewer where the per-warp buffers do not fit.  The operators sit in shared memory while at
+  // least 6 warps fit beside them (N <= 4: all of them); otherwise the kernel reads them from
+  // global memory through L1, the volume operator in its transposed copy so that the lanes'
+  // reads of one column are contiguous.
+  static constexpr int SMEM_CAP = 226 * 1024;
+  static constexpr int NW_DEF = T == DG_PYR ? 22 : 16;
+  static constexpr int WB_B = WB * 16;
+  static constexpr int NW_SM = (SMEM_CAP - OPS_B - IOPS_B) / WB_B;
+  static constexpr bool OPS_SMEM = NW_SM >= (N <= 4 ? NW_DEF : 6);
+  static constexpr int NW_FIT = OPS_SMEM ? NW_SM : (SMEM_CAP - IOPS_B) / WB_B;
+  static constexpr int NW = NW_FIT < NW_DEF ? NW_FIT : NW_DEF;
+  static constexpr int SMEM = (OPS_SMEM ? OPS_B : 0) + IOPS_B + NW * WB_B;
   static constexpr int R = (NP + 31) / 32;
+  static_assert(N > 4 || (OPS_SMEM && NW == NW_DEF), "N <= 4 keeps its operators and warps in shared memory");
+  static_assert(NW >= 1, "per-warp buffers exceed the shared memory");
 };
 
 __device__ __forceinline__ float4 f4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
@@ -87,12 +103,17 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
   constexpr int NP = C::NP, NQ = C::NQ, NFN = C::NFN, NF = C::NF, NTRI = C::NTRI, NQUAD = C::NQUAD;
   constexpr int NC = C::NC, NW = C::NW, R = C::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* sop = reinterpret_cast<float*>(smem_raw);
-  int* sio = reinterpret_cast<int*>(smem_raw + C::OPS_B);
-  float4* swarp = reinterpret_cast<float4*>(smem_raw + C::OPS_B + C::IOPS_B);
-  for (int x = threadIdx.x; x < C::OPS; x += blockDim.x) sop[x] = A.ops2[x];
+  constexpr int OPS_SB = C::OPS_SMEM ? C::OPS_B : 0;
+  int* sio = reinterpret_cast<int*>(smem_raw + OPS_SB);
+  float4* swarp = reinterpret_cast<float4*>(smem_raw + OPS_SB + C::IOPS_B);
+  if constexpr (C::OPS_SMEM) {
+    float* sops = reinterpret_cast<float*>(smem_raw);
+    for (int x = threadIdx.x; x < C::OPS; x += blockDim.x) sops[x] = A.ops2[x];
+  }
   for (int x = threadIdx.x; x < C::IOPS; x += blockDim.x) sio[x] = A.iops2[x];
   __syncthreads();
+  const float* sop = C::OPS_SMEM ? reinterpret_cast<const float*>(smem_raw) : A.ops2;
+  const float4* DT4 = reinterpret_cast<const float4*>(A.ops2 + C::OPS_T);   // global: D^T (tet, pyramid)
 
   const float4* DV4 = reinterpret_cast<const float4*>(sop);     // tet/pyr [NP][NP]; wedge Vt4 [NQ][NT]
   const float* V1 = sop + NQ * C::NT * 4;                        // wedge [N1][N1] (l, j)
@@ -311,7 +332,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
           const float4* drow = DV4 + n * NP;
           #pragma unroll 4
         for (int m = 0; m < NP; ++m) {
-            const float4 d = drow[m], w = W4[m];
+            const float4 d = C::OPS_SMEM ? drow[m] : __ldg(DT4 + m * NP + n), w = W4[m];
             dvr = fmaf(d.x, w.x, dvr);
             dvs = fmaf(d.y, w.y, dvs);
             dvt = fmaf(d.z, w.z, dvt);
@@ -344,7 +365,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
             pr = fmaf(dc.x, w.x, pr);
             ps = fmaf(dc.y, w.y, ps);
             pt = fmaf(dc.z, w.z, pt);
-            const float4 dr = DV4[n * NP + m];
+            const float4 dr = C::OPS_SMEM ? DV4[n * NP + m] : __ldg(DT4 + m * NP + n);
             dpr = fmaf(dr.x, w.w, dpr);
             dps = fmaf(dr.y, w.w, dps);
             dpt = fmaf(dr.z, w.w, dpt);
@@ -670,7 +691,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
 template <int T, int N, int MODE>
 static bool launch_one(const Args& A, cudaStream_t s) {
   using C = G2<T, N>;
-  if (C::SMEM > 227 * 1024) return false;
+  if (A.nops2 != C::NOPS) return false;   // host operator layout of another (type, N)
   static int blocks = 0;   // persistent grid: resident blocks per SM x SMs (computed once)
   if (blocks == 0) {
     if (cudaFuncSetAttribute(gen2_kernel<T, N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
@@ -700,7 +721,7 @@ bool launch_gen2(int t, int N, const Args& A, cudaStream_t s) {
     if (t == DG_PYR) return launch_one<DG_PYR, NN, MODE>(A, s);            \
     if (t == DG_WEDGE) return launch_one<DG_WEDGE, NN, MODE>(A, s);        \
     return false;
-    G2_CASE(1) G2_CASE(2) G2_CASE(3) G2_CASE(4)
+    G2_CASE(1) G2_CASE(2) G2_CASE(3) G2_CASE(4) G2_CASE(5) G2_CASE(6) G2_CASE(7)
 #undef G2_CASE
     default: return false;
   }

@@ -151,6 +151,7 @@ extern "C" dg_status dg_energy_noalloc(dg_mesh* m, const float* q, double* E) {
     case 4: launch_parts<4>(m, q, part); break;
     case 5: launch_parts<5>(m, q, part); break;
     case 6: launch_parts<6>(m, q, part); break;
+    case 7: launch_parts<7>(m, q, part); break;
     default: return DG_ENOTSUP;
   }
   ordered_sum<<<1, 1024, 0, m->stream>>>(part, nel);

@@ -1190,6 +1190,15 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
           }
         }
         for (double v : E) o2.push_back((float)v);
+        if (t != WEDGE) {
+          // the volume operator transposed (float4 rows), 16-byte aligned after the operators
+          while (o2.size() % 4) o2.push_back(0.f);
+          std::vector<float> dt4((size_t)Np * Np * 4);
+          for (int n = 0; n < Np; ++n)
+            for (int mm = 0; mm < Np; ++mm)
+              for (int c = 0; c < 4; ++c) dt4[((size_t)mm * Np + n) * 4 + c] = o2[((size_t)n * Np + mm) * 4 + c];
+          o2.insert(o2.end(), dt4.begin(), dt4.end());
+        }
         td.ops2 = upload(o2, owned);
         td.iops2 = upload(i2, owned);
         td.nops2 = (int)o2.size();

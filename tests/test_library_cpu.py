@@ -66,7 +66,7 @@ def test_host_setup_sem_matches_oracle_and_table(N):
 def test_host_setup_rejects_bad_meshes():
     m = small_hybrid_mesh()
     with pytest.raises(dg.DGError, match="not supported"):
-        dg.host_check(m, 7)
+        dg.host_check(m, 8)
     bad = small_hybrid_mesh()
     c = bad.conn[0].copy()
     c[0] = c[0][[1, 0, 3, 2, 5, 4, 7, 6]]          # mirrored hexahedron: J < 0
