@@ -202,10 +202,31 @@ dg_status dg_batch_step(dg_batch *batch, int nsteps, const double *dt, double *t
 dg_status dg_batch_stats(const dg_batch *batch, int64_t *replays, int64_t *captures);
 void dg_batch_destroy(dg_batch *batch);
 
-/* Adjoint of dg_step (gradient w.r.t. c^2 and source amplitude): not built,
- * returns DG_ENOTSUP. */
-dg_status dg_adjoint_step(dg_mesh *mesh, int nsteps, float *lambda_dev, double *grad_c2_dev,
-                          double *grad_amp);
+/* Discrete adjoint of nsteps single-rate LSRK(5,4) steps of size dt (dt <= 0:
+ * dt_min, as dg_step) started from the mesh's current state q_0 (a checkpoint).
+ * No counterpart in the paper: the exact derivative of the discrete map of
+ * Sec. 2.2-2.4 (the FP32 forward kernels, recomputed from q_0), for a loss L of
+ * q_n = the state after the nsteps steps.
+ *   lambda_dev   device [4][ndof] FP32: dL/dq_n on entry, dL/dq_0 on return.
+ *   grad_c2_dev  device, one double per element in the type order of dg_layout
+ *                (hexahedra, wedges, pyramids, tets; element order within a
+ *                type), or NULL: dL/dc^2_K is ADDED to it (c^2 enters through
+ *                1/rho = c^2 and through tau_p = 1/{rho c}, tau_u = {rho c} on
+ *                the element's faces).  Contributions are summed with atomics:
+ *                the last bits vary from run to run.
+ *   grad_amp     must be NULL (the library has no source term; DG_ENOTSUP).
+ * The transpose of the operator is applied as R^T = W F R F W^{-1} with
+ * W = blockdiag(M, M/c^2) the energy weight and F = diag(1,-1,-1,-1), exact
+ * for GL hexahedra and skew-form pyramids; DG_ENOTSUP for SEM hexahedra,
+ * strong-form pyramids and nlevels = 2.  The mesh state is left unchanged; the
+ * LSRK residual and trace buffers are overwritten.  Allocates nsteps + 9 state
+ * copies of scratch on first use (kept until the mesh is destroyed or a larger
+ * nsteps needs more) and synchronises on that first use only; otherwise
+ * asynchronous on the mesh's stream.  Chain windows of steps by calling it per
+ * window, last window first, after restoring each window's checkpoint with
+ * dg_set_state. */
+dg_status dg_adjoint_step(dg_mesh *mesh, int nsteps, double dt, float *lambda_dev,
+                          double *grad_c2_dev, double *grad_amp);
 
 const char *dg_status_string(dg_status s);
 /* Message of the last DG_ECUDA / DG_EMESH / DG_EINVAL error on this thread. */

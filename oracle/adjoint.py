@@ -101,10 +101,17 @@ def c2_term(o: DGOracle, q, rho):
 
 
 def adjoint_steps(o: DGOracle, q0, lam, dt, nsteps, Rm=None):
-    """(dL/dq_0, dL/dc^2 per type) for lambda = dL/dq_n after nsteps LSRK(5,4) steps from q0."""
-    if Rm is None:
-        Rm = dense_rhs(o)
+    """(dL/dq_0, dL/dc^2 per type) for lambda = dL/dq_n after nsteps LSRK(5,4) steps from q0.
+    R^T from the dense matrix Rm (computed when None), or, with Rm = "similarity", as
+    W F R F W^{-1} (for meshes too large for the dense matrix; the identity is pinned on the
+    dense matrices)."""
     shape = (4, o.ndof)
+    if isinstance(Rm, str):
+        rt = lambda x: apply_w(o, flip(o.rhs(flip(apply_winv(o, x)))))
+    else:
+        if Rm is None:
+            Rm = dense_rhs(o)
+        rt = lambda x: (Rm.T @ x.ravel()).reshape(shape)
     states = [q0.copy()]
     for _ in range(nsteps - 1):
         states.append(o.lsrk_step(states[-1], dt))
@@ -120,7 +127,7 @@ def adjoint_steps(o: DGOracle, q0, lam, dt, nsteps, Rm=None):
         rho = np.zeros(shape)
         for k in range(4, -1, -1):
             rho = rho + LSRK_B[k] * lam
-            lam = lam + dt * (Rm.T @ rho.ravel()).reshape(shape)
+            lam = lam + dt * rt(rho)
             for t, gt in enumerate(c2_term(o, Q[k], rho)):
                 g[t] += dt * gt
             rho = LSRK_A[k] * rho

@@ -8,15 +8,15 @@
 
 #include "internal.h"
 
-namespace {
-thread_local std::string g_err;
-
 // Carpenter & Kennedy (1994) five-stage fourth-order 2N-storage Runge-Kutta.
 const double RK_A[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
                         -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
 const double RK_B[5] = {1432997174477.0 / 9575080441904.0, 5161836677717.0 / 13612068292357.0,
                         1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
                         2277821191437.0 / 14882151754819.0};
+
+namespace {
+thread_local std::string g_err;
 
 dg_status cuda_fail(cudaError_t e) {
   g_err = cudaGetErrorString(e);
@@ -396,10 +396,21 @@ dg_status dg_profile(dg_mesh* m, int enable, double* ms, int64_t* launches) {
   return DG_OK;
 }
 
-dg_status dg_adjoint_step(dg_mesh* m, int nsteps, float* lambda, double* g_c2, double* g_amp) {
-  (void)m; (void)nsteps; (void)lambda; (void)g_c2; (void)g_amp;
-  g_err = "adjoint not built";
-  return DG_ENOTSUP;
+dg_status dg_adjoint_step(dg_mesh* m, int nsteps, double dt, float* lambda, double* g_c2, double* g_amp) {
+  if (!m || nsteps < 0 || !lambda) return DG_EINVAL;
+  if (g_amp) {
+    g_err = "the library has no source term: grad_amp must be NULL";
+    return DG_ENOTSUP;
+  }
+  if (m->nlevels != 1 || m->hex_sem || m->pyr_form != 0) {
+    g_err = "adjoint built for single-rate LSRK with GL hexahedra and skew-form pyramids";
+    return DG_ENOTSUP;
+  }
+  if (!(dt > 0)) dt = m->dt_min;
+  if (nsteps == 0) return DG_OK;
+  cudaError_t e = dg_adjoint_run(m, nsteps, dt, lambda, g_c2);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return DG_OK;
 }
 
 }  // extern "C"

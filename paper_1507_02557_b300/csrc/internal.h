@@ -86,6 +86,16 @@ struct dg_mesh {
   bool mr_started = false;
   bool hex_sem = false;           // SEM hexahedra (GLL nodes)
   bool tri_lat = true;            // tet / pyramid triangle faces exchange lattice values (gen2)
+  bool wall_self = false;         // trace launches also write a wall side's own trace into its slot
+  // adjoint (adjoint.cu): host data kept by the setup, device copies made on first use
+  std::vector<float> face_w;      // [nsides][nq] w_q J^s at the canonical points (lattice faces: J^s)
+  std::vector<double> face_mass;  // [nfn][nfn] face mass of the triangle lattice basis
+  std::vector<double> tet_mhat_inv;
+  float* face_w_dev = nullptr;
+  float* face_mass_dev = nullptr;
+  float* tet_minv_dev = nullptr;
+  float* adj_buf = nullptr;       // scratch states of the reverse sweep
+  size_t adj_states = 0;
   int* derr = nullptr;            // device error word: bit 0 = a bounded device wait timed out
   dgk::TmaArr tma[5];             // q, res, hist, trace, trace3 (hex TMA staging)
   // per-type kernel timing (dg_profile): event pairs recorded around each launch
@@ -120,14 +130,25 @@ cudaError_t upload_hex_constants(int N, bool sem, const float* hc, int count);
 // Message returned by dg_last_error() on this thread (api.cpp).
 void dg_set_last_error(const std::string& msg);
 
+// Carpenter & Kennedy (1994) LSRK(5,4) coefficients (api.cpp).
+extern const double RK_A[5];
+extern const double RK_B[5];
+
 // nsteps time steps of m on m->stream: LSRK(5,4), or multi-rate AB3 whose first call also runs the
 // start-up (nsteps = 0 runs the start-up alone).  No synchronization (api.cpp).
 cudaError_t dg_enqueue_steps(dg_mesh* m, int nsteps, double dt);
 // Simulated time that dg_enqueue_steps(m, nsteps, dt) advances; fresh = the start-up runs too.
 double dg_step_time(const dg_mesh* m, int nsteps, double dt, bool fresh);
 
+// Reverse sweep of nsteps LSRK(5,4) steps of dt from the state m->q (adjoint.cu): lam (device,
+// [4][ndof]) holds dL/dq_n on entry and dL/dq_0 on return; grad (device, one double per element
+// in type order, or NULL) accumulates dL/dc^2.  Enqueued on m->stream; m->q is left unchanged.
+cudaError_t dg_adjoint_run(dg_mesh* m, int nsteps, double dt, float* lam, double* grad);
+
 // Host setup (setup.cpp).
 dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err);
 void dg_free(dg_mesh* m);
+// cudaMalloc whose block dg_free releases with the mesh's other buffers (NULL on failure).
+void* dg_alloc_owned(dg_mesh* m, size_t bytes);
 // Host setup without any device allocation or transfer (dg_host_check).
 dg_status dg_setup_host_only(dg_mesh* m, const dg_mesh_desc* d, std::string& err, double ct[4]);

@@ -215,7 +215,8 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
       const int ax = f >> 1;
       const int64_t gs = A.side_off + e * 6 + f;
       const int nb = A.nbr[gs];
-      if (nb < 0) continue;
+      const int64_t dst = nb >= 0 ? (int64_t)nb : (A.wall_self ? gs : -1);
+      if (dst < 0) continue;
       const float* V = (f & 1) ? s_Vp : s_Vm;
       float nv[3];
       if (MODE == MODE_STAGE) {
@@ -248,8 +249,8 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
         tr[fl] = acc;
       }
       const int cidx = s_perm[A.code[gs] * NQ + lp];
-      A.tout[(int64_t)nb * NQ + cidx] = tr[0];
-      A.tout[A.plane + (int64_t)nb * NQ + cidx] = nv[0] * tr[1] + nv[1] * tr[2] + nv[2] * tr[3];
+      A.tout[dst * NQ + cidx] = tr[0];
+      A.tout[A.plane + dst * NQ + cidx] = nv[0] * tr[1] + nv[1] * tr[2] + nv[2] * tr[3];
     }
   }
 }
@@ -873,7 +874,8 @@ __global__ void __launch_bounds__(128, DG_HEXP_MINB) hexw_kernel(Args A, const _
           for (int sd = 0; sd < 2; ++sd) {
             const int f = 2 * ax + sd;
             const int nb = s_nb[f];
-            if (nb < 0) continue;
+            const int64_t dst = nb >= 0 ? (int64_t)nb : (A.wall_self ? A.side_off + e * 6 + f : -1);
+            if (dst < 0) continue;
             float nv[3];
             if (MODE != MODE_TRACE) {
               const float4 nn = s_N[f * NQ + col];
@@ -886,8 +888,8 @@ __global__ void __launch_bounds__(128, DG_HEXP_MINB) hexw_kernel(Args A, const _
             }
             const float4 tr = sd ? tp : tm;
             const int cidx = s_perm[s_code[f] * NQ + col];
-            tout[(int64_t)nb * NQ + cidx] = tr.x;
-            tout[A.plane + (int64_t)nb * NQ + cidx] = nv[0] * tr.y + nv[1] * tr.z + nv[2] * tr.w;
+            tout[dst * NQ + cidx] = tr.x;
+            tout[A.plane + dst * NQ + cidx] = nv[0] * tr.y + nv[1] * tr.z + nv[2] * tr.w;
           }
         }
       }
@@ -1198,7 +1200,8 @@ __global__ void __launch_bounds__(128) gen_kernel(Args A) {
       const int f = fq / NQ, qq = fq % NQ;
       const int64_t gs = A.side_off + e * NF + f;
       const int nb = A.nbr[gs];
-      if (nb < 0) continue;
+      const int64_t dst = nb >= 0 ? (int64_t)nb : (A.wall_self ? gs : -1);
+      if (dst < 0) continue;
       const float* Tt = A.Tt + ((size_t)(f * NCODES + s_code[f]) * NP) * NQ;
       float tr[4] = {0.f, 0.f, 0.f, 0.f};
       for (int m = 0; m < NP; ++m) {
@@ -1213,8 +1216,8 @@ __global__ void __launch_bounds__(128) gen_kernel(Args A) {
         for (int fl = 0; fl < 4; ++fl) tr[fl] *= is;
       }
       const float4 sg = A.sgeo[sp];
-      A.tout[(int64_t)nb * NQ + qq] = tr[0];
-      A.tout[A.plane + (int64_t)nb * NQ + qq] = sg.x * tr[1] + sg.y * tr[2] + sg.z * tr[3];
+      A.tout[dst * NQ + qq] = tr[0];
+      A.tout[A.plane + dst * NQ + qq] = sg.x * tr[1] + sg.y * tr[2] + sg.z * tr[3];
     }
   }
 }
@@ -1315,6 +1318,7 @@ static Args make_args(dg_mesh* m, int t) {
   A.ops2 = td.ops2;
   A.iops2 = td.iops2;
   A.nops2 = td.nops2;
+  A.wall_self = m->wall_self ? 1 : 0;
   A.K = td.K;
   A.elist = nullptr;
   A.err = m->derr;

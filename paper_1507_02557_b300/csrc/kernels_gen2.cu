@@ -660,7 +660,8 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
         }
         const int64_t gs = A.side_off + e * NF + f;
         const int nb = A.nbr[gs];
-        if (nb < 0) continue;
+        const int64_t dst = nb >= 0 ? (int64_t)nb : (A.wall_self ? gs : -1);
+        if (dst < 0) continue;
         if (LAT) {
           lat_point(fq, f, ci, tr, sg);
         } else {
@@ -669,8 +670,8 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
           ci = tri_of<T>(f) >= 0 ? idx : qperm[code[f] * NQ + idx];
           sg = A.sgeo2[(e * NF + f) * NQ + idx];
         }
-        tout[(int64_t)nb * NQ + ci] = tr.x;
-        tout[A.plane + (int64_t)nb * NQ + ci] = sg.x * tr.y + sg.y * tr.z + sg.z * tr.w;
+        tout[dst * NQ + ci] = tr.x;
+        tout[A.plane + dst * NQ + ci] = sg.x * tr.y + sg.y * tr.z + sg.z * tr.w;
       }
       __syncwarp();
     };

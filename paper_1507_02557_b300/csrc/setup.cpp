@@ -443,6 +443,13 @@ dg_status dg_setup_host_only(dg_mesh* m, const dg_mesh_desc* d, std::string& err
   return st;
 }
 
+void* dg_alloc_owned(dg_mesh* m, size_t bytes) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  owned_list(m).push_back(p);
+  return p;
+}
+
 void dg_free(dg_mesh* m) {
   std::vector<void*> v;
   {
@@ -454,6 +461,8 @@ void dg_free(dg_mesh* m) {
     }
   }
   for (void* p : v) cudaFree(p);
+  if (m->adj_buf) cudaFree(m->adj_buf);
+  m->adj_buf = nullptr;
 }
 
 dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
@@ -588,6 +597,7 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
       tauu[t].assign(K, 0.0);
     }
     std::vector<double> phi(512), grad(3 * 512);
+    m->face_w.assign((size_t)m->nsides * nq, 0.f);
 
     for (int t = 0; t < 4; ++t) {
       auto& td = m->td[t];
@@ -730,6 +740,10 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
             if (pass == 0) {
               jsmax[t][e] = std::max(jsmax[t][e], Js / Jsref);
               jsj[t][e] = std::max(jsj[t][e], Js / Jsref / J);
+              // face measure at the canonical points (adjoint): w J^s, or J^s alone on a face
+              // whose traces are exchanged at the lattice (the face mass carries the weights)
+              const bool lat = m->tri_lat && fnv == 3 && (t == TET || t == PYR);
+              m->face_w[(size_t)s * nq + q] = (float)(lat ? Js : w[q] * Js);
             }
             if (!(J > 0)) flag("J <= 0 at a face point");
             if (t != HEX) {
@@ -836,6 +850,7 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
             }
           }
           Minv = I;
+          m->tet_mhat_inv = Minv;
           std::vector<float> mh(M.begin(), M.end());
           m->tet_mhat_dev = upload(mh, owned);
           // Cholesky factor M = R^T R (R upper triangular): the energy kernel takes p^T M p = |R p|^2
@@ -978,6 +993,7 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
         for (int a = 0; a < nfn; ++a)
           for (int b2 = 0; b2 < nfn; ++b2)
             for (int q = 0; q < nq; ++q) Mf[a * nfn + b2] += tw[q] * E[q * nfn + a] * E[q * nfn + b2];
+        m->face_mass = Mf;
         std::vector<float> o2;
         std::vector<int> i2(tperm.begin(), tperm.end());
         i2.insert(i2.end(), tinv.begin(), tinv.end());

@@ -50,6 +50,7 @@ _lib.dg_state_ptr.argtypes = [_vp, C.POINTER(_vp)]
 _lib.dg_energy.argtypes = [_vp, _vp, C.POINTER(C.c_double)]
 _lib.dg_energy_noalloc.argtypes = [_vp, _vp, C.POINTER(C.c_double)]
 _lib.dg_watchdog_selftest.argtypes = [_vp, C.c_int64]
+_lib.dg_adjoint_step.argtypes = [_vp, C.c_int, C.c_double, _vp, _vp, _vp]
 _lib.dg_profile.argtypes = [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
 _lib.dg_batch_create.argtypes = [C.POINTER(_vp), C.c_int, _vp, C.POINTER(_vp)]
 _lib.dg_batch_step.argtypes = [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -182,6 +183,12 @@ class Mesh:
         E = C.c_double()
         _check(_lib.dg_energy_noalloc(self._h, _ptr(q_dev) if q_dev is not None else None, C.byref(E)))
         return E.value
+
+    def adjoint_step(self, nsteps, lam_dev, grad_c2_dev=None, dt=0.0):
+        """dg_adjoint_step: lam_dev (device [4][ndof] float32) from dL/dq_n to dL/dq_0 for nsteps
+        LSRK steps from the current state; grad_c2_dev (device float64, one per element) += dL/dc^2."""
+        _check(_lib.dg_adjoint_step(self._h, int(nsteps), float(dt), _ptr(lam_dev),
+                                    _ptr(grad_c2_dev) if grad_c2_dev is not None else None, None))
 
     def watchdog_selftest(self, limit_cycles):
         """dg_watchdog_selftest: the status (an int) a bounded device wait that runs out reports."""
