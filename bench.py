@@ -19,7 +19,9 @@ every quadrilateral face) and the ratio of its hex kernel time per step to the G
 Beside them ("batch"): 256 seeded meshes of n^3 cells (n log-uniform in [6, 40], N uniform in
 2..6, c uniform in [1, 3] per layer, layers H*a | W | H*b | T | K*k) advanced by LSRK(5,4), once
 mesh after mesh through dg_step and once through one dg_batch (a captured CUDA graph with one
-branch per mesh); also the subset of the meshes with n <= 12.
+branch per mesh); also the subset of the meshes with n <= 12.  And ("adjoint"): a window of 20
+LSRK steps on a 32x32x40-cell mesh at N = 4 forward and through dg_adjoint_step (dL/dq_0 and
+dL/dc^2).  And ("high_order"): the throughput mesh at N = 5 and N = 7, single-rate LSRK.
 
 Under torchrun (N > 1) every rank advances its own replica of the mesh (no
 exchange): value = sum over ranks, time = max over ranks ("replicas only").
@@ -239,6 +241,60 @@ def batch_run(dg, torch, stream, barrier, world, steps=6):
     return out
 
 
+def high_order_run(dg, torch, stream, barrier, world, mesh, max_ms, steps=5):
+    """The throughput mesh at N = 5 and N = 7 (75.9M / 177.8M DOFs), single-rate LSRK(5,4):
+    GDOF-stage/s and the kernel time per element type."""
+    from paper_1507_02557_b300.inputs import random_state
+    out = {}
+    for N in (5, 7):
+        g = dg.Mesh(mesh, N, stream=stream.cuda_stream)
+        g.set_state((1e-3 * random_state(g.ndof, 11)).astype(np.float32), on_device=False)
+        dt = g.timestep()
+        g.step(3, dt)
+        ms, kms, _, _ = timed_run(g, torch, stream, steps, dt, barrier)
+        ms = max_ms(ms)
+        out["N%d" % N] = {"ndof": g.ndof, "value": g.ndof * 5 * steps * world / (ms / 1e3) / 1e9,
+                          "unit": METRIC, "ms_per_step": ms / steps,
+                          "kernel_ms_per_step": {k: v / steps for k, v in
+                                                 zip(["hex", "wedge", "pyramid", "tet"], kms)}}
+        del g
+        torch.cuda.synchronize()
+    return out
+
+
+def adjoint_run(dg, torch, stream, barrier, world, steps=20):
+    """Differentiation workload: 32x32x40 cells (H*17 | W | H*19 | T | K*2), N = 4, a window of 20
+    LSRK(5,4) steps forward (dg_step) and backward (dg_adjoint_step with the c^2 gradient: stage
+    states recomputed from the checkpoint, one forward rhs per reverse stage, two traces and the
+    gradient kernels).  Rate = forward-equivalent element-stages of the window / time."""
+    from paper_1507_02557_b300.inputs import layered_mesh, random_state
+    layers = "H" * 17 + "W" + "H" * 19 + "T" + "K" * 2
+    mesh = layered_mesh(32, 32, 40, layers, seed=0)
+    g = dg.Mesh(mesh, ORDER, stream=stream.cuda_stream)
+    q0 = torch.from_numpy((1e-3 * random_state(g.ndof, 7)).astype(np.float32)).cuda()
+    lam0 = torch.from_numpy(random_state(g.ndof, 8).astype(np.float32)).cuda()
+    grad = torch.zeros(sum(mesh.nelem), dtype=torch.float64, device="cuda")
+    units = g.ndof * 5 * steps * world
+    out = {"workload": "32x32x40 cells (H*17|W|H*19|T|K*2), N=4, window of %d LSRK(5,4) steps" % steps,
+           "ndof": g.ndof, "unit": METRIC}
+    for arm in ("forward", "adjoint"):
+        for rep in range(2):                     # the first adjoint call allocates its scratch
+            g.set_state(q0, on_device=True)
+            lam = lam0.clone()
+            barrier()
+            t0 = time.perf_counter()
+            if arm == "forward":
+                g.step(steps)
+            else:
+                g.adjoint_step(steps, lam, grad)
+            barrier()
+            out[arm] = units / (time.perf_counter() - t0) / 1e9
+    out["adjoint_time_over_forward"] = out["forward"] / out["adjoint"]
+    del g
+    torch.cuda.synchronize()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -381,6 +437,8 @@ def main():
     del gs
     torch.cuda.synchronize()
     batch = None if args.no_batch else batch_run(dg, torch, stream, barrier, world)
+    adjoint = adjoint_run(dg, torch, stream, barrier, world)
+    high = high_order_run(dg, torch, stream, barrier, world, mesh, max_ms)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -398,6 +456,8 @@ def main():
                 "single_rate": single, "sem_hex": sem, "e2e": e2e, "clocks": clk}
         if batch:
             line["batch"] = batch
+        line["adjoint"] = adjoint
+        line["high_order"] = high
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

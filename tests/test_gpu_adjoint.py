@@ -82,3 +82,42 @@ def test_adjoint_refuses_uncovered_formulations(lib):
         lam = torch.zeros((4, g.ndof), dtype=torch.float32, device="cuda")
         with pytest.raises(lib.DGError, match="not supported"):
             g.adjoint_step(1, lam)
+
+
+def test_autograd_checkpointed_windows(lib):
+    """torch.autograd through Propagate (checkpoints every 7 of 20 steps) against one
+    dg_adjoint_step over the 20 steps (dL/dq_0 bit for bit: it does not depend on the states);
+    dL/dq_0 against central differences of the forward."""
+    from paper_1507_02557_b300.autograd import propagate
+    m = tiny()
+    N = 3
+    g = lib.Mesh(m, N)
+    q0 = torch.from_numpy(random_state(g.ndof, 5).astype(np.float32)).cuda()
+    w = torch.from_numpy(random_state(g.ndof, 6).astype(np.float32)).cuda()
+    c2 = torch.zeros(sum(m.nelem), dtype=torch.float64, device="cuda", requires_grad=True)
+    qa = q0.clone().requires_grad_(True)
+    loss = (propagate(g, qa, c2, 20, every=7) * w).sum()
+    loss.backward()
+    lam = w.clone()
+    grad = torch.zeros(sum(m.nelem), dtype=torch.float64, device="cuda")
+    g.set_state(q0, on_device=True)
+    g.adjoint_step(20, lam, grad)
+    torch.cuda.synchronize()
+    assert torch.equal(qa.grad, lam)
+    # the stage states of the two runs agree to FP32 rounding: the windows restart from dg_step's
+    # states, whose traces between steps come from the fused stage kernels (one trace launch per
+    # window instead of per step)
+    assert float((c2.grad - grad).abs().max()) <= 1e-6 * float(grad.abs().max())
+    # the loss is linear in q0: a central difference along a random direction is exact up to FP32
+    d = torch.from_numpy(random_state(g.ndof, 7).astype(np.float32)).cuda()
+
+    def L(q):
+        g.set_state(q, on_device=True)
+        g.step(20)
+        out = torch.empty_like(q)
+        g.get_state(out, on_device=True)
+        return float((out.double() * w.double()).sum())
+
+    fd = (L(q0 + 0.5 * d) - L(q0 - 0.5 * d)) / 1.0
+    ad = float((lam.double() * d.double()).sum())
+    assert abs(fd - ad) < 1e-5 * float(lam.norm()) * float(d.norm()), (fd, ad)
