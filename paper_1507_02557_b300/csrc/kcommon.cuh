@@ -37,7 +37,7 @@ struct Args {
   const float* ops2;
   const int* iops2;
   int nops2;          // floats in ops2 (layout check of the orientation-free kernels)
-  int wall_self;      // trace output: a wall side's own trace goes to its own slot
+  int wall_self;      // trace launches (MODE_TRACE): a wall side's own trace also goes to its own slot
   int* err;           // device error word (bit 0: a bounded wait timed out)
   const int* elist;   // optional element list (multi-rate levels); NULL = elements 0..K-1
   int K;              // number of elements processed

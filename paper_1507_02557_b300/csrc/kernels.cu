@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
       const int ax = f >> 1;
       const int64_t gs = A.side_off + e * 6 + f;
       const int nb = A.nbr[gs];
-      const int64_t dst = nb >= 0 ? (int64_t)nb : (A.wall_self ? gs : -1);
+      const int64_t dst = nb >= 0 ? (int64_t)nb : ((MODE == MODE_TRACE && A.wall_self) ? gs : -1);
       if (dst < 0) continue;
       const float* V = (f & 1) ? s_Vp : s_Vm;
       float nv[3];
@@ -874,7 +874,7 @@ __global__ void __launch_bounds__(128, DG_HEXP_MINB) hexw_kernel(Args A, const _
           for (int sd = 0; sd < 2; ++sd) {
             const int f = 2 * ax + sd;
             const int nb = s_nb[f];
-            const int64_t dst = nb >= 0 ? (int64_t)nb : (A.wall_self ? A.side_off + e * 6 + f : -1);
+            const int64_t dst = nb >= 0 ? (int64_t)nb : ((MODE == MODE_TRACE && A.wall_self) ? A.side_off + e * 6 + f : -1);
             if (dst < 0) continue;
             float nv[3];
             if (MODE != MODE_TRACE) {
@@ -1200,7 +1200,7 @@ __global__ void __launch_bounds__(128) gen_kernel(Args A) {
       const int f = fq / NQ, qq = fq % NQ;
       const int64_t gs = A.side_off + e * NF + f;
       const int nb = A.nbr[gs];
-      const int64_t dst = nb >= 0 ? (int64_t)nb : (A.wall_self ? gs : -1);
+      const int64_t dst = nb >= 0 ? (int64_t)nb : ((MODE == MODE_TRACE && A.wall_self) ? gs : -1);
       if (dst < 0) continue;
       const float* Tt = A.Tt + ((size_t)(f * NCODES + s_code[f]) * NP) * NQ;
       float tr[4] = {0.f, 0.f, 0.f, 0.f};

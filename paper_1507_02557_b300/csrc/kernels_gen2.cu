@@ -660,7 +660,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
         }
         const int64_t gs = A.side_off + e * NF + f;
         const int nb = A.nbr[gs];
-        const int64_t dst = nb >= 0 ? (int64_t)nb : (A.wall_self ? gs : -1);
+        const int64_t dst = nb >= 0 ? (int64_t)nb : ((MODE == MODE_TRACE && A.wall_self) ? gs : -1);
         if (dst < 0) continue;
         if (LAT) {
           lat_point(fq, f, ci, tr, sg);
