@@ -31,7 +31,8 @@ import dataclasses
 
 import numpy as np
 
-from .dg import LSRK_A, LSRK_B, DGOracle
+from .dg import LSRK_A, LSRK_B, LSRK_C, DGOracle
+from .sources import PointSources, lsrk_step_src, record, ricker
 
 
 def dense_rhs(o: DGOracle):
@@ -100,11 +101,15 @@ def c2_term(o: DGOracle, q, rho):
     return g
 
 
-def adjoint_steps(o: DGOracle, q0, lam, dt, nsteps, Rm=None):
-    """(dL/dq_0, dL/dc^2 per type) for lambda = dL/dq_n after nsteps LSRK(5,4) steps from q0.
-    R^T from the dense matrix Rm (computed when None), or, with Rm = "similarity", as
-    W F R F W^{-1} (for meshes too large for the dense matrix; the identity is pinned on the
-    dense matrices)."""
+def adjoint_steps(o: DGOracle, q0, lam, dt, nsteps, Rm=None, t0=0.0, src: PointSources | None = None,
+                  resid=None):
+    """(dL/dq_0, dL/dc^2 per type[, dL/damp]) for lambda = dL/dq_n after nsteps LSRK(5,4) steps
+    from q0 at time t0.  R^T from the dense matrix Rm (computed when None), or, with
+    Rm = "similarity", as W F R F W^{-1} (for meshes too large for the dense matrix; the identity
+    is pinned on the dense matrices).  With a source, the steps include it and dL/damp is
+    returned as a third value; with receiver residuals resid[n, r] (of the state after step n+1),
+    lambda += the receivers' transpose of resid[n] before step n is reversed (the gradient of
+    L = 1/2 sum |d - d_obs|^2 when resid = d - d_obs)."""
     shape = (4, o.ndof)
     if isinstance(Rm, str):
         rt = lambda x: apply_w(o, flip(o.rhs(flip(apply_winv(o, x)))))
@@ -113,16 +118,21 @@ def adjoint_steps(o: DGOracle, q0, lam, dt, nsteps, Rm=None):
             Rm = dense_rhs(o)
         rt = lambda x: (Rm.T @ x.ravel()).reshape(shape)
     states = [q0.copy()]
-    for _ in range(nsteps - 1):
-        states.append(o.lsrk_step(states[-1], dt))
+    for j in range(nsteps - 1):
+        states.append(lsrk_step_src(o, states[-1], dt, t0 + j * dt, src))
     lam = lam.copy()
     g = [np.zeros(k) for k in o.K]
+    g_amp = 0.0
     for j in range(nsteps - 1, -1, -1):
+        if resid is not None:
+            lam = lam + src.inject(resid[j])
+        tj = t0 + j * dt
         # stage inputs q^0..q^4 of step j
         Q = [states[j].copy()]
         res = np.zeros(shape)
         for k in range(4):
-            res = LSRK_A[k] * res + dt * o.rhs(Q[-1])
+            r = o.rhs(Q[-1]) + (src.field(tj + LSRK_C[k] * dt) if src is not None else 0.0)
+            res = LSRK_A[k] * res + dt * r
             Q.append(Q[-1] + LSRK_B[k] * res)
         rho = np.zeros(shape)
         for k in range(4, -1, -1):
@@ -130,7 +140,11 @@ def adjoint_steps(o: DGOracle, q0, lam, dt, nsteps, Rm=None):
             lam = lam + dt * rt(rho)
             for t, gt in enumerate(c2_term(o, Q[k], rho)):
                 g[t] += dt * gt
+            if src is not None:
+                g_amp += dt * float(np.sum(rho * src.unit_field(tj + LSRK_C[k] * dt)))
             rho = LSRK_A[k] * rho
+    if src is not None:
+        return lam, g, g_amp
     return lam, g
 
 
@@ -169,3 +183,11 @@ def similarity_defect(o: DGOracle, Rm=None):
         x = e.reshape(4, o.ndof)
         T[:, j] = apply_w(o, flip(rhs_of(flip(apply_winv(o, x))))).ravel()
     return float(np.abs(Rm.T - T).max() / np.abs(Rm).max())
+
+
+def misfit(mesh, N, q0, dt, nsteps, xs, amp, f0, t0, receivers, obs, **kw):
+    """L = 1/2 sum_n sum_r (d[n, r] - obs[n, r])^2 of a forward run (the definition)."""
+    o = DGOracle(mesh, N, **kw)
+    src = PointSources(o, xs, amp, f0, t0, receivers)
+    d, _ = record(o, q0, dt, nsteps, src)
+    return 0.5 * float(np.sum((d - obs) ** 2))
