@@ -202,19 +202,47 @@ dg_status dg_batch_step(dg_batch *batch, int nsteps, const double *dt, double *t
 dg_status dg_batch_stats(const dg_batch *batch, int64_t *replays, int64_t *captures);
 void dg_batch_destroy(dg_batch *batch);
 
+/* ---- point source and receivers (hexahedra) --------------------------------
+ * The pressure equation (1/kappa) p_t + div u = f of Sec. 2.2 with the point
+ * source f = amp ricker(t) delta(x - x_s), ricker(t) = (1 - 2 a) exp(-a),
+ * a = pi^2 f0^2 (t - t0)^2; the paper's experiments have f = 0.  Its weak form
+ * adds amp ricker(t) M_K^{-1} phi(x_s) to the p rhs of the hexahedron K that
+ * holds x_s.  Receivers read p(x_r) = sum_n phi_n(x_r) p_n.  Points are located
+ * by Newton's method on the trilinear maps; a point on a face shared by two
+ * hexahedra belongs to the one of lower index; DG_EINVAL if no hexahedron holds
+ * it.  Host arrays are borrowed for the call; both calls synchronise and
+ * allocate device memory (kept until the mesh is destroyed).
+ * dg_set_source: x[3], amp, f0 > 0, t0.  With a source, dg_step needs t_inout
+ *   (its value is the start time; DG_EINVAL if NULL), adds the source at the
+ *   stage times t + c_k dt, and is built for nlevels = 1 only (DG_ENOTSUP);
+ *   dg_rhs adds it at t; batches refuse the mesh (DG_ENOTSUP).
+ * dg_set_receivers: xyz[nrec][3] (nrec = 0 removes them).
+ * dg_sample_receivers: out_dev[nrec] (device FP32) = p at the receivers of the
+ *   device state q_dev (NULL = the mesh's state); asynchronous. */
+dg_status dg_set_source(dg_mesh *mesh, const double *x, double amp, double f0, double t0);
+dg_status dg_set_receivers(dg_mesh *mesh, int nrec, const double *xyz);
+dg_status dg_sample_receivers(dg_mesh *mesh, const float *q_dev, float *out_dev);
+
 /* Discrete adjoint of nsteps single-rate LSRK(5,4) steps of size dt (dt <= 0:
- * dt_min, as dg_step) started from the mesh's current state q_0 (a checkpoint).
- * No counterpart in the paper: the exact derivative of the discrete map of
- * Sec. 2.2-2.4 (the FP32 forward kernels, recomputed from q_0), for a loss L of
- * q_n = the state after the nsteps steps.
- *   lambda_dev   device [4][ndof] FP32: dL/dq_n on entry, dL/dq_0 on return.
+ * dt_min, as dg_step) started at time t0 from the mesh's current state q_0 (a
+ * checkpoint).  No counterpart in the paper: the exact derivative of the
+ * discrete map of Sec. 2.2-2.4 (the FP32 forward kernels, recomputed from q_0,
+ * with the point source if one is set), for a loss L of the states q_1..q_n
+ * after the steps.
+ *   lambda_dev   device [4][ndof] FP32: dL/dq_n from what follows the window on
+ *                entry (zeros if nothing), dL/dq_0 on return.
+ *   resid_dev    device [nsteps][nrec] FP32 or NULL: receiver forcing; row j is
+ *                dL/dd of the receiver samples of q_{j+1}, so for
+ *                L = 1/2 sum (d - d_obs)^2 it is d - d_obs (DG_EINVAL without
+ *                receivers).
  *   grad_c2_dev  device, one double per element in the type order of dg_layout
  *                (hexahedra, wedges, pyramids, tets; element order within a
  *                type), or NULL: dL/dc^2_K is ADDED to it (c^2 enters through
  *                1/rho = c^2 and through tau_p = 1/{rho c}, tau_u = {rho c} on
  *                the element's faces).  Contributions are summed with atomics:
  *                the last bits vary from run to run.
- *   grad_amp     must be NULL (the library has no source term; DG_ENOTSUP).
+ *   grad_amp_dev device double or NULL: dL/damp of the point source is ADDED to
+ *                it (DG_EINVAL without a source).
  * The transpose of the operator is applied as R^T = W F R F W^{-1} with
  * W = blockdiag(M, M/c^2) the energy weight and F = diag(1,-1,-1,-1), exact
  * for GL hexahedra and skew-form pyramids; DG_ENOTSUP for SEM hexahedra,
@@ -225,8 +253,8 @@ void dg_batch_destroy(dg_batch *batch);
  * asynchronous on the mesh's stream.  Chain windows of steps by calling it per
  * window, last window first, after restoring each window's checkpoint with
  * dg_set_state. */
-dg_status dg_adjoint_step(dg_mesh *mesh, int nsteps, double dt, float *lambda_dev,
-                          double *grad_c2_dev, double *grad_amp);
+dg_status dg_adjoint_step(dg_mesh *mesh, int nsteps, double dt, double t0, float *lambda_dev,
+                          const float *resid_dev, double *grad_c2_dev, double *grad_amp_dev);
 
 const char *dg_status_string(dg_status s);
 /* Message of the last DG_ECUDA / DG_EMESH / DG_EINVAL error on this thread. */

@@ -53,3 +53,52 @@ class Propagate(torch.autograd.Function):
 def propagate(mesh, q0, c2, nsteps, dt=0.0, every=20):
     """Functional form of Propagate.apply."""
     return Propagate.apply(q0, c2, mesh, nsteps, dt, every)
+
+
+class Seismogram(torch.autograd.Function):
+    """Receiver traces d[n, r]: p at the receivers after each of nsteps single-rate LSRK(5,4)
+    steps of dt from q0 at time t0, on a Mesh with a point source and receivers set.
+
+    Inputs: ``q0`` (device float32 [4, ndof]); ``c2`` (device float64, one per element in the
+    dg_layout type order) and ``amp`` (device float64 [1]) stand for the mesh's c^2 and source
+    amplitude and receive dL/dc^2 and dL/damp (their values are not read); ``every`` the
+    checkpoint interval.  Backward: dg_adjoint_step per window, last first, with the window's
+    rows of dL/dd as receiver forcing."""
+
+    @staticmethod
+    def forward(ctx, q0, c2, amp, mesh, nsteps, dt=0.0, t0=0.0, every=20):
+        q = q0.detach().contiguous()
+        mesh.set_state(q, on_device=True)
+        out = torch.empty((nsteps, mesh.nrec), dtype=torch.float32, device=q.device)
+        ckpts, starts, lens = [], [], []
+        t = t0
+        for n in range(nsteps):
+            if n % every == 0:
+                ck = torch.empty_like(q)
+                mesh.get_state(ck, on_device=True)
+                ckpts.append(ck)
+                starts.append(t)
+                lens.append(min(every, nsteps - n))
+            t = mesh.step(1, dt, t)
+            mesh.sample_receivers(out[n])
+        ctx.save_for_backward(*ckpts)
+        ctx.mesh, ctx.starts, ctx.lens, ctx.dt, ctx.nc2, ctx.every = mesh, starts, lens, dt, c2.numel(), every
+        return out
+
+    @staticmethod
+    def backward(ctx, gd):
+        mesh = ctx.mesh
+        gd = gd.detach().to(torch.float32).contiguous()
+        lam = torch.zeros_like(ctx.saved_tensors[0])
+        grad_c2 = torch.zeros(ctx.nc2, dtype=torch.float64, device=lam.device) if ctx.needs_input_grad[1] else None
+        grad_amp = torch.zeros(1, dtype=torch.float64, device=lam.device) if ctx.needs_input_grad[2] else None
+        for w in range(len(ctx.lens) - 1, -1, -1):
+            mesh.set_state(ctx.saved_tensors[w], on_device=True)
+            rows = gd[w * ctx.every:w * ctx.every + ctx.lens[w]].contiguous()
+            mesh.adjoint_step(ctx.lens[w], lam, grad_c2, ctx.dt, ctx.starts[w], rows, grad_amp)
+        return lam, grad_c2, grad_amp, None, None, None, None, None
+
+
+def seismogram(mesh, q0, c2, amp, nsteps, dt=0.0, t0=0.0, every=20):
+    """Functional form of Seismogram.apply."""
+    return Seismogram.apply(q0, c2, amp, mesh, nsteps, dt, t0, every)

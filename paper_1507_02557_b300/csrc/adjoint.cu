@@ -283,7 +283,8 @@ cudaError_t traces_all(dg_mesh* m, const float* x, float* tout) {
 }  // namespace
 }  // namespace dgk
 
-cudaError_t dg_adjoint_run(dg_mesh* m, int nsteps, double dt, float* lam, double* grad) {
+cudaError_t dg_adjoint_run(dg_mesh* m, int nsteps, double dt, double t0, float* lam, const float* resid,
+                           double* grad, double* grad_amp) {
   using namespace dgk;
   const int64_t fs = 4 * m->ndof;
   const size_t need = (size_t)nsteps + 9;   // step states S[0..n-1], Q1..Q4, rho, v, fv, y, z
@@ -340,14 +341,17 @@ cudaError_t dg_adjoint_run(dg_mesh* m, int nsteps, double dt, float* lam, double
     if ((e = launch_trace(m, qj, TB[0])) != cudaSuccess) return e;
     int cur = 0;
     for (int k = 0; k < 5; ++k) {
-      if ((e = launch_stage(m, qj, m->res, TB[cur], TB[cur ^ 1], (float)RK_A[k], (float)RK_B[k], (float)dt)) !=
-          cudaSuccess)
-        return e;
+      dg_source_at(m, t0 + (j + RK_C[k]) * dt);
+      e = launch_stage(m, qj, m->res, TB[cur], TB[cur ^ 1], (float)RK_A[k], (float)RK_B[k], (float)dt);
+      m->src_now = 0.f;
+      if (e != cudaSuccess) return e;
       cur ^= 1;
     }
   }
   for (int j = nsteps - 1; j >= 0; --j) {
     float* Sj = S + (size_t)j * fs;
+    // receiver forcing of the state after step j
+    if (resid && (e = dg_receiver_inject(m, resid + (size_t)j * m->nrec, lam)) != cudaSuccess) return e;
     // stage inputs q^1..q^4 of step j (the stage kernels update in place)
     if ((e = launch_trace(m, Sj, TB[0])) != cudaSuccess) return e;
     int cur = 0;
@@ -356,15 +360,21 @@ cudaError_t dg_adjoint_run(dg_mesh* m, int nsteps, double dt, float* lam, double
       if ((e = cudaMemcpyAsync(dst, k == 0 ? Sj : stage_state(k), fs * sizeof(float), cudaMemcpyDeviceToDevice, st)) !=
           cudaSuccess)
         return e;
-      if ((e = launch_stage(m, dst, m->res, TB[cur], TB[cur ^ 1], (float)RK_A[k], (float)RK_B[k], (float)dt)) !=
-          cudaSuccess)
-        return e;
+      dg_source_at(m, t0 + (j + RK_C[k]) * dt);
+      e = launch_stage(m, dst, m->res, TB[cur], TB[cur ^ 1], (float)RK_A[k], (float)RK_B[k], (float)dt);
+      m->src_now = 0.f;
+      if (e != cudaSuccess) return e;
       cur ^= 1;
     }
     if ((e = cudaMemsetAsync(rho, 0, fs * sizeof(float), st)) != cudaSuccess) return e;
     for (int k = 4; k >= 0; --k) {
       const float* qk = k == 0 ? Sj : stage_state(k);
       if ((e = axpby(m, fs, 1.f, rho, (float)RK_B[k], lam)) != cudaSuccess) return e;
+      if (grad_amp && m->src_e >= 0) {   // d(stage source dt amp ricker(t_k) g)/d amp against rho
+        const double tk = t0 + (j + RK_C[k]) * dt;
+        if ((e = dg_source_amp_grad(m, rho, dt * dg_ricker(tk, m->src_f0, m->src_t0), grad_amp)) != cudaSuccess)
+          return e;
+      }
       if ((e = apply_mass(m, 0, rho, v, fv, 0.f)) != cudaSuccess) return e;
       if (grad) {
         if ((e = traces_all(m, qk, TB[0])) != cudaSuccess) return e;

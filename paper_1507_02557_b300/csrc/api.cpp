@@ -14,6 +14,8 @@ const double RK_A[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0
 const double RK_B[5] = {1432997174477.0 / 9575080441904.0, 5161836677717.0 / 13612068292357.0,
                         1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
                         2277821191437.0 / 14882151754819.0};
+const double RK_C[5] = {0.0, 1432997174477.0 / 9575080441904.0, 2526269341429.0 / 6820363962896.0,
+                        2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
 
 namespace {
 thread_local std::string g_err;
@@ -173,12 +175,13 @@ dg_status dg_get_state(const dg_mesh* m, float* q, int on_device) {
 }
 
 dg_status dg_rhs(dg_mesh* m, const float* q, float* rhs, double t) {
-  (void)t;
   if (!m || !q || !rhs) return DG_EINVAL;
   float* tr = m->trace;  // buffer 0 used as scratch
   cudaError_t e = dgk::launch_trace(m, q, tr);
   if (e != cudaSuccess) return cuda_fail(e);
+  dg_source_at(m, t);
   e = dgk::launch_rhs(m, q, tr, rhs);
+  m->src_now = 0.f;
   if (e != cudaSuccess) return cuda_fail(e);
   return DG_OK;
 }
@@ -196,7 +199,7 @@ dg_status dg_timestep(const dg_mesh* m, double* dt_min, int64_t* level_count) {
 namespace {
 
 // nsteps single-rate LSRK(5,4) steps: one trace launch, then fused stage kernels (ping-pong traces).
-cudaError_t lsrk_steps(dg_mesh* m, int nsteps, double dt) {
+cudaError_t lsrk_steps(dg_mesh* m, int nsteps, double dt, double t0 = 0.0) {
   const size_t plane2 = 2 * (size_t)m->nsides * m->nq;
   float* buf[2] = {m->trace, m->trace + plane2};
   cudaError_t e = dgk::launch_trace(m, m->q, buf[0]);
@@ -204,7 +207,9 @@ cudaError_t lsrk_steps(dg_mesh* m, int nsteps, double dt) {
   int cur = 0;
   for (int s = 0; s < nsteps; ++s)
     for (int k = 0; k < 5; ++k) {
+      dg_source_at(m, t0 + (s + RK_C[k]) * dt);
       e = dgk::launch_stage(m, m->q, m->res, buf[cur], buf[cur ^ 1], (float)RK_A[k], (float)RK_B[k], (float)dt);
+      m->src_now = 0.f;
       if (e != cudaSuccess) return e;
       cur ^= 1;
     }
@@ -331,10 +336,10 @@ extern "C" dg_status dg_watchdog_selftest(dg_mesh* m, int64_t limit_cycles) {
   return device_flags(m);
 }
 
-cudaError_t dg_enqueue_steps(dg_mesh* m, int nsteps, double dt) {
+cudaError_t dg_enqueue_steps(dg_mesh* m, int nsteps, double dt, double t0) {
   if (m->nlevels == 2)   // fused kernels: N <= 4 with lattice exchange on tet / pyramid triangle faces
     return m->N <= 4 && m->tri_lat ? mrab3_fused(m, nsteps, dt) : mrab3(m, nsteps, dt);
-  return nsteps > 0 ? lsrk_steps(m, nsteps, dt) : cudaSuccess;
+  return nsteps > 0 ? lsrk_steps(m, nsteps, dt, t0) : cudaSuccess;
 }
 
 double dg_step_time(const dg_mesh* m, int nsteps, double dt, bool fresh) {
@@ -346,8 +351,18 @@ extern "C" dg_status dg_step(dg_mesh* m, int nsteps, double dt, double* t_inout)
   if (!m || nsteps < 0) return DG_EINVAL;
   if (!(dt > 0)) dt = m->dt_min;
   if (nsteps == 0) return DG_OK;
+  if (m->src_e >= 0) {
+    if (m->nlevels != 1) {
+      g_err = "a point source is built for single-rate LSRK";
+      return DG_ENOTSUP;
+    }
+    if (!t_inout) {
+      g_err = "a point source needs the start time (t_inout)";
+      return DG_EINVAL;
+    }
+  }
   const bool fresh = m->nlevels == 2 && !m->mr_started;
-  cudaError_t e = dg_enqueue_steps(m, nsteps, dt);
+  cudaError_t e = dg_enqueue_steps(m, nsteps, dt, t_inout ? *t_inout : 0.0);
   if (e != cudaSuccess) return cuda_fail(e);
   if (t_inout) *t_inout += dg_step_time(m, nsteps, dt, fresh);
   return DG_OK;
@@ -396,11 +411,16 @@ dg_status dg_profile(dg_mesh* m, int enable, double* ms, int64_t* launches) {
   return DG_OK;
 }
 
-dg_status dg_adjoint_step(dg_mesh* m, int nsteps, double dt, float* lambda, double* g_c2, double* g_amp) {
+dg_status dg_adjoint_step(dg_mesh* m, int nsteps, double dt, double t0, float* lambda, const float* resid,
+                          double* g_c2, double* g_amp) {
   if (!m || nsteps < 0 || !lambda) return DG_EINVAL;
-  if (g_amp) {
-    g_err = "the library has no source term: grad_amp must be NULL";
-    return DG_ENOTSUP;
+  if (g_amp && m->src_e < 0) {
+    g_err = "grad_amp needs a point source (dg_set_source)";
+    return DG_EINVAL;
+  }
+  if (resid && m->nrec == 0) {
+    g_err = "receiver residuals need receivers (dg_set_receivers)";
+    return DG_EINVAL;
   }
   if (m->nlevels != 1 || m->hex_sem || m->pyr_form != 0) {
     g_err = "adjoint built for single-rate LSRK with GL hexahedra and skew-form pyramids";
@@ -408,7 +428,7 @@ dg_status dg_adjoint_step(dg_mesh* m, int nsteps, double dt, float* lambda, doub
   }
   if (!(dt > 0)) dt = m->dt_min;
   if (nsteps == 0) return DG_OK;
-  cudaError_t e = dg_adjoint_run(m, nsteps, dt, lambda, g_c2);
+  cudaError_t e = dg_adjoint_run(m, nsteps, dt, t0, lambda, resid, g_c2, g_amp);
   if (e != cudaSuccess) return cuda_fail(e);
   return DG_OK;
 }

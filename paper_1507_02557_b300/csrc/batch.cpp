@@ -130,6 +130,11 @@ dg_status dg_batch_step(dg_batch* b, int nsteps, const double* dt, double* t_ino
   const size_t n = b->m.size();
   std::vector<double> h(n);
   std::vector<char> fresh(n);
+  for (size_t i = 0; i < n; ++i)
+    if (b->m[i]->src_e >= 0) {
+      dg_set_last_error("a mesh with a point source cannot be stepped in a batch (the graph fixes the source values)");
+      return DG_ENOTSUP;
+    }
   for (size_t i = 0; i < n; ++i) {
     h[i] = dt && dt[i] > 0 ? dt[i] : b->m[i]->dt_min;
     fresh[i] = b->m[i]->nlevels == 2 && !b->m[i]->mr_started;

@@ -96,6 +96,16 @@ struct dg_mesh {
   float* tet_minv_dev = nullptr;
   float* adj_buf = nullptr;       // scratch states of the reverse sweep
   size_t adj_states = 0;
+  // point source and receivers in hexahedra (source.cu)
+  std::vector<double> hex_coef;   // [K_hex][8][3] trilinear-map coefficients c0..c7 (x = c0 + c1 r + ...)
+  std::vector<double> hex_r1, hex_w1;   // 1D nodes and weights of the hexahedron
+  int64_t src_e = -1;             // hexahedron holding the source, -1 = none
+  float* src_g = nullptr;         // [Np] M^{-1} phi(x_s)
+  double src_amp = 0.0, src_f0 = 0.0, src_t0 = 0.0;
+  float src_now = 0.f;            // amp ricker(t) for the next rhs / stage launch (0 = none)
+  int nrec = 0;
+  int* rec_e = nullptr;           // [nrec] hexahedron of each receiver
+  float* rec_rows = nullptr;      // [nrec][Np] phi(x_r)
   int* derr = nullptr;            // device error word: bit 0 = a bounded device wait timed out
   dgk::TmaArr tma[5];             // q, res, hist, trace, trace3 (hex TMA staging)
   // per-type kernel timing (dg_profile): event pairs recorded around each launch
@@ -133,17 +143,30 @@ void dg_set_last_error(const std::string& msg);
 // Carpenter & Kennedy (1994) LSRK(5,4) coefficients (api.cpp).
 extern const double RK_A[5];
 extern const double RK_B[5];
+extern const double RK_C[5];   // stage times
+
+// Point source and receivers (source.cu).  dg_source_at sets m->src_now = amp ricker(t) (0 without
+// a source) for the next rhs / stage launch.
+double dg_ricker(double t, double f0, double t0);
+void dg_source_at(dg_mesh* m, double t);
+// lam_p += the receivers' transpose of resid [nrec]
+cudaError_t dg_receiver_inject(dg_mesh* m, const float* resid, float* lam);
+// *g += coef rho_p . g_s over the source's hexahedron (device double g)
+cudaError_t dg_source_amp_grad(dg_mesh* m, const float* rho, double coef, double* g);
 
 // nsteps time steps of m on m->stream: LSRK(5,4), or multi-rate AB3 whose first call also runs the
 // start-up (nsteps = 0 runs the start-up alone).  No synchronization (api.cpp).
-cudaError_t dg_enqueue_steps(dg_mesh* m, int nsteps, double dt);
+cudaError_t dg_enqueue_steps(dg_mesh* m, int nsteps, double dt, double t0 = 0.0);
 // Simulated time that dg_enqueue_steps(m, nsteps, dt) advances; fresh = the start-up runs too.
 double dg_step_time(const dg_mesh* m, int nsteps, double dt, bool fresh);
 
-// Reverse sweep of nsteps LSRK(5,4) steps of dt from the state m->q (adjoint.cu): lam (device,
-// [4][ndof]) holds dL/dq_n on entry and dL/dq_0 on return; grad (device, one double per element
-// in type order, or NULL) accumulates dL/dc^2.  Enqueued on m->stream; m->q is left unchanged.
-cudaError_t dg_adjoint_run(dg_mesh* m, int nsteps, double dt, float* lam, double* grad);
+// Reverse sweep of nsteps LSRK(5,4) steps of dt from the state m->q at time t0 (adjoint.cu): lam
+// (device, [4][ndof]) holds dL/dq_n on entry and dL/dq_0 on return; resid (device [nsteps][nrec]
+// or NULL) is the receiver forcing of the states after steps 1..nsteps; grad (device, one double
+// per element in type order, or NULL) accumulates dL/dc^2, grad_amp (device double or NULL)
+// dL/damp of the source.  Enqueued on m->stream; m->q is left unchanged.
+cudaError_t dg_adjoint_run(dg_mesh* m, int nsteps, double dt, double t0, float* lam, const float* resid,
+                           double* grad, double* grad_amp);
 
 // Host setup (setup.cpp).
 dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err);

@@ -38,6 +38,10 @@ struct Args {
   const int* iops2;
   int nops2;          // floats in ops2 (layout check of the orientation-free kernels)
   int wall_self;      // trace launches (MODE_TRACE): a wall side's own trace also goes to its own slot
+  // point source (hexahedra, RHS / STAGE): rhs_p += src_s src_g[node] in element src_e (-1: none)
+  int64_t src_e;
+  float src_s;
+  const float* src_g;
   int* err;           // device error word (bit 0: a bounded wait timed out)
   const int* elist;   // optional element list (multi-rate levels); NULL = elements 0..K-1
   int K;              // number of elements processed

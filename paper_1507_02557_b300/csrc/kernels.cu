@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
                     s_Vm[k] * s_F[le][4][fl][ij] + s_Vp[k] * s_F[le][5][fl][ij];
         rhs[fl] += (fl == 0 ? 1.f : c2) * iM * sum;
       }
+      if (e == A.src_e) rhs[0] += A.src_s * A.src_g[tid];   // point source on p
       if (MODE == MODE_RHS) {
 #pragma unroll
         for (int fl = 0; fl < 4; ++fl) A.rhs[fl * A.ndof + base + tid] = rhs[fl];
@@ -778,6 +779,10 @@ __global__ void __launch_bounds__(128, DG_HEXP_MINB) hexw_kernel(Args A, const _
           rhs[2][k] += c2 * iM * sum.z;
           rhs[3][k] += c2 * iM * sum.w;
         }
+        if ((MODE == MODE_RHS || MODE == MODE_STAGE) && e == A.src_e) {   // point source on p
+#pragma unroll
+          for (int k = 0; k < n1; ++k) rhs[0][k] += A.src_s * A.src_g[col + NQ * k];
+        }
       }
       cp_async_wait<2>();   // aux(g) has landed
       if (TMA && H::NAUX > 0 && !wait_bar(3)) {
@@ -1319,6 +1324,9 @@ static Args make_args(dg_mesh* m, int t) {
   A.iops2 = td.iops2;
   A.nops2 = td.nops2;
   A.wall_self = m->wall_self ? 1 : 0;
+  A.src_e = (t == DG_HEX && m->src_e >= 0 && m->src_now != 0.f) ? m->src_e : -1;
+  A.src_s = m->src_now;
+  A.src_g = m->src_g;
   A.K = td.K;
   A.elist = nullptr;
   A.err = m->derr;

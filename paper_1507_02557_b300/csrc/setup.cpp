@@ -479,6 +479,9 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
     m->hex_sem = sem;
     Basis B[4];
     for (int t = 0; t < 4; ++t) B[t].init(t, N, sem && t == HEX);
+    m->hex_r1 = B[HEX].r1;
+    m->hex_w1 = B[HEX].w1;
+    m->hex_coef.assign((size_t)d->nelem[HEX] * 24, 0.0);
     const int nfc[4] = {6, 5, 5, 4};
 
     // --- offsets
@@ -650,6 +653,8 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
           }
           for (int mm = 1; mm < 8; ++mm)
             for (int dd = 0; dd < 3; ++dd) ge[3 * (mm - 1) + dd] = (float)cf[mm][dd];
+          for (int mm = 0; mm < 8; ++mm)
+            for (int dd = 0; dd < 3; ++dd) m->hex_coef[(size_t)e * 24 + 3 * mm + dd] = cf[mm][dd];
           double jmin = 1e300;
           for (int n = 0; n < Np; ++n) {
             map_jacobian(HEX, xv, &B[t].nodes[3 * n], F);

@@ -22,6 +22,7 @@ EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_host_check", "dg_layout", "d
            "dg_set_state", "dg_get_state", "dg_rhs", "dg_timestep", "dg_step", "dg_state_ptr",
            "dg_energy", "dg_energy_noalloc", "dg_profile", "dg_watchdog_selftest", "dg_adjoint_step",
            "dg_batch_create", "dg_batch_step", "dg_batch_stats", "dg_batch_destroy",
+           "dg_set_source", "dg_set_receivers", "dg_sample_receivers",
            "dg_status_string", "dg_last_error")
 
 
@@ -50,7 +51,10 @@ _lib.dg_state_ptr.argtypes = [_vp, C.POINTER(_vp)]
 _lib.dg_energy.argtypes = [_vp, _vp, C.POINTER(C.c_double)]
 _lib.dg_energy_noalloc.argtypes = [_vp, _vp, C.POINTER(C.c_double)]
 _lib.dg_watchdog_selftest.argtypes = [_vp, C.c_int64]
-_lib.dg_adjoint_step.argtypes = [_vp, C.c_int, C.c_double, _vp, _vp, _vp]
+_lib.dg_adjoint_step.argtypes = [_vp, C.c_int, C.c_double, C.c_double, _vp, _vp, _vp, _vp]
+_lib.dg_set_source.argtypes = [_vp, C.POINTER(C.c_double), C.c_double, C.c_double, C.c_double]
+_lib.dg_set_receivers.argtypes = [_vp, C.c_int, C.POINTER(C.c_double)]
+_lib.dg_sample_receivers.argtypes = [_vp, _vp, _vp]
 _lib.dg_profile.argtypes = [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
 _lib.dg_batch_create.argtypes = [C.POINTER(_vp), C.c_int, _vp, C.POINTER(_vp)]
 _lib.dg_batch_step.argtypes = [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -184,11 +188,30 @@ class Mesh:
         _check(_lib.dg_energy_noalloc(self._h, _ptr(q_dev) if q_dev is not None else None, C.byref(E)))
         return E.value
 
-    def adjoint_step(self, nsteps, lam_dev, grad_c2_dev=None, dt=0.0):
+    def adjoint_step(self, nsteps, lam_dev, grad_c2_dev=None, dt=0.0, t0=0.0, resid_dev=None, grad_amp_dev=None):
         """dg_adjoint_step: lam_dev (device [4][ndof] float32) from dL/dq_n to dL/dq_0 for nsteps
-        LSRK steps from the current state; grad_c2_dev (device float64, one per element) += dL/dc^2."""
-        _check(_lib.dg_adjoint_step(self._h, int(nsteps), float(dt), _ptr(lam_dev),
-                                    _ptr(grad_c2_dev) if grad_c2_dev is not None else None, None))
+        LSRK steps from the current state at time t0; resid_dev (device [nsteps][nrec] float32)
+        receiver forcing; grad_c2_dev (device float64, one per element) += dL/dc^2;
+        grad_amp_dev (device float64 [1]) += dL/damp."""
+        opt = lambda x: _ptr(x) if x is not None else None
+        _check(_lib.dg_adjoint_step(self._h, int(nsteps), float(dt), float(t0), _ptr(lam_dev), opt(resid_dev),
+                                    opt(grad_c2_dev), opt(grad_amp_dev)))
+
+    def set_source(self, x, amp, f0, t0):
+        """dg_set_source: Ricker point source amp ricker(t; f0, t0) at x (inside a hexahedron)."""
+        xs = (C.c_double * 3)(*[float(v) for v in x])
+        _check(_lib.dg_set_source(self._h, xs, float(amp), float(f0), float(t0)))
+
+    def set_receivers(self, xyz):
+        """dg_set_receivers: receivers at the rows of xyz (n, 3)."""
+        a = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
+        self.nrec = a.shape[0]
+        _check(_lib.dg_set_receivers(self._h, a.shape[0], a.ctypes.data_as(C.POINTER(C.c_double))))
+
+    def sample_receivers(self, out_dev, q_dev=None):
+        """dg_sample_receivers: p at the receivers into out_dev (device float32 [nrec])."""
+        _check(_lib.dg_sample_receivers(self._h, _ptr(q_dev) if q_dev is not None else None, _ptr(out_dev)))
+        return out_dev
 
     def watchdog_selftest(self, limit_cycles):
         """dg_watchdog_selftest: the status (an int) a bounded device wait that runs out reports."""
