@@ -19,9 +19,10 @@ every quadrilateral face) and the ratio of its hex kernel time per step to the G
 Beside them ("batch"): 256 seeded meshes of n^3 cells (n log-uniform in [6, 40], N uniform in
 2..6, c uniform in [1, 3] per layer, layers H*a | W | H*b | T | K*k) advanced by LSRK(5,4), once
 mesh after mesh through dg_step and once through one dg_batch (a captured CUDA graph with one
-branch per mesh); also the subset of the meshes with n <= 12.  And ("adjoint"): a window of 20
-LSRK steps on a 32x32x40-cell mesh at N = 4 forward and through dg_adjoint_step (dL/dq_0 and
-dL/dc^2).  And ("high_order"): the throughput mesh at N = 5 and N = 7, single-rate LSRK.
+branch per mesh); also the subset of the meshes with n <= 12.  And ("differentiation"): 400 LSRK
+steps on a 32x32x40-cell mesh at N = 4 with a Ricker point source and 64 receivers, the receiver
+misfit's gradient w.r.t. c^2 and the source amplitude through the checkpointed adjoint, and
+central differences along 20 random c^2 directions.  And ("high_order"): the throughput mesh at N = 5 and N = 7, single-rate LSRK.
 
 Under torchrun (N > 1) every rank advances its own replica of the mesh (no
 exchange): value = sum over ranks, time = max over ranks ("replicas only").
@@ -262,34 +263,89 @@ def high_order_run(dg, torch, stream, barrier, world, mesh, max_ms, steps=5):
     return out
 
 
-def adjoint_run(dg, torch, stream, barrier, world, steps=20):
-    """Differentiation workload: 32x32x40 cells (H*17 | W | H*19 | T | K*2), N = 4, a window of 20
-    LSRK(5,4) steps forward (dg_step) and backward (dg_adjoint_step with the c^2 gradient: stage
-    states recomputed from the checkpoint, one forward rhs per reverse stage, two traces and the
-    gradient kernels).  Rate = forward-equivalent element-stages of the window / time."""
-    from paper_1507_02557_b300.inputs import layered_mesh, random_state
+def differentiation_run(dg, torch, stream, barrier, world, steps=400, every=20, ndir=20):
+    """Differentiation workload: 32x32x40 cells (H*17 | W | H*19 | T | K*2), N = 4, c = 1, a Ricker
+    point source (f0 = 3, t0 = 1.2/f0, amp 1) at (0, 0, -0.5), 64 receivers on an 8x8 grid of
+    z = 0.8, 400 LSRK(5,4) steps of dt_min from the standing mode interpolated at the hexahedra's
+    nodes; observed data from c^2 perturbed by up to 5 % per element (seeded).  Gradient of
+    1/2 sum (d - d_obs)^2 w.r.t. c^2 and amp through autograd.Seismogram (checkpoints every 20
+    steps); dL/dc^2 checked against central differences of forward runs along ndir random
+    directions (relative step 1e-3)."""
+    import dataclasses
+
+    from paper_1507_02557_b300.autograd import seismogram
+    from paper_1507_02557_b300.inputs import layered_mesh
     layers = "H" * 17 + "W" + "H" * 19 + "T" + "K" * 2
     mesh = layered_mesh(32, 32, 40, layers, seed=0)
-    g = dg.Mesh(mesh, ORDER, stream=stream.cuda_stream)
-    q0 = torch.from_numpy((1e-3 * random_state(g.ndof, 7)).astype(np.float32)).cuda()
-    lam0 = torch.from_numpy(random_state(g.ndof, 8).astype(np.float32)).cuda()
-    grad = torch.zeros(sum(mesh.nelem), dtype=torch.float64, device="cuda")
+    g1 = np.linspace(-0.75, 0.75, 8)
+    recs = [[x, y, 0.8] for y in g1 for x in g1]
+    f0 = 3.0
+    rng = np.random.default_rng(5)
+
+    def make(c2, amp=1.0):
+        g = dg.Mesh(dataclasses.replace(mesh, c2=c2), ORDER, stream=stream.cuda_stream)
+        g.set_source([0.0, 0.0, -0.5], amp, f0, 1.2 / f0)
+        g.set_receivers(recs)
+        return g
+
+    g = make(mesh.c2)
+    dt = g.timestep()
+    nel = sum(mesh.nelem)
+    # initial state: the standing mode's p at the hexahedra's GL nodes (trilinear maps), 0 elsewhere
+    x, _ = np.polynomial.legendre.leggauss(ORDER + 1)
+    n1 = ORDER + 1
+    idx = np.arange(n1 ** 3)
+    rst = np.stack([x[idx % n1], x[(idx // n1) % n1], x[idx // n1 ** 2]], 1)
+    corner = np.array([[(-1) ** (1 + (v & 1)), (-1) ** (1 + ((v >> 1) & 1)), (-1) ** (1 + ((v >> 2) & 1))]
+                       for v in range(8)], float)
+    shape = np.prod(1 + rst[:, None, :] * corner[None, :, :], axis=2) / 8
+    X = torch.einsum("nv,kvd->knd", torch.from_numpy(shape).cuda(), torch.from_numpy(mesh.xyz[mesh.conn[0]]).cuda())
+    q0 = torch.zeros((4, g.ndof), dtype=torch.float32, device="cuda")
+    p0 = torch.cos(np.pi / 2 * X[..., 0]) * torch.cos(np.pi / 2 * X[..., 1]) * torch.cos(np.pi / 2 * X[..., 2])
+    q0[0, :p0.numel()] = p0.reshape(-1).float()
+    zeros = lambda n: torch.zeros(n, dtype=torch.float64, device="cuda")
+    go = make([c * (1 + 0.05 * rng.uniform(-1, 1, len(c))) for c in mesh.c2])
+    with torch.no_grad():
+        obs = seismogram(go, q0, zeros(nel), zeros(1), steps, dt, 0.0, every).double()
+    del go
+
+    def loss(gm, grad=False):
+        c2 = zeros(nel).requires_grad_(grad)
+        amp = zeros(1).requires_grad_(grad)
+        d = seismogram(gm, q0, c2, amp, steps, dt, 0.0, every)
+        return 0.5 * ((d.double() - obs) ** 2).sum(), c2, amp
+
+    Lw, _, _ = loss(g, True)          # warm-up (first use of the loss's torch kernels, adjoint scratch)
+    Lw.backward()
+    barrier()
+    t0 = time.perf_counter()
+    L, c2, amp = loss(g, True)
+    barrier()
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    L.backward()
+    barrier()
+    t_bwd = time.perf_counter() - t0
+    gc = c2.grad.cpu().numpy()
+    c2all = np.concatenate(mesh.c2)
+    errs = []
+    for _ in range(ndir):
+        dirs = rng.standard_normal(nel)
+        parts = np.split(dirs, np.cumsum(mesh.nelem)[:-1])
+        lp = float(loss(make([c * (1 + 1e-3 * d_) for c, d_ in zip(mesh.c2, parts)]))[0])
+        lm = float(loss(make([c * (1 - 1e-3 * d_) for c, d_ in zip(mesh.c2, parts)]))[0])
+        fd = (lp - lm) / 2e-3
+        ad = float(np.sum(gc * c2all * dirs))
+        errs.append(abs(fd - ad) / max(abs(ad), 1e-300))
+    lp = float(loss(make(mesh.c2, 1.0 + 1e-3))[0])
+    lm = float(loss(make(mesh.c2, 1.0 - 1e-3))[0])
     units = g.ndof * 5 * steps * world
-    out = {"workload": "32x32x40 cells (H*17|W|H*19|T|K*2), N=4, window of %d LSRK(5,4) steps" % steps,
-           "ndof": g.ndof, "unit": METRIC}
-    for arm in ("forward", "adjoint"):
-        for rep in range(2):                     # the first adjoint call allocates its scratch
-            g.set_state(q0, on_device=True)
-            lam = lam0.clone()
-            barrier()
-            t0 = time.perf_counter()
-            if arm == "forward":
-                g.step(steps)
-            else:
-                g.adjoint_step(steps, lam, grad)
-            barrier()
-            out[arm] = units / (time.perf_counter() - t0) / 1e9
-    out["adjoint_time_over_forward"] = out["forward"] / out["adjoint"]
+    out = {"workload": "32x32x40 cells (H*17|W|H*19|T|K*2), N=4, Ricker source at (0,0,-0.5), 64 receivers "
+                       "at z=0.8, %d LSRK(5,4) steps of dt_min, checkpoints every %d" % (steps, every),
+           "ndof": g.ndof, "dt": dt, "loss": float(L.detach()), "unit": METRIC,
+           "forward": units / t_fwd / 1e9, "backward": units / t_bwd / 1e9, "backward_over_forward": t_bwd / t_fwd,
+           "fd_directions": ndir, "fd_rel_err_max": max(errs), "fd_rel_err_median": float(np.median(errs)),
+           "grad_amp": float(amp.grad.item()), "grad_amp_fd": (lp - lm) / 2e-3}
     del g
     torch.cuda.synchronize()
     return out
@@ -437,7 +493,7 @@ def main():
     del gs
     torch.cuda.synchronize()
     batch = None if args.no_batch else batch_run(dg, torch, stream, barrier, world)
-    adjoint = adjoint_run(dg, torch, stream, barrier, world)
+    diff = differentiation_run(dg, torch, stream, barrier, world)
     high = high_order_run(dg, torch, stream, barrier, world, mesh, max_ms)
 
     if rank == 0:
@@ -456,7 +512,7 @@ def main():
                 "single_rate": single, "sem_hex": sem, "e2e": e2e, "clocks": clk}
         if batch:
             line["batch"] = batch
-        line["adjoint"] = adjoint
+        line["differentiation"] = diff
         line["high_order"] = high
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
