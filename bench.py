@@ -351,6 +351,27 @@ def differentiation_run(dg, torch, stream, barrier, world, steps=400, every=20, 
     return out
 
 
+def run_case(args, dg, torch, mesh):
+    """--case: warm-up steps, then the timed steps (lsrk) or one adjoint window (adjoint); one JSON
+    line with the wall time (not a bench value)."""
+    from paper_1507_02557_b300.inputs import random_state
+    g = dg.Mesh(mesh, args.order)
+    g.set_state((1e-3 * random_state(g.ndof, 1)).astype(np.float32), on_device=False)
+    dt = g.timestep()
+    g.step(args.warmup, dt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if args.case == "lsrk":
+        g.step(args.steps, dt)
+    else:
+        lam = torch.from_numpy(random_state(g.ndof, 2).astype(np.float32)).cuda()
+        grad = torch.zeros(sum(mesh.nelem), dtype=torch.float64, device="cuda")
+        g.adjoint_step(args.steps, lam, grad, dt)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "order": args.order, "cells": args.cells, "ndof": g.ndof,
+                      "steps": args.steps, "wall_s": time.perf_counter() - t0}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -360,6 +381,10 @@ def main():
     ap.add_argument("--cells", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--case", choices=["lsrk", "adjoint"], default=None,
+                    help="run one small case only (for profiling): LSRK steps at --order, or one adjoint "
+                         "window of --steps steps with the c^2 gradient, on the --cells x --cells x 80 mesh")
+    ap.add_argument("--order", type=int, default=ORDER)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -380,6 +405,8 @@ def main():
     import json
 
     mesh = scale_mesh(args.cells, args.cells)
+    if args.case:
+        return run_case(args, dg, torch, mesh)
     stream = torch.cuda.current_stream()
     peaks = {}
     try:

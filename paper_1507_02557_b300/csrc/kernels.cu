@@ -54,7 +54,7 @@ template <int N, int MODE>
 __global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
   using C = HexCfg<N>;
   constexpr int n1 = C::n1, NP = C::NP, NQ = C::NQ, EPB = C::EPB, TPE = C::TPE;
-  __shared__ float s_q[EPB][4][NP];
+  __shared__ float4 s_q4[EPB][NP];   // (p, u, v, w) per node
   __shared__ float s_geo[EPB][24];
   __shared__ float s_F[EPB][6][4][NQ];
   __shared__ float s_n[EPB][6][3][NQ];
@@ -76,7 +76,8 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
   const int64_t base = A.dof_off + e * NP;
   if (valid && tid < NP) {
 #pragma unroll
-    for (int f = 0; f < 4; ++f) s_q[le][f][tid] = A.q[f * A.ndof + base + tid];
+    s_q4[le][tid] = make_float4(A.q[base + tid], A.q[A.ndof + base + tid], A.q[2 * A.ndof + base + tid],
+                                A.q[3 * A.ndof + base + tid]);
   }
   if (valid && tid < 24) s_geo[le][tid] = A.geo[e * 24 + tid];
   __syncthreads();
@@ -89,19 +90,21 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
   if (MODE != MODE_TRACE) {
     // ---- volume term, Alg. hex_vol: collocated strong form (M^{-1} cancels w J)
     if (valid && tid < NP) {
-      float dr[4], ds[4], dt[4];
+      float dr[4] = {0.f, 0.f, 0.f, 0.f}, ds[4] = {0.f, 0.f, 0.f, 0.f}, dt[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+      for (int m = 0; m < n1; ++m) {
+        const float di = s_D[i * n1 + m], dj = s_D[j * n1 + m], dk = s_D[k * n1 + m];
+        const float4 vr = s_q4[le][m + n1 * (j + n1 * k)];
+        const float4 vs = s_q4[le][i + n1 * (m + n1 * k)];
+        const float4 vt = s_q4[le][i + n1 * (j + n1 * m)];
+        const float r4[4] = {vr.x, vr.y, vr.z, vr.w}, s4[4] = {vs.x, vs.y, vs.z, vs.w};
+        const float t4[4] = {vt.x, vt.y, vt.z, vt.w};
 #pragma unroll
-        for (int m = 0; m < n1; ++m) {
-          a0 += s_D[i * n1 + m] * s_q[le][f][m + n1 * (j + n1 * k)];
-          a1 += s_D[j * n1 + m] * s_q[le][f][i + n1 * (m + n1 * k)];
-          a2 += s_D[k * n1 + m] * s_q[le][f][i + n1 * (j + n1 * m)];
+        for (int f = 0; f < 4; ++f) {
+          dr[f] += di * r4[f];
+          ds[f] += dj * s4[f];
+          dt[f] += dk * t4[f];
         }
-        dr[f] = a0;
-        ds[f] = a1;
-        dt[f] = a2;
       }
       float xr[3], xs[3], xt[3], g0[3], g1[3], g2[3];
       hex_jac(s_geo[le], s_r[i], s_r[j], s_r[k], xr, xs, xt);
@@ -139,16 +142,15 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
       const float Js = sqrtf(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
       const float inv = sg / Js;
       nv[0] *= inv; nv[1] *= inv; nv[2] *= inv;
-      float tr[4];
+      float tr[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int fl = 0; fl < 4; ++fl) {
-        float acc = 0.f;
-#pragma unroll
-        for (int m = 0; m < n1; ++m) {
-          int id = ax == 0 ? m + n1 * (a + n1 * b) : ax == 1 ? a + n1 * (m + n1 * b) : a + n1 * (b + n1 * m);
-          acc += V[m] * s_q[le][fl][id];
-        }
-        tr[fl] = acc;
+      for (int m = 0; m < n1; ++m) {
+        const int id = ax == 0 ? m + n1 * (a + n1 * b) : ax == 1 ? a + n1 * (m + n1 * b) : a + n1 * (b + n1 * m);
+        const float4 v = s_q4[le][id];
+        tr[0] += V[m] * v.x;
+        tr[1] += V[m] * v.y;
+        tr[2] += V[m] * v.z;
+        tr[3] += V[m] * v.w;
       }
       const float unm = nv[0] * tr[1] + nv[1] * tr[2] + nv[2] * tr[3];
       const int64_t gs = A.side_off + e * 6 + f;
@@ -188,11 +190,13 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
 #pragma unroll
         for (int fl = 0; fl < 4; ++fl) A.rhs[fl * A.ndof + base + tid] = rhs[fl];
       } else {
+        const float4 qo = s_q4[le][tid];
+        const float qv[4] = {qo.x, qo.y, qo.z, qo.w};
 #pragma unroll
         for (int fl = 0; fl < 4; ++fl) {
           const int64_t id = fl * A.ndof + base + tid;
           float r = A.a * A.res[id] + A.dt * rhs[fl];
-          float qn = s_q[le][fl][tid] + A.b * r;
+          float qn = qv[fl] + A.b * r;
           A.res[id] = r;
           A.qout[id] = qn;
           rhs[fl] = qn;
@@ -202,8 +206,7 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
     if (MODE == MODE_STAGE) {
       __syncthreads();
       if (valid && tid < NP) {
-#pragma unroll
-        for (int fl = 0; fl < 4; ++fl) s_q[le][fl][tid] = rhs[fl];
+        s_q4[le][tid] = make_float4(rhs[0], rhs[1], rhs[2], rhs[3]);
       }
     }
   }
@@ -238,16 +241,15 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
         const float inv = sg / sqrtf(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
         nv[0] *= inv; nv[1] *= inv; nv[2] *= inv;
       }
-      float tr[4];
+      float tr[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int fl = 0; fl < 4; ++fl) {
-        float acc = 0.f;
-#pragma unroll
-        for (int m = 0; m < n1; ++m) {
-          int id = ax == 0 ? m + n1 * (a + n1 * b) : ax == 1 ? a + n1 * (m + n1 * b) : a + n1 * (b + n1 * m);
-          acc += V[m] * s_q[le][fl][id];
-        }
-        tr[fl] = acc;
+      for (int m = 0; m < n1; ++m) {
+        const int id = ax == 0 ? m + n1 * (a + n1 * b) : ax == 1 ? a + n1 * (m + n1 * b) : a + n1 * (b + n1 * m);
+        const float4 v = s_q4[le][id];
+        tr[0] += V[m] * v.x;
+        tr[1] += V[m] * v.y;
+        tr[2] += V[m] * v.z;
+        tr[3] += V[m] * v.w;
       }
       const int cidx = s_perm[A.code[gs] * NQ + lp];
       A.tout[dst * NQ + cidx] = tr[0];

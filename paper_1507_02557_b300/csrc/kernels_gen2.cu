@@ -27,6 +27,16 @@
 
 namespace dgk {
 
+// fewest warps per block for which the N >= 5 kernels keep their operators in shared memory
+// (measured at N = 5..7: the tets do better with 16 warps and operators read through L1, the
+// wedges with their operators in shared memory)
+#ifndef DG_G2_MIN_WARPS
+#define DG_G2_MIN_WARPS 6
+#endif
+#ifndef DG_G2_MIN_WARPS_TET
+#define DG_G2_MIN_WARPS_TET 12
+#endif
+
 template <int T, int N>
 struct G2 {
   static constexpr int NP = np_of(T, N), NQ = (N + 1) * (N + 1), NFN = (N + 1) * (N + 2) / 2;
@@ -51,8 +61,14 @@ struct G2 {
   static constexpr int IOPS_B = ((IOPS * 4 + 15) / 16) * 16;
   // per-warp float4 buffers: q4, W4 (wedge: Y/Z pair + X1,X2), F4, G4 (local-order moments),
   // V4 (canonical lattice values)
-  static constexpr int WB = NP + (T == DG_WEDGE ? 2 * NT * N1 + 2 * NC : NP) + NF * NQ + 2 * NTRI * NFN +
-                            (T == DG_PYR ? NKL * N1 + NQ : 0);
+  // wedge volume scratch: Y/Z pairs [2][NT][N1] and the cubature-point intermediates X1, X2, all
+  // NC points at once (N <= 4) or one 1D plane of NQ points at a time (N >= 5); also holds the face
+  // values (Z [2][NT], Y [3][N1][N1], quad traces [3][NQ]) and the lift factors
+  static constexpr bool WPLANE = N >= 5;
+  static constexpr int WXN = WPLANE ? NQ : NC;
+  static constexpr int WV0 = 2 * NT * N1 + 2 * WXN, WV1 = 2 * NT + 3 * N1 * N1 + 3 * NQ;
+  static constexpr int WV = T == DG_WEDGE ? (WV0 > WV1 ? WV0 : WV1) : NP;
+  static constexpr int WB = NP + WV + NF * NQ + 2 * NTRI * NFN + (T == DG_PYR ? NKL * N1 + NQ : 0);
   // tet / pyramid: the volume operator transposed, (D^T)[m][n] = D[n][m] as float4, follows the
   // operators in global memory at float offset OPS_T (host layout size NOPS)
   static constexpr int OPS_T = ((OPS + 3) / 4) * 4;
@@ -66,7 +82,9 @@ struct G2 {
   static constexpr int NW_DEF = T == DG_PYR ? 22 : 16;
   static constexpr int WB_B = WB * 16;
   static constexpr int NW_SM = (SMEM_CAP - OPS_B - IOPS_B) / WB_B;
-  static constexpr bool OPS_SMEM = NW_SM >= (N <= 4 ? NW_DEF : 6);
+  static constexpr bool OPS_SMEM =
+      NW_SM >= (N <= 4 ? NW_DEF : T == DG_TET ? DG_G2_MIN_WARPS_TET : DG_G2_MIN_WARPS);
+  static constexpr int UNR = 4;   // volume loops (8 measured no faster from L2, slower for pyramids)
   static constexpr int NW_FIT = OPS_SMEM ? NW_SM : (SMEM_CAP - IOPS_B) / WB_B;
   static constexpr int NW = NW_FIT < NW_DEF ? NW_FIT : NW_DEF;
   static constexpr int SMEM = (OPS_SMEM ? OPS_B : 0) + IOPS_B + NW * WB_B;
@@ -143,7 +161,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
   int* code = s_code[warp];
   float4* q4 = swarp + warp * C::WB;
   float4* W4 = q4 + NP;
-  float4* F4 = W4 + (T == DG_WEDGE ? 2 * C::NT * C::N1 + 2 * NC : NP);
+  float4* F4 = W4 + C::WV;
   float4* G4 = F4 + NF * NQ;
   float4* V4 = G4 + NTRI * NFN;
   float4* PZB = V4 + NTRI * NFN;                                 // pyramid [NKL][N1]
@@ -330,8 +348,8 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
           if (n >= NP) break;
           float dvr = 0.f, dvs = 0.f, dvt = 0.f, dpr = 0.f, dps = 0.f, dpt = 0.f;
           const float4* drow = DV4 + n * NP;
-          #pragma unroll 4
-        for (int m = 0; m < NP; ++m) {
+#pragma unroll C::UNR
+          for (int m = 0; m < NP; ++m) {
             const float4 d = C::OPS_SMEM ? drow[m] : __ldg(DT4 + m * NP + n), w = W4[m];
             dvr = fmaf(d.x, w.x, dvr);
             dvs = fmaf(d.y, w.y, dvs);
@@ -359,8 +377,8 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
           const int n = lane + 32 * r;
           if (n >= NP) break;
           float pr = 0.f, ps = 0.f, pt = 0.f, dpr = 0.f, dps = 0.f, dpt = 0.f;
-          #pragma unroll 4
-        for (int m = 0; m < NP; ++m) {
+#pragma unroll C::UNR
+          for (int m = 0; m < NP; ++m) {
             const float4 dc = DV4[m * NP + n], w = W4[m];   // (D^a)^T
             pr = fmaf(dc.x, w.x, pr);
             ps = fmaf(dc.y, w.y, ps);
@@ -379,8 +397,8 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
         constexpr int NT = C::NT, N1 = C::N1;
         float4* Y4 = W4;                  // phase 1: [NT][N1] sum_j V1 q ; phase 2: ZA
         float4* Ys4 = W4 + NT * N1;       // phase 1: [NT][N1] sum_j D1 p (x); phase 2: ZB
-        float4* X1 = W4 + 2 * NT * N1;    // [NC] w (A0, A1, A2, UJ)
-        float4* X2 = X1 + NC;             // [NC] w (GU0, GU1, GU2, 0)
+        float4* X1 = W4 + 2 * NT * N1;    // [WXN] w (A0, A1, A2, UJ)
+        float4* X2 = X1 + C::WXN;         // [WXN] w (GU0, GU1, GU2, 0)
         const float* geo = A.geo + e * NC * 12;
         for (int x = lane; x < NT * N1; x += 32) {
           const int mt = x / N1, l = x % N1;
@@ -396,7 +414,13 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
           Ys4[x] = f4(ys, 0.f, 0.f, 0.f);
         }
         __syncwarp();
-        for (int qc = lane; qc < NC; qc += 32) {
+        constexpr bool PL = C::WPLANE;
+        float4* ZA = Y4;
+        float4* ZB = Ys4;
+#pragma unroll 1
+        for (int lp = 0; lp < (PL ? N1 : 1); ++lp) {
+        const int q0 = PL ? lp * NQ : 0, q1 = PL ? q0 + NQ : NC;
+        for (int qc = q0 + lane; qc < q1; qc += 32) {
           const int qt = qc % NQ, l = qc / NQ;
           float P = 0.f, Pr = 0.f, Ps = 0.f, Pt = 0.f, U0 = 0.f, U1 = 0.f, U2 = 0.f;
           const float4* vrow = DV4 + qt * NT;
@@ -417,28 +441,29 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
           const float A1 = g[1] * Pr + g[4] * Ps + g[7] * Pt - P * g[10];
           const float A2 = g[2] * Pr + g[5] * Ps + g[8] * Pt - P * g[11];
           const float UJ = U0 * g[9] + U1 * g[10] + U2 * g[11];
-          X1[qc] = f4(w * A0, w * A1, w * A2, w * UJ);
-          X2[qc] = f4(w * (g[0] * U0 + g[1] * U1 + g[2] * U2), w * (g[3] * U0 + g[4] * U1 + g[5] * U2),
-                      w * (g[6] * U0 + g[7] * U1 + g[8] * U2), 0.f);
+          X1[qc - q0] = f4(w * A0, w * A1, w * A2, w * UJ);
+          X2[qc - q0] = f4(w * (g[0] * U0 + g[1] * U1 + g[2] * U2), w * (g[3] * U0 + g[4] * U1 + g[5] * U2),
+                           w * (g[6] * U0 + g[7] * U1 + g[8] * U2), 0.f);
         }
         __syncwarp();
-        float4* ZA = Y4;
-        float4* ZB = Ys4;
-        for (int x = lane; x < NT * N1; x += 32) {
-          const int mt = x / N1, l = x % N1;
+        // Z of plane l overwrites Y of plane l, whose last reads precede the warp barrier above
+        for (int x = lane; x < NT * (PL ? 1 : N1); x += 32) {
+          const int mt = PL ? x : x / N1, l = PL ? lp : x % N1;
+          const int xo = PL ? 0 : NQ * l;
           float4 za = f4(0.f, 0.f, 0.f, 0.f);
           float zr = 0.f, zs = 0.f;
 #pragma unroll 5
           for (int qt = 0; qt < NQ; ++qt) {
-            const float4 v = DV4[qt * NT + mt], x1 = X1[qt + NQ * l], x2 = X2[qt + NQ * l];
+            const float4 v = DV4[qt * NT + mt], x1 = X1[qt + xo], x2 = X2[qt + xo];
             f4acc(za, v.x, x1);
             zr = fmaf(v.y, x2.x, fmaf(v.z, x2.z, zr));
             zs = fmaf(v.x, x2.y, zs);
           }
-          ZA[x] = za;
-          ZB[x] = f4(zr, zs, 0.f, 0.f);
+          ZA[mt * N1 + l] = za;
+          ZB[mt * N1 + l] = f4(zr, zs, 0.f, 0.f);
         }
         __syncwarp();
+        }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const int n = lane + 32 * r;
