@@ -135,13 +135,13 @@ __global__ void grad_vol_kernel(TypeView V, int64_t ndof, const float* rho, cons
   for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < V.K;
        e += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const int64_t base = V.dof_off + e * V.Np;
-    double acc = 0.0;
+    float acc = 0.f;   // FP32 products of FP32 fields; FP64 only for the accumulation into g
     for (int n = lane; n < V.Np; n += 32)
 #pragma unroll
-      for (int f = 1; f < 4; ++f) acc += (double)rho[f * ndof + base + n] * y[f * ndof + base + n];
+      for (int f = 1; f < 4; ++f) acc = fmaf(rho[f * ndof + base + n], y[f * ndof + base + n], acc);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) g[V.goff + e] += dt * acc / V.c2[e];
+    if (lane == 0) g[V.goff + e] += dt * (double)acc / V.c2[e];
   }
 }
 
@@ -185,7 +185,7 @@ __global__ void grad_face_kernel(FaceView F, const float* TQ, const float* TV, d
   const int npt = lat ? F.nfn : F.nq;
   const int64_t o = s * F.nq, on = (int64_t)(nb >= 0 ? nb : 0) * F.nq;
   float jqp[MAX_NFN], jvp[MAX_NFN], jqn[MAX_NFN], jvn[MAX_NFN];
-  double Ip = 0.0, Iu = 0.0;
+  float Ip = 0.f, Iu = 0.f;   // FP32 sums of FP32 trace products (FP64 is slow here)
   for (int i = 0; i < npt; ++i) {
     float qp, vp, qn = 0.f, vn = 0.f;
     if (nb >= 0) {   // jumps [x] = x(neighbour) - x(own); u.n planes carry each writer's normal
@@ -200,20 +200,20 @@ __global__ void grad_face_kernel(FaceView F, const float* TQ, const float* TV, d
     if (lat) {
       jqp[i] = qp; jvp[i] = vp; jqn[i] = qn; jvn[i] = vn;
     } else {
-      const double w = F.fw[o + i];
-      Ip += w * qp * vp;
-      Iu += w * qn * vn;
+      const float w = F.fw[o + i];
+      Ip = fmaf(w * qp, vp, Ip);
+      Iu = fmaf(w * qn, vn, Iu);
     }
   }
   if (lat) {
     for (int i = 0; i < npt; ++i) {
-      double sp = 0.0, su = 0.0;
+      float sp = 0.f, su = 0.f;
       for (int j = 0; j < npt; ++j) {
-        sp += (double)F.Mf[i * F.nfn + j] * jvp[j];
-        su += (double)F.Mf[i * F.nfn + j] * jvn[j];
+        sp = fmaf(F.Mf[i * F.nfn + j], jvp[j], sp);
+        su = fmaf(F.Mf[i * F.nfn + j], jvn[j], su);
       }
-      Ip += jqp[i] * sp;
-      Iu += jqn[i] * su;
+      Ip = fmaf(jqp[i], sp, Ip);
+      Iu = fmaf(jqn[i], su, Iu);
     }
     Ip *= F.fw[o];
     Iu *= F.fw[o];
