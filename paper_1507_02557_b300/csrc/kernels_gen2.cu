@@ -85,9 +85,20 @@ struct G2 {
   static constexpr bool OPS_SMEM =
       NW_SM >= (N <= 4 ? NW_DEF : T == DG_TET ? DG_G2_MIN_WARPS_TET : DG_G2_MIN_WARPS);
   static constexpr int UNR = 4;   // volume loops (8 measured no faster from L2, slower for pyramids)
-  static constexpr int NW_FIT = OPS_SMEM ? NW_SM : (SMEM_CAP - IOPS_B) / WB_B;
+  // Tets whose operators are read from global memory: the block stages the volume operator in
+  // chunks of CM rows that all its warps use, so each operator entry crosses from L2 once per
+  // block iteration instead of once per element (N = 6: 14.3 -> 11.9 ms, N = 7: 30.8 -> 22.1 ms
+  // per step on the throughput mesh).  Pyramids stage D and D^T per chunk: at N = 6 (10-row
+  // chunks) that pays (17.7 -> 15.5 ms); at N = 7 the chunks are 7 rows and the block barriers
+  // cost more than the L2 reads saved (29.9 -> 36.1 ms), so there they read through L1.
+  static constexpr bool CHUNK = !OPS_SMEM && (T == DG_TET || (T == DG_PYR && N == 6));
+  static constexpr int NOPV = T == DG_PYR ? 2 : 1;
+  static constexpr int CM0 = 49152 / (NP * 16 * NOPV);
+  static constexpr int CM = CM0 < 4 ? 4 : (CM0 > NP ? NP : CM0);
+  static constexpr int CHUNK_B = CHUNK ? CM * NP * 16 * NOPV : 0;
+  static constexpr int NW_FIT = OPS_SMEM ? NW_SM : (SMEM_CAP - IOPS_B - CHUNK_B) / WB_B;
   static constexpr int NW = NW_FIT < NW_DEF ? NW_FIT : NW_DEF;
-  static constexpr int SMEM = (OPS_SMEM ? OPS_B : 0) + IOPS_B + NW * WB_B;
+  static constexpr int SMEM = (OPS_SMEM ? OPS_B : 0) + IOPS_B + CHUNK_B + NW * WB_B;
   static constexpr int R = (NP + 31) / 32;
   static_assert(N > 4 || (OPS_SMEM && NW == NW_DEF), "N <= 4 keeps its operators and warps in shared memory");
   static_assert(NW >= 1, "per-warp buffers exceed the shared memory");
@@ -123,7 +134,8 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int OPS_SB = C::OPS_SMEM ? C::OPS_B : 0;
   int* sio = reinterpret_cast<int*>(smem_raw + OPS_SB);
-  float4* swarp = reinterpret_cast<float4*>(smem_raw + OPS_SB + C::IOPS_B);
+  float4* sch = reinterpret_cast<float4*>(smem_raw + OPS_SB + C::IOPS_B);   // [NOPV][CM][NP] (CHUNK)
+  float4* swarp = reinterpret_cast<float4*>(smem_raw + OPS_SB + C::IOPS_B + C::CHUNK_B);
   if constexpr (C::OPS_SMEM) {
     float* sops = reinterpret_cast<float*>(smem_raw);
     for (int x = threadIdx.x; x < C::OPS; x += blockDim.x) sops[x] = A.ops2[x];
@@ -167,7 +179,13 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
   float4* PZB = V4 + NTRI * NFN;                                 // pyramid [NKL][N1]
   float4* PTQB = PZB + NKL * C::N1;                              // pyramid [NQ] base traces
 
-  for (int64_t li = (int64_t)blockIdx.x * NW + warp; li < A.K; li += (int64_t)gridDim.x * NW) {
+  // CHUNK: the block's warps walk their elements in step (lb is the block's first) and every warp
+  // takes part in every operator chunk (block barriers); a warp past the end redoes the last
+  // element and stores nothing.  Otherwise each warp walks its own elements (lb is the warp's).
+  for (int64_t lb = (int64_t)blockIdx.x * NW + (C::CHUNK ? 0 : warp); lb < A.K; lb += (int64_t)gridDim.x * NW) {
+    const int64_t li_raw = C::CHUNK ? lb + warp : lb;
+    const bool act = C::CHUNK ? li_raw < A.K : true;
+    const int64_t li = act ? li_raw : A.K - 1;
     const int64_t e = A.elist ? (int64_t)A.elist[li] : li;
     const int64_t base = A.dof_off + e * NP;
     const float c2 = A.c2[e];
@@ -342,25 +360,52 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
                      G[6] * v.y + G[7] * v.z + G[8] * v.w, v.x);
         }
         __syncwarp();
+        auto tet_acc = [&](float* a, const float4& d, const float4& w) {
+          a[0] = fmaf(d.x, w.x, a[0]);
+          a[1] = fmaf(d.y, w.y, a[1]);
+          a[2] = fmaf(d.z, w.z, a[2]);
+          a[3] = fmaf(d.x, w.w, a[3]);
+          a[4] = fmaf(d.y, w.w, a[4]);
+          a[5] = fmaf(d.z, w.w, a[5]);
+        };
+        auto tet_out = [&](int r, const float* a) {
+          const float div = a[0] + a[1] + a[2];
+          acc[r] = f4(-div, -c2 * (G[0] * a[3] + G[3] * a[4] + G[6] * a[5]),
+                      -c2 * (G[1] * a[3] + G[4] * a[4] + G[7] * a[5]), -c2 * (G[2] * a[3] + G[5] * a[4] + G[8] * a[5]));
+        };
+        if constexpr (C::CHUNK) {   // all rows accumulate across the block's operator chunks
+          float s6[R][6];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const int n = lane + 32 * r;
-          if (n >= NP) break;
-          float dvr = 0.f, dvs = 0.f, dvt = 0.f, dpr = 0.f, dps = 0.f, dpt = 0.f;
-          const float4* drow = DV4 + n * NP;
-#pragma unroll C::UNR
-          for (int m = 0; m < NP; ++m) {
-            const float4 d = C::OPS_SMEM ? drow[m] : __ldg(DT4 + m * NP + n), w = W4[m];
-            dvr = fmaf(d.x, w.x, dvr);
-            dvs = fmaf(d.y, w.y, dvs);
-            dvt = fmaf(d.z, w.z, dvt);
-            dpr = fmaf(d.x, w.w, dpr);
-            dps = fmaf(d.y, w.w, dps);
-            dpt = fmaf(d.z, w.w, dpt);
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) s6[r][c] = 0.f;
+          for (int m0 = 0; m0 < NP; m0 += C::CM) {
+            const int mc = NP - m0 < C::CM ? NP - m0 : C::CM;
+            __syncthreads();
+            for (int x = threadIdx.x; x < mc * NP; x += blockDim.x) sch[x] = __ldg(DT4 + (size_t)m0 * NP + x);
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              const int n = lane + 32 * r;
+              if (n >= NP) break;
+#pragma unroll 4
+              for (int mm = 0; mm < mc; ++mm) tet_acc(s6[r], sch[mm * NP + n], W4[m0 + mm]);
+            }
           }
-          const float div = dvr + dvs + dvt;
-          acc[r] = f4(-div, -c2 * (G[0] * dpr + G[3] * dps + G[6] * dpt), -c2 * (G[1] * dpr + G[4] * dps + G[7] * dpt),
-                      -c2 * (G[2] * dpr + G[5] * dps + G[8] * dpt));
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+            if (lane + 32 * r < NP) tet_out(r, s6[r]);
+        } else {   // one row at a time
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int n = lane + 32 * r;
+            if (n >= NP) break;
+            float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const float4* drow = DV4 + n * NP;
+#pragma unroll C::UNR
+            for (int m = 0; m < NP; ++m) tet_acc(a, C::OPS_SMEM ? drow[m] : __ldg(DT4 + m * NP + n), W4[m]);
+            tet_out(r, a);
+          }
         }
       } else if (T == DG_PYR) {
         const float* geo = A.geo + e * NP * 10;
@@ -372,26 +417,57 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
                      J * (g[6] * v.y + g[7] * v.z + g[8] * v.w), v.x);
         }
         __syncwarp();
+        // (D^a)^T against J G u (skew part), D^a against p
+        auto pyr_acc = [&](float* a, const float4& dc, const float4& dr, const float4& w) {
+          a[0] = fmaf(dc.x, w.x, a[0]);
+          a[1] = fmaf(dc.y, w.y, a[1]);
+          a[2] = fmaf(dc.z, w.z, a[2]);
+          a[3] = fmaf(dr.x, w.w, a[3]);
+          a[4] = fmaf(dr.y, w.w, a[4]);
+          a[5] = fmaf(dr.z, w.w, a[5]);
+        };
+        auto pyr_out = [&](int r, const float* a) {
+          const float* g = geo + (lane + 32 * r) * 10;
+          acc[r] = f4((a[0] + a[1] + a[2]) / g[9], -c2 * (g[0] * a[3] + g[3] * a[4] + g[6] * a[5]),
+                      -c2 * (g[1] * a[3] + g[4] * a[4] + g[7] * a[5]), -c2 * (g[2] * a[3] + g[5] * a[4] + g[8] * a[5]));
+        };
+        if constexpr (C::CHUNK) {   // all rows accumulate across the block's operator chunks
+          float s6[R][6];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const int n = lane + 32 * r;
-          if (n >= NP) break;
-          float pr = 0.f, ps = 0.f, pt = 0.f, dpr = 0.f, dps = 0.f, dpt = 0.f;
-#pragma unroll C::UNR
-          for (int m = 0; m < NP; ++m) {
-            const float4 dc = DV4[m * NP + n], w = W4[m];   // (D^a)^T
-            pr = fmaf(dc.x, w.x, pr);
-            ps = fmaf(dc.y, w.y, ps);
-            pt = fmaf(dc.z, w.z, pt);
-            const float4 dr = C::OPS_SMEM ? DV4[n * NP + m] : __ldg(DT4 + m * NP + n);
-            dpr = fmaf(dr.x, w.w, dpr);
-            dps = fmaf(dr.y, w.w, dps);
-            dpt = fmaf(dr.z, w.w, dpt);
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) s6[r][c] = 0.f;
+          float4* schT = sch + C::CM * NP;
+          for (int m0 = 0; m0 < NP; m0 += C::CM) {
+            const int mc = NP - m0 < C::CM ? NP - m0 : C::CM;
+            __syncthreads();
+            for (int x = threadIdx.x; x < mc * NP; x += blockDim.x) {
+              sch[x] = __ldg(DV4 + (size_t)m0 * NP + x);
+              schT[x] = __ldg(DT4 + (size_t)m0 * NP + x);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              const int n = lane + 32 * r;
+              if (n >= NP) break;
+#pragma unroll 4
+              for (int mm = 0; mm < mc; ++mm) pyr_acc(s6[r], sch[mm * NP + n], schT[mm * NP + n], W4[m0 + mm]);
+            }
           }
-          const float* g = geo + n * 10;
-          const float pint = pr + ps + pt;
-          acc[r] = f4(pint / g[9], -c2 * (g[0] * dpr + g[3] * dps + g[6] * dpt),
-                      -c2 * (g[1] * dpr + g[4] * dps + g[7] * dpt), -c2 * (g[2] * dpr + g[5] * dps + g[8] * dpt));
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+            if (lane + 32 * r < NP) pyr_out(r, s6[r]);
+        } else {   // one row at a time
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int n = lane + 32 * r;
+            if (n >= NP) break;
+            float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll C::UNR
+            for (int m = 0; m < NP; ++m)
+              pyr_acc(a, DV4[m * NP + n], C::OPS_SMEM ? DV4[n * NP + m] : __ldg(DT4 + m * NP + n), W4[m]);
+            pyr_out(r, a);
+          }
         }
       } else {   // wedge, sum-factorised (triangle x 1D) form of Alg. wedge_vol1/2
         constexpr int NT = C::NT, N1 = C::N1;
@@ -605,7 +681,8 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
         acc[r].z += c2 * iM * sum.z;
         acc[r].w += c2 * iM * sum.w;
       }
-      if (MODE == MODE_RHS) {
+      if (!act) {
+      } else if (MODE == MODE_RHS) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const int n = lane + 32 * r;
@@ -700,8 +777,8 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
       }
       __syncwarp();
     };
-    if (MODE != MODE_RHS) emit(A.tout);
-    if (MODE == MODE_MRC) {
+    if (MODE != MODE_RHS && act) emit(A.tout);
+    if (MODE == MODE_MRC && act) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int n = lane + 32 * r;
