@@ -31,6 +31,15 @@ struct HexCfg {
   static constexpr int NT = TPE * EPB;
 };
 
+// a x + y on the four fields as two packed FP32 pair FMAs (round to nearest, the same values as
+// four fmaf)
+__device__ __forceinline__ float4 f4fma(float a, float4 x, float4 y) {
+  const float2 aa = make_float2(a, a);
+  const float2 lo = __ffma2_rn(aa, make_float2(x.x, x.y), make_float2(y.x, y.y));
+  const float2 hi = __ffma2_rn(aa, make_float2(x.z, x.w), make_float2(y.z, y.w));
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
 // x_r, x_s, x_t of the trilinear map at (r,s,t); g = c1..c7 (3 floats each)
 __device__ __forceinline__ void hex_jac(const float* g, float r, float s, float t, float xr[3],
                                         float xs[3], float xt[3]) {
@@ -90,22 +99,15 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
   if (MODE != MODE_TRACE) {
     // ---- volume term, Alg. hex_vol: collocated strong form (M^{-1} cancels w J)
     if (valid && tid < NP) {
-      float dr[4] = {0.f, 0.f, 0.f, 0.f}, ds[4] = {0.f, 0.f, 0.f, 0.f}, dt[4] = {0.f, 0.f, 0.f, 0.f};
+      float4 dr4 = make_float4(0.f, 0.f, 0.f, 0.f), ds4 = dr4, dt4 = dr4;
 #pragma unroll
       for (int m = 0; m < n1; ++m) {
-        const float di = s_D[i * n1 + m], dj = s_D[j * n1 + m], dk = s_D[k * n1 + m];
-        const float4 vr = s_q4[le][m + n1 * (j + n1 * k)];
-        const float4 vs = s_q4[le][i + n1 * (m + n1 * k)];
-        const float4 vt = s_q4[le][i + n1 * (j + n1 * m)];
-        const float r4[4] = {vr.x, vr.y, vr.z, vr.w}, s4[4] = {vs.x, vs.y, vs.z, vs.w};
-        const float t4[4] = {vt.x, vt.y, vt.z, vt.w};
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          dr[f] += di * r4[f];
-          ds[f] += dj * s4[f];
-          dt[f] += dk * t4[f];
-        }
+        dr4 = f4fma(s_D[i * n1 + m], s_q4[le][m + n1 * (j + n1 * k)], dr4);
+        ds4 = f4fma(s_D[j * n1 + m], s_q4[le][i + n1 * (m + n1 * k)], ds4);
+        dt4 = f4fma(s_D[k * n1 + m], s_q4[le][i + n1 * (j + n1 * m)], dt4);
       }
+      const float dr[4] = {dr4.x, dr4.y, dr4.z, dr4.w}, ds[4] = {ds4.x, ds4.y, ds4.z, ds4.w};
+      const float dt[4] = {dt4.x, dt4.y, dt4.z, dt4.w};
       float xr[3], xs[3], xt[3], g0[3], g1[3], g2[3];
       hex_jac(s_geo[le], s_r[i], s_r[j], s_r[k], xr, xs, xt);
       cross3(xs, xt, g0);
@@ -142,16 +144,13 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
       const float Js = sqrtf(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
       const float inv = sg / Js;
       nv[0] *= inv; nv[1] *= inv; nv[2] *= inv;
-      float tr[4] = {0.f, 0.f, 0.f, 0.f};
+      float4 tr4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int m = 0; m < n1; ++m) {
         const int id = ax == 0 ? m + n1 * (a + n1 * b) : ax == 1 ? a + n1 * (m + n1 * b) : a + n1 * (b + n1 * m);
-        const float4 v = s_q4[le][id];
-        tr[0] += V[m] * v.x;
-        tr[1] += V[m] * v.y;
-        tr[2] += V[m] * v.z;
-        tr[3] += V[m] * v.w;
+        tr4 = f4fma(V[m], s_q4[le][id], tr4);
       }
+      const float tr[4] = {tr4.x, tr4.y, tr4.z, tr4.w};
       const float unm = nv[0] * tr[1] + nv[1] * tr[2] + nv[2] * tr[3];
       const int64_t gs = A.side_off + e * 6 + f;
       const int nb = A.nbr[gs];
@@ -241,16 +240,13 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
         const float inv = sg / sqrtf(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
         nv[0] *= inv; nv[1] *= inv; nv[2] *= inv;
       }
-      float tr[4] = {0.f, 0.f, 0.f, 0.f};
+      float4 tr4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int m = 0; m < n1; ++m) {
         const int id = ax == 0 ? m + n1 * (a + n1 * b) : ax == 1 ? a + n1 * (m + n1 * b) : a + n1 * (b + n1 * m);
-        const float4 v = s_q4[le][id];
-        tr[0] += V[m] * v.x;
-        tr[1] += V[m] * v.y;
-        tr[2] += V[m] * v.z;
-        tr[3] += V[m] * v.w;
+        tr4 = f4fma(V[m], s_q4[le][id], tr4);
       }
+      const float tr[4] = {tr4.x, tr4.y, tr4.z, tr4.w};
       const int cidx = s_perm[A.code[gs] * NQ + lp];
       A.tout[dst * NQ + cidx] = tr[0];
       A.tout[A.plane + dst * NQ + cidx] = nv[0] * tr[1] + nv[1] * tr[2] + nv[2] * tr[3];
@@ -283,10 +279,6 @@ struct HexW {
   static constexpr int WPB = 4;         // warps per block
   static constexpr int EPB = EPW * WPB;
 };
-
-__device__ __forceinline__ float4 f4fma(float a, float4 x, float4 y) {
-  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
-}
 
 // Outward unit normal and surface Jacobian at point (a,b) of hex face f (local face parameters).
 template <int N>
@@ -677,13 +669,10 @@ __global__ void __launch_bounds__(128, DG_HEXP_MINB) hexw_kernel(Args A, const _
           dr = f4fma(Dri[m], s_q[m + n1 * j + NQ * k], dr);
           ds = f4fma(Dsj[m], s_q[i + n1 * m + NQ * k], ds);
         }
-        float dt[4] = {0.f, 0.f, 0.f, 0.f};
+        float4 dt4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int m = 0; m < n1; ++m) {
-          const float dk = Dm[k * n1 + m];
-#pragma unroll
-          for (int f = 0; f < 4; ++f) dt[f] = fmaf(dk, q[f][m], dt[f]);
-        }
+        for (int m = 0; m < n1; ++m) dt4 = f4fma(Dm[k * n1 + m], make_float4(q[0][m], q[1][m], q[2][m], q[3][m]), dt4);
+        const float dt[4] = {dt4.x, dt4.y, dt4.z, dt4.w};
         const float drf[4] = {dr.x, dr.y, dr.z, dr.w}, dsf[4] = {ds.x, ds.y, ds.z, ds.w};
         // -div u and -c^2 grad p
         float div = 0.f;

@@ -105,11 +105,12 @@ struct G2 {
 };
 
 __device__ __forceinline__ float4 f4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+// s += c v on the four fields as two packed FP32 pair FMAs (the same values as four fmaf)
 __device__ __forceinline__ void f4acc(float4& s, float c, const float4& v) {
-  s.x = fmaf(c, v.x, s.x);
-  s.y = fmaf(c, v.y, s.y);
-  s.z = fmaf(c, v.z, s.z);
-  s.w = fmaf(c, v.w, s.w);
+  const float2 cc = make_float2(c, c);
+  const float2 lo = __ffma2_rn(cc, make_float2(v.x, v.y), make_float2(s.x, s.y));
+  const float2 hi = __ffma2_rn(cc, make_float2(v.z, v.w), make_float2(s.z, s.w));
+  s = make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
 // face f of type T: triangle index (or -1) and quad index (or -1)
