@@ -455,7 +455,9 @@ def main():
            (ORDER + 1) * (ORDER + 2) * (2 * ORDER + 3) // 6, (ORDER + 1) * (ORDER + 2) * (ORDER + 3) // 6]
     ndof_fine = sum(c * n for c, n in zip(fine, npe))
     g.step(args.warmup, h)                                   # includes the LSRK start-up
+    E_before = g.energy()                                    # synchronises; outside the timed region
     ms, kms, launches, clk = timed_run(g, torch, stream, args.steps, h, barrier)
+    E_after = g.energy()
     ms = max_ms(ms)
     stage_units = (ndof + ndof_fine) * args.steps * world    # rhs evaluations actually performed
     value = stage_units / (ms / 1e3) / 1e9
@@ -537,7 +539,9 @@ def main():
                              "traffic": traffic, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
                 "kernel_ms": dict(zip(["hex", "wedge", "pyramid", "tet"], kms)),
                 "gpu_launches": int(sum(launches)) + 2 * 4 * args.steps,
-                "single_rate": single, "sem_hex": sem, "e2e": e2e, "clocks": clk}
+                "single_rate": single, "sem_hex": sem, "e2e": e2e, "clocks": clk,
+                "energy": {"before": E_before, "after": E_after, "rel_change": (E_after - E_before) / E_before,
+                           "note": "discrete energy of the timed multi-rate steps (upwind: non-increasing)"}}
         if batch:
             line["batch"] = batch
         if diff:

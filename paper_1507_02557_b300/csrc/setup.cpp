@@ -12,6 +12,7 @@
 #include <array>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -318,11 +319,23 @@ int key_to_code(int nv, const int key[4]) {
 
 thread_local bool g_host_only = false;   // dg_host_check: run the host setup only
 
+// Device bytes of the current setup call and an optional budget (environment DG_DEVICE_BYTES_LIMIT,
+// read per dg_mesh_create): past it the setup fails with DG_ENOMEM before calling cudaMalloc, so
+// out-of-memory handling can be exercised without exhausting a GPU.
+thread_local size_t g_dev_bytes = 0, g_dev_limit = 0;
+void* device_alloc(size_t bytes) {
+  if (g_dev_limit && g_dev_bytes + bytes > g_dev_limit)
+    throw SetupError(DG_ENOMEM, "device byte budget (DG_DEVICE_BYTES_LIMIT) exceeded");
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) throw SetupError(DG_ENOMEM, "cudaMalloc failed");
+  g_dev_bytes += bytes;
+  return p;
+}
+
 template <class T>
 T* upload(const std::vector<T>& h, std::vector<void*>& owned) {
   if (h.empty() || g_host_only) return nullptr;
-  void* p = nullptr;
-  if (cudaMalloc(&p, h.size() * sizeof(T)) != cudaSuccess) throw SetupError(DG_ENOMEM, "cudaMalloc failed");
+  void* p = device_alloc(h.size() * sizeof(T));
   owned.push_back(p);
   if (cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
     throw SetupError(DG_ECUDA, "cudaMemcpy failed");
@@ -334,7 +347,7 @@ T* alloc_zero(size_t n, std::vector<void*>& owned) {
   void* p = nullptr;
   if (g_host_only) return nullptr;
   if (n == 0) n = 1;
-  if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) throw SetupError(DG_ENOMEM, "cudaMalloc failed");
+  p = device_alloc(n * sizeof(T));
   owned.push_back(p);
   if (cudaMemset(p, 0, n * sizeof(T)) != cudaSuccess) throw SetupError(DG_ECUDA, "cudaMemset failed");
   return static_cast<T*>(p);
@@ -466,6 +479,9 @@ void dg_free(dg_mesh* m) {
 }
 
 dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
+  g_dev_bytes = 0;
+  const char* lim = std::getenv("DG_DEVICE_BYTES_LIMIT");
+  g_dev_limit = lim ? std::strtoull(lim, nullptr, 10) : 0;
   try {
     std::vector<void*>& owned = owned_list(m);
     const int N = d->N;

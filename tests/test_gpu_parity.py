@@ -211,7 +211,7 @@ def test_watchdog_reports_timeout(lib):
     assert np.isfinite(g.energy())
 
 
-@pytest.mark.parametrize("N", [2, 3, 4])
+@pytest.mark.parametrize("N", [2, 3, 4, 5])
 def test_error_against_exact_mode_matches_oracle(lib, N):
     """FP32 state with the tensor-core (TF32x3) tets and FP32 SIMT kernels elsewhere: the L2
     error against the exact standing mode after LSRK steps to t = 0.02 equals the FP64 oracle's
@@ -221,7 +221,7 @@ def test_error_against_exact_mode_matches_oracle(lib, N):
     o = DGOracle(m, N)
     q0 = o.project(standing_mode, 0.0)
     g = lib.Mesh(m, N)
-    T = 0.02
+    T = 0.02 if N <= 4 else 0.01        # fewer oracle steps at N = 5
     n = int(np.ceil(T / g.timestep()))
     dt = T / n
     g.set_state(q0.astype(np.float32), on_device=False)

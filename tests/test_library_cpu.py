@@ -106,3 +106,11 @@ def test_batch_calls_reject_bad_arguments_without_a_device():
     assert dg._lib.dg_batch_step(None, 3, None, None) == -1
     assert dg._lib.dg_batch_stats(None, None, None) == -1
     dg._lib.dg_batch_destroy(None)
+
+
+def test_device_byte_budget_fails_cleanly_before_allocating(monkeypatch):
+    """Host-side out-of-memory injection: with a device byte budget the setup stops with
+    DG_ENOMEM before its first cudaMalloc (and frees what it holds)."""
+    monkeypatch.setenv("DG_DEVICE_BYTES_LIMIT", "1")
+    with pytest.raises(dg.DGError, match="out of device memory.*DG_DEVICE_BYTES_LIMIT"):
+        dg.Mesh(small_hybrid_mesh(), 2)
