@@ -24,9 +24,14 @@
  *   - Every call returns a dg_status and never aborts or throws across the ABI.
  *   - Host arrays are borrowed for the duration of the call.  Device pointers
  *     are borrowed; the caller keeps them alive until the stream has finished.
- *   - Work is enqueued on the CUDA stream given to dg_mesh_create.  Only
- *     dg_mesh_create, dg_timestep, dg_energy and dg_get_state(on_device = 0)
- *     synchronise with the host.
+ *   - Work is enqueued on the CUDA stream given to dg_mesh_create.  Inside a
+ *     stage or substep the four element types' kernels run side by side on
+ *     four streams the mesh owns, forked from and joined back into that stream
+ *     with events, so the ordering seen on the given stream is unchanged (set
+ *     DG_TYPE_STREAMS=0 in the environment at creation to keep them on the
+ *     one stream; per-type timing with dg_profile does so while it is on).
+ *     Only dg_mesh_create, dg_timestep, dg_energy and
+ *     dg_get_state(on_device = 0) synchronise with the host.
  *   - Errors: DG_EINVAL bad argument; DG_ENOMEM device allocation failed;
  *     DG_ECUDA a CUDA call failed (dg_last_error() gives the message);
  *     DG_EMESH invalid mesh (J <= 0 at a quadrature point, a face shared by

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -81,6 +82,8 @@ dg_status dg_mesh_create(const dg_mesh_desc* d, void* stream, dg_mesh** out) {
   if (!m) return DG_ENOMEM;
   cudaGetDevice(&m->device);
   m->stream = static_cast<cudaStream_t>(stream);
+  const char* ts = std::getenv("DG_TYPE_STREAMS");
+  m->type_streams = !(ts && ts[0] == '0');
   std::string err;
   dg_status st = dg_setup(m, d, err);
   if (st != DG_OK) {
@@ -88,6 +91,12 @@ dg_status dg_mesh_create(const dg_mesh_desc* d, void* stream, dg_mesh** out) {
     dg_free(m);
     delete m;
     return st;
+  }
+  if (m->type_streams) {   // created here, not inside a later stream capture
+    bool ok = true;
+    for (int t = 0; t < 4 && ok; ++t) ok = cudaStreamCreateWithFlags(&m->tstream[t], cudaStreamNonBlocking) == cudaSuccess;
+    for (int t = 0; t < 5 && ok; ++t) ok = cudaEventCreateWithFlags(&m->tev[t], cudaEventDisableTiming) == cudaSuccess;
+    m->type_streams = ok;
   }
   *out = m;
   return DG_OK;
@@ -118,6 +127,10 @@ void dg_mesh_destroy(dg_mesh* m) {
   if (!m) return;
   cudaStreamSynchronize(m->stream);
   for (cudaEvent_t ev : m->ev_pool) cudaEventDestroy(ev);
+  for (int t = 0; t < 4; ++t)
+    if (m->tstream[t]) cudaStreamSynchronize(m->tstream[t]), cudaStreamDestroy(m->tstream[t]);
+  for (int t = 0; t < 5; ++t)
+    if (m->tev[t]) cudaEventDestroy(m->tev[t]);
   dg_free(m);
   delete m;
 }

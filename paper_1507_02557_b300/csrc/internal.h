@@ -87,6 +87,11 @@ struct dg_mesh {
   bool hex_sem = false;           // SEM hexahedra (GLL nodes)
   bool tri_lat = true;            // tet / pyramid triangle faces exchange lattice values (gen2)
   bool wall_self = false;         // trace launches also write a wall side's own trace into its slot
+  // element types of one stage / substep on their own streams (off with DG_TYPE_STREAMS=0, and
+  // while per-type timing is on)
+  bool type_streams = false;
+  cudaStream_t tstream[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t tev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   // adjoint (adjoint.cu): host data kept by the setup, device copies made on first use
   std::vector<float> face_w;      // [nsides][nq] w_q J^s at the canonical points (lattice faces: J^s)
   std::vector<double> face_mass;  // [nfn][nfn] face mass of the triangle lattice basis

@@ -1414,12 +1414,26 @@ static void launch_type(dg_mesh* m, const Args& A, int t) {
 
 template <int MODE>
 static void launch_all(dg_mesh* m, Args* A, const Sel* sel = nullptr) {
+  // the four types of one launch group read the previous trace buffer and write disjoint slots of
+  // the next, so they may run side by side (per-type timing keeps them on one stream)
+  const bool par = m->type_streams && !m->profiling && m->tev[4];
+  if (par) cudaEventRecord(m->tev[4], m->stream);
   for (int t = 0; t < 4; ++t) {
     if (sel) {
       A[t].elist = sel->list[t];
       A[t].K = (int)sel->count[t];
     }
-    launch_type<MODE>(m, A[t], t);
+    if (par && A[t].K > 0) {
+      cudaStream_t home = m->stream;
+      cudaStreamWaitEvent(m->tstream[t], m->tev[4], 0);
+      m->stream = m->tstream[t];
+      launch_type<MODE>(m, A[t], t);
+      m->stream = home;
+      cudaEventRecord(m->tev[t], m->tstream[t]);
+      cudaStreamWaitEvent(home, m->tev[t], 0);
+    } else {
+      launch_type<MODE>(m, A[t], t);
+    }
   }
 }
 
