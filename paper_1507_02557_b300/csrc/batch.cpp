@@ -35,16 +35,20 @@ namespace {
 
 constexpr size_t MAX_GRAPHS = 4;
 
-// Runs f with the mesh's work going to stream s (and per-launch timing off), then restores both.
+// Runs f with the mesh's work going to stream s, per-launch timing off and the element types on
+// that one stream (the meshes' branches already run side by side; per-type forks would only add
+// graph nodes), then restores all three.
 template <class F>
 cudaError_t on_stream(dg_mesh* m, cudaStream_t s, F f) {
   cudaStream_t keep = m->stream;
-  bool prof = m->profiling;
+  const bool prof = m->profiling, ts = m->type_streams;
   m->stream = s;
   m->profiling = false;
+  m->type_streams = false;
   cudaError_t e = f();
   m->stream = keep;
   m->profiling = prof;
+  m->type_streams = ts;
   return e;
 }
 
