@@ -240,6 +240,21 @@ def batch_run(dg, torch, stream, barrier, world, steps=6):
         res["graph_over_eager"] = res["graph"] / res["eager"]
         res["graph_replays_captures"] = list(b.stats())
         b.close()
+        # the same graph after dg_autotune picked each mesh's kernel choices
+        t1 = time.perf_counter()
+        picks = [g.autotune(2) for g in ms]
+        res["autotune_s"] = time.perf_counter() - t1
+        res["autotune_picks"] = {k: sum(p[k] for p in picks) for k in ms[0].CHOICES}
+        b = dg.Batch(ms, stream=stream.cuda_stream)
+        graph()
+        barrier()
+        t1 = time.perf_counter()
+        graph()
+        barrier()
+        res["graph_tuned"] = units / (time.perf_counter() - t1) / 1e9
+        b.close()
+        for g in ms:
+            g.set_choices()
         out[name] = res
     del meshes
     torch.cuda.synchronize()

@@ -171,6 +171,22 @@ dg_status dg_profile(dg_mesh *mesh, int enable, double *ms, int64_t *launches);
  * DG_EINVAL for a null mesh or a limit out of range. */
 dg_status dg_watchdog_selftest(dg_mesh *mesh, int64_t limit_cycles);
 
+/* Autotuner: picks, for this mesh, among the kernel choices the library has at
+ * run time by timing nsteps (1..100) LSRK(5,4) steps of dt_min of a scratch
+ * copy of the state on the mesh's stream, one choice after the other (the
+ * others held): [0] TMA staging of the fused N = 4 hex kernels or cp.async
+ * staging, [1] tensor-core tets (N <= 4) or the SIMT tet kernel, [2] the element
+ * types of a stage on their own streams or on one.  The choices hold for all
+ * later calls on the mesh (a batch graph bakes in those at its capture); the
+ * results of the alternatives agree to FP32 rounding.  choice[3] (host, or
+ * NULL) receives them (1 = the first alternative).  nsteps = 0 applies
+ * choice[] as given instead (no timing, no synchronisation; choice[2] is set
+ * to 0 where the mesh has no type streams).  Synchronises; allocates
+ * one state copy for the call; the mesh's state is unchanged, its LSRK residual
+ * and trace buffers are overwritten.  No counterpart in the paper (Sec. 4.3
+ * notes the cost per degree of freedom changing with the number of elements). */
+dg_status dg_autotune(dg_mesh *mesh, int nsteps, int *choice);
+
 /* ---- batches: many meshes stepped together ---------------------------------
  * Sec. 4.3 (Figure perDofTimes) measures the time per degree of freedom rising
  * for small meshes, whose kernels cannot fill the GPU.  A batch steps several

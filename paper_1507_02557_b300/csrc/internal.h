@@ -90,6 +90,8 @@ struct dg_mesh {
   // element types of one stage / substep on their own streams (off with DG_TYPE_STREAMS=0, and
   // while per-type timing is on)
   bool type_streams = false;
+  // kernel choices (dg_autotune): TMA staging of the fused N = 4 hex kernels, tensor-core tets
+  bool use_hex_tma = true, use_tet_tc = true;
   cudaStream_t tstream[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t tev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   // adjoint (adjoint.cu): host data kept by the setup, device copies made on first use

@@ -1367,7 +1367,7 @@ template <int N, int MODE, bool SEM>
 static void launch_hex_fast_b(dg_mesh* m, const Args& A, cudaStream_t s) {
   HexMaps M{};
   if constexpr (N == 4 && (MODE == MODE_STAGE || MODE == MODE_MRC || MODE == MODE_MRF)) {
-    if (hex_maps<MODE>(m, A, &M)) {
+    if (m->use_hex_tma && hex_maps<MODE>(m, A, &M)) {
       launch_hexw_n<N, MODE, true, SEM>(A, M, s);
       return;
     }
@@ -1394,7 +1394,7 @@ static void launch_type(dg_mesh* m, const Args& A, int t) {
 #define DG_CASE(NN)                                                   \
   case NN:                                                            \
     if (t == DG_HEX) { if (NN <= 4) launch_hex_fast<(NN <= 4 ? NN : 4), MODE>(m, A, s); else launch_hex_n<NN, (MODE > 2 ? 1 : MODE)>(A, s); } \
-    else if (DG_TET_TC && t == DG_TET && m->tri_lat && launch_tet_tc<MODE>(NN, A, s)) {}   \
+    else if (DG_TET_TC && t == DG_TET && m->tri_lat && m->use_tet_tc && launch_tet_tc<MODE>(NN, A, s)) {}   \
     else if ((t == DG_WEDGE || m->tri_lat) && launch_gen2<MODE>(t, NN, A, s)) {}   \
     else if (t == DG_WEDGE) launch_gen_n<DG_WEDGE, NN, (MODE > 2 ? 1 : MODE)>(A, s);   \
     else if (t == DG_PYR) launch_gen_n<DG_PYR, NN, (MODE > 2 ? 1 : MODE)>(A, s);       \

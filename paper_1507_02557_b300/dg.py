@@ -22,7 +22,7 @@ EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_host_check", "dg_layout", "d
            "dg_set_state", "dg_get_state", "dg_rhs", "dg_timestep", "dg_step", "dg_state_ptr",
            "dg_energy", "dg_energy_noalloc", "dg_profile", "dg_watchdog_selftest", "dg_adjoint_step",
            "dg_batch_create", "dg_batch_step", "dg_batch_stats", "dg_batch_destroy",
-           "dg_set_source", "dg_set_receivers", "dg_sample_receivers",
+           "dg_set_source", "dg_set_receivers", "dg_sample_receivers", "dg_autotune",
            "dg_status_string", "dg_last_error")
 
 
@@ -52,6 +52,7 @@ _lib.dg_energy.argtypes = [_vp, _vp, C.POINTER(C.c_double)]
 _lib.dg_energy_noalloc.argtypes = [_vp, _vp, C.POINTER(C.c_double)]
 _lib.dg_watchdog_selftest.argtypes = [_vp, C.c_int64]
 _lib.dg_adjoint_step.argtypes = [_vp, C.c_int, C.c_double, C.c_double, _vp, _vp, _vp, _vp]
+_lib.dg_autotune.argtypes = [_vp, C.c_int, C.POINTER(C.c_int)]
 _lib.dg_set_source.argtypes = [_vp, C.POINTER(C.c_double), C.c_double, C.c_double, C.c_double]
 _lib.dg_set_receivers.argtypes = [_vp, C.c_int, C.POINTER(C.c_double)]
 _lib.dg_sample_receivers.argtypes = [_vp, _vp, _vp]
@@ -196,6 +197,20 @@ class Mesh:
         opt = lambda x: _ptr(x) if x is not None else None
         _check(_lib.dg_adjoint_step(self._h, int(nsteps), float(dt), float(t0), _ptr(lam_dev), opt(resid_dev),
                                     opt(grad_c2_dev), opt(grad_amp_dev)))
+
+    CHOICES = ("hex_tma", "tet_tensor_cores", "type_streams")
+
+    def autotune(self, nsteps=2):
+        """dg_autotune: {"hex_tma", "tet_tensor_cores", "type_streams"} chosen for this mesh."""
+        c = (C.c_int * 3)()
+        _check(_lib.dg_autotune(self._h, int(nsteps), c))
+        return dict(zip(self.CHOICES, (bool(v) for v in c)))
+
+    def set_choices(self, hex_tma=True, tet_tensor_cores=True, type_streams=True):
+        """dg_autotune with nsteps = 0: apply kernel choices; returns those in effect."""
+        c = (C.c_int * 3)(int(hex_tma), int(tet_tensor_cores), int(type_streams))
+        _check(_lib.dg_autotune(self._h, 0, c))
+        return dict(zip(self.CHOICES, (bool(v) for v in c)))
 
     def set_source(self, x, amp, f0, t0):
         """dg_set_source: Ricker point source amp ricker(t; f0, t0) at x (inside a hexahedron)."""

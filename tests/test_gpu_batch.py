@@ -132,3 +132,30 @@ def test_gl_and_sem_meshes_of_one_order_coexist(lib):
     g.rhs(q, r1)
     torch.cuda.synchronize()
     assert torch.equal(r0, r1)
+
+
+def test_autotune_choices_all_match_the_oracle(lib):
+    """Every combination of the run-time kernel choices (TMA / cp.async hex staging, tensor-core /
+    SIMT tets, element types on their own streams or one) gives the oracle's LSRK steps; the
+    autotuner leaves the mesh's state as it found it and picks one of them."""
+    from oracle.dg import standing_mode
+    import itertools
+    m = small_hybrid_mesh()
+    N = 4
+    o = DGOracle(m, N)
+    q0 = o.project(standing_mode, 0.0).astype(np.float32)
+    g = lib.Mesh(m, N)
+    dt = g.timestep()
+    q = q0.astype(np.float64)
+    for _ in range(3):
+        q = o.lsrk_step(q, dt)
+    for combo in itertools.product((True, False), repeat=3):
+        g.set_choices(*combo)
+        g.set_state(q0, on_device=False)
+        g.step(3, dt)
+        got = g.get_state(np.zeros_like(q0), on_device=False).astype(np.float64)
+        assert float(np.linalg.norm(got - q) / np.linalg.norm(q)) < TOL, combo
+    g.set_state(q0, on_device=False)
+    ch = g.autotune(2)
+    assert set(ch) == set(g.CHOICES)
+    assert np.array_equal(g.get_state(np.zeros_like(q0), on_device=False), q0)
