@@ -122,6 +122,12 @@ __global__ void mass_tet_kernel(TypeView V, const float* Mh, const float* Minv, 
   }
 }
 
+// traces of F v from those of v: the p plane as is, the u.n plane negated
+__global__ void flip_traces_kernel(int64_t plane, const float* tv, float* tfv) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * plane; i += (int64_t)gridDim.x * blockDim.x)
+    tfv[i] = i < plane ? tv[i] : -tv[i];
+}
+
 // y = a y + b x over n floats
 __global__ void axpby_kernel(int64_t n, float a, float* y, float b, const float* x) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -387,7 +393,12 @@ cudaError_t dg_adjoint_run(dg_mesh* m, int nsteps, double dt, double t0, float* 
         grad_face_kernel<<<(unsigned)((m->nsides + 255) / 256), 256, 0, st>>>(F, TB[0], TB[1], grad, dt);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
       }
-      if ((e = launch_trace(m, fv, TB[0])) != cudaSuccess) return e;
+      if (grad) {   // traces of F v = those of v (in TB[1]) with u.n negated: no trace launch
+        flip_traces_kernel<<<grid_for(2 * (int64_t)plane, 256), 256, 0, st>>>((int64_t)plane, TB[1], TB[0]);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      } else if ((e = launch_trace(m, fv, TB[0])) != cudaSuccess) {
+        return e;
+      }
       if ((e = launch_rhs(m, fv, TB[0], z)) != cudaSuccess) return e;
       if ((e = apply_mass(m, 1, z, lam, nullptr, (float)dt)) != cudaSuccess) return e;
       if (k > 0 && (e = axpby(m, fs, (float)RK_A[k], rho, 0.f, nullptr)) != cudaSuccess) return e;
