@@ -341,14 +341,14 @@ cudaError_t dg_adjoint_run(dg_mesh* m, int nsteps, double dt, double t0, float* 
   // step states S[j] = q_j, j < nsteps
   if ((e = cudaMemcpyAsync(S, m->q, fs * sizeof(float), cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
   for (int j = 0; j + 1 < nsteps; ++j) {
+    float* qp = S + (size_t)j * fs;
     float* qj = S + (size_t)(j + 1) * fs;
-    if ((e = cudaMemcpyAsync(qj, S + (size_t)j * fs, fs * sizeof(float), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
-      return e;
-    if ((e = launch_trace(m, qj, TB[0])) != cudaSuccess) return e;
+    if ((e = launch_trace(m, qp, TB[0])) != cudaSuccess) return e;
     int cur = 0;
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < 5; ++k) {   // the first stage writes q_{j+1} from q_j, the others update it
       dg_source_at(m, t0 + (j + RK_C[k]) * dt);
-      e = launch_stage(m, qj, m->res, TB[cur], TB[cur ^ 1], (float)RK_A[k], (float)RK_B[k], (float)dt);
+      e = launch_stage(m, k == 0 ? qp : qj, m->res, TB[cur], TB[cur ^ 1], (float)RK_A[k], (float)RK_B[k], (float)dt,
+                       qj);
       m->src_now = 0.f;
       if (e != cudaSuccess) return e;
       cur ^= 1;
@@ -361,13 +361,11 @@ cudaError_t dg_adjoint_run(dg_mesh* m, int nsteps, double dt, double t0, float* 
     // stage inputs q^1..q^4 of step j (the stage kernels update in place)
     if ((e = launch_trace(m, Sj, TB[0])) != cudaSuccess) return e;
     int cur = 0;
-    for (int k = 0; k < 4; ++k) {
-      float* dst = stage_state(k + 1);
-      if ((e = cudaMemcpyAsync(dst, k == 0 ? Sj : stage_state(k), fs * sizeof(float), cudaMemcpyDeviceToDevice, st)) !=
-          cudaSuccess)
-        return e;
+    for (int k = 0; k < 4; ++k) {   // out of place: q^{k+1} from q^k
+      float* src = k == 0 ? Sj : stage_state(k);
       dg_source_at(m, t0 + (j + RK_C[k]) * dt);
-      e = launch_stage(m, dst, m->res, TB[cur], TB[cur ^ 1], (float)RK_A[k], (float)RK_B[k], (float)dt);
+      e = launch_stage(m, src, m->res, TB[cur], TB[cur ^ 1], (float)RK_A[k], (float)RK_B[k], (float)dt,
+                       stage_state(k + 1));
       m->src_now = 0.f;
       if (e != cudaSuccess) return e;
       cur ^= 1;

@@ -127,8 +127,9 @@ namespace dgk {
 // Kernel launchers (kernels.cu).  Return cudaSuccess or the launch error.
 cudaError_t launch_trace(dg_mesh* m, const float* q, float* tout);
 cudaError_t launch_rhs(dg_mesh* m, const float* q, const float* tin, float* rhs);
+// (qout: the updated state, NULL = in place)
 cudaError_t launch_stage(dg_mesh* m, float* q, float* res, const float* tin, float* tout, float a,
-                         float b, float dt);
+                         float b, float dt, float* qout = nullptr);
 cudaError_t launch_energy(dg_mesh* m, const float* q, double* acc);
 cudaError_t launch_trace_sel(dg_mesh* m, const float* q, float* tout, const Sel& sel);
 cudaError_t launch_rhs_sel(dg_mesh* m, const float* q, const float* tin, float* rhs, const Sel& sel);

@@ -1517,12 +1517,12 @@ cudaError_t launch_rhs(dg_mesh* m, const float* q, const float* tin, float* rhs)
 }
 
 cudaError_t launch_stage(dg_mesh* m, float* q, float* res, const float* tin, float* tout, float a,
-                         float b, float dt) {
+                         float b, float dt, float* qout) {
   Args A[4];
   for (int t = 0; t < 4; ++t) {
     A[t] = make_args(m, t);
     A[t].q = q;
-    A[t].qout = q;
+    A[t].qout = qout ? qout : q;
     A[t].res = res;
     A[t].tin = tin;
     A[t].tout = tout;
