@@ -442,6 +442,11 @@ dg_status dg_adjoint_step(dg_mesh* m, int nsteps, double dt, double t0, float* l
   if (!(dt > 0)) dt = m->dt_min;
   if (nsteps == 0) return DG_OK;
   cudaError_t e = dg_adjoint_run(m, nsteps, dt, t0, lambda, resid, g_c2, g_amp);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();   // clear the (non-sticky) allocation error
+    g_err = "dg_adjoint_step: scratch of nsteps + 9 states does not fit; use shorter windows";
+    return DG_ENOMEM;
+  }
   if (e != cudaSuccess) return cuda_fail(e);
   return DG_OK;
 }
