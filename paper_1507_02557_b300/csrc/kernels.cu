@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
   constexpr int n1 = C::n1, NP = C::NP, NQ = C::NQ, EPB = C::EPB, TPE = C::TPE;
   __shared__ float4 s_q4[EPB][NP];   // (p, u, v, w) per node
   __shared__ float s_geo[EPB][24];
-  __shared__ float s_F[EPB][6][4][NQ];
+  __shared__ float4 s_F4[EPB][6][NQ];   // J^s-weighted fluxes (p, u, v, w) per face point
   __shared__ float s_n[EPB][6][3][NQ];
   __shared__ float s_D[n1 * n1], s_Vm[n1], s_Vp[n1], s_w[n1], s_r[n1];
   __shared__ int s_perm[8 * NQ];
@@ -164,10 +164,7 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
       float fp, fu;
       flux(nb < 0, tr[0], unm, P, UN, tp, tu, false, fp, fu);
       const float wgt = s_w[a] * s_w[b] * Js;
-      s_F[le][f][0][lp] = wgt * fp;
-      s_F[le][f][1][lp] = wgt * fu * nv[0];
-      s_F[le][f][2][lp] = wgt * fu * nv[1];
-      s_F[le][f][3][lp] = wgt * fu * nv[2];
+      s_F4[le][f][lp] = make_float4(wgt * fp, wgt * fu * nv[0], wgt * fu * nv[1], wgt * fu * nv[2]);
       s_n[le][f][0][lp] = nv[0];
       s_n[le][f][1][lp] = nv[1];
       s_n[le][f][2][lp] = nv[2];
@@ -177,13 +174,16 @@ __global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
     if (valid && tid < NP) {
       const float iM = 1.f / (s_w[i] * s_w[j] * s_w[k] * Jn);
       const int jk = j + n1 * k, ik = i + n1 * k, ij = i + n1 * j;
+      float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+      sum = f4fma(s_Vm[i], s_F4[le][0][jk], sum);
+      sum = f4fma(s_Vp[i], s_F4[le][1][jk], sum);
+      sum = f4fma(s_Vm[j], s_F4[le][2][ik], sum);
+      sum = f4fma(s_Vp[j], s_F4[le][3][ik], sum);
+      sum = f4fma(s_Vm[k], s_F4[le][4][ij], sum);
+      sum = f4fma(s_Vp[k], s_F4[le][5][ij], sum);
+      const float sf[4] = {sum.x, sum.y, sum.z, sum.w};
 #pragma unroll
-      for (int fl = 0; fl < 4; ++fl) {
-        float sum = s_Vm[i] * s_F[le][0][fl][jk] + s_Vp[i] * s_F[le][1][fl][jk] +
-                    s_Vm[j] * s_F[le][2][fl][ik] + s_Vp[j] * s_F[le][3][fl][ik] +
-                    s_Vm[k] * s_F[le][4][fl][ij] + s_Vp[k] * s_F[le][5][fl][ij];
-        rhs[fl] += (fl == 0 ? 1.f : c2) * iM * sum;
-      }
+      for (int fl = 0; fl < 4; ++fl) rhs[fl] += (fl == 0 ? 1.f : c2) * iM * sf[fl];
       if (e == A.src_e) rhs[0] += A.src_s * A.src_g[tid];   // point source on p
       if (MODE == MODE_RHS) {
 #pragma unroll
