@@ -29,6 +29,8 @@ struct HexCfg {
   static constexpr int TPE = ((NP + 31) / 32) * 32;
   static constexpr int EPB = TPE >= 256 ? 1 : 256 / TPE;
   static constexpr int NT = TPE * EPB;
+  // resident blocks per SM the register allocation aims at (N = 5..7: 6, 4, 3)
+  static constexpr int MINB = N >= 7 ? 3 : N == 6 ? 4 : N == 5 ? 6 : 1;
 };
 
 // a x + y on the four fields as two packed FP32 pair FMAs (round to nearest, the same values as
@@ -60,7 +62,7 @@ __device__ __forceinline__ void cross3(const float a[3], const float b[3], float
 }
 
 template <int N, int MODE>
-__global__ void __launch_bounds__(HexCfg<N>::NT) hex_kernel(Args A) {
+__global__ void __launch_bounds__(HexCfg<N>::NT, HexCfg<N>::MINB) hex_kernel(Args A) {
   using C = HexCfg<N>;
   constexpr int n1 = C::n1, NP = C::NP, NQ = C::NQ, EPB = C::EPB, TPE = C::TPE;
   __shared__ float4 s_q4[EPB][NP];   // (p, u, v, w) per node
