@@ -29,8 +29,9 @@ struct HexCfg {
   static constexpr int TPE = ((NP + 31) / 32) * 32;
   static constexpr int EPB = TPE >= 256 ? 1 : 256 / TPE;
   static constexpr int NT = TPE * EPB;
-  // resident blocks per SM the register allocation aims at (N = 5..7: 6, 4, 3)
-  static constexpr int MINB = N >= 7 ? 3 : N == 6 ? 4 : N == 5 ? 6 : 1;
+  // resident blocks per SM the register allocation aims at (measured best: N = 5..7: 8, 5, 3; one
+  // more block at N = 7 spills enough to lose)
+  static constexpr int MINB = N >= 7 ? 3 : N == 6 ? 5 : N == 5 ? 8 : 1;
 };
 
 // a x + y on the four fields as two packed FP32 pair FMAs (round to nearest, the same values as
