@@ -68,7 +68,7 @@ struct G2 {
   static constexpr int WXN = WPLANE ? NQ : NC;
   static constexpr int WV0 = 2 * NT * N1 + 2 * WXN, WV1 = 2 * NT + 3 * N1 * N1 + 3 * NQ;
   static constexpr int WV = T == DG_WEDGE ? (WV0 > WV1 ? WV0 : WV1) : NP;
-  static constexpr int WB = NP + WV + NF * NQ + 2 * NTRI * NFN + (T == DG_PYR ? NKL * N1 + NQ : 0);
+  static constexpr int WB = NP + WV + NFX + 2 * NTRI * NFN + (T == DG_PYR ? NKL * N1 + NQ : 0);   // F4: NFX
   // tet / pyramid: the volume operator transposed, (D^T)[m][n] = D[n][m] as float4, follows the
   // operators in global memory at float offset OPS_T (host layout size NOPS)
   static constexpr int OPS_T = ((OPS + 3) / 4) * 4;
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
   float4* q4 = swarp + warp * C::WB;
   float4* W4 = q4 + NP;
   float4* F4 = W4 + C::WV;
-  float4* G4 = F4 + NF * NQ;
+  float4* G4 = F4 + NFX;
   float4* V4 = G4 + NTRI * NFN;
   float4* PZB = V4 + NTRI * NFN;                                 // pyramid [NKL][N1]
   float4* PTQB = PZB + NKL * C::N1;                              // pyramid [NQ] base traces
