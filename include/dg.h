@@ -174,7 +174,8 @@ dg_status dg_watchdog_selftest(dg_mesh *mesh, int64_t limit_cycles);
 /* Autotuner: picks, for this mesh, among the kernel choices the library has at
  * run time by timing nsteps (1..100) LSRK(5,4) steps of dt_min of a scratch
  * copy of the state on the mesh's stream, one choice after the other (the
- * others held): [0] TMA staging of the fused N = 4 hex kernels or cp.async
+ * others held; best of three runs, an alternative taken only when at least 2 %
+ * faster): [0] TMA staging of the fused N = 4 hex kernels or cp.async
  * staging, [1] tensor-core tets (N <= 4) or the SIMT tet kernel, [2] the element
  * types of a stage on their own streams or on one.  The choices hold for all
  * later calls on the mesh (a batch graph bakes in those at its capture); the

@@ -6,7 +6,8 @@
 // Which is faster depends on the mesh: small meshes leave SMs idle (the tensor-core kernel works
 // on tiles of 32 tets), large ones are bound by the per-type kernels.  Each choice is tried in
 // turn, the others held at their current values (coordinate descent, one pass), on nsteps
-// LSRK(5,4) steps of a scratch copy of the state; the mesh's state is not modified.
+// LSRK(5,4) steps of a scratch copy of the state (best of three runs), and taken only when it is
+// at least 2 % faster than the current choice; the mesh's state is not modified.
 #include <cuda_runtime.h>
 
 #include <string>
@@ -65,11 +66,18 @@ extern "C" dg_status dg_autotune(dg_mesh* m, int nsteps, int* choice) {
   const bool prof = m->profiling;
   m->profiling = false;
   const double dt = m->dt_min;
+  // best of three timed runs after a warm-up run (the first launches of a variant)
   auto trial = [&](float* ms) {
     cudaError_t r = cudaMemcpyAsync(qs, m->q, bytes, cudaMemcpyDeviceToDevice, m->stream);
-    if (r == cudaSuccess) r = time_steps(m, qs, 1, dt, ms);   // warm-up (first launch of a variant)
-    if (r == cudaSuccess) r = cudaMemcpyAsync(qs, m->q, bytes, cudaMemcpyDeviceToDevice, m->stream);
-    if (r == cudaSuccess) r = time_steps(m, qs, nsteps, dt, ms);
+    if (r == cudaSuccess) r = time_steps(m, qs, 1, dt, ms);
+    float best = 3.4e38f;
+    for (int rep = 0; rep < 3 && r == cudaSuccess; ++rep) {
+      r = cudaMemcpyAsync(qs, m->q, bytes, cudaMemcpyDeviceToDevice, m->stream);
+      float t = 0.f;
+      if (r == cudaSuccess) r = time_steps(m, qs, nsteps, dt, &t);
+      if (t < best) best = t;
+    }
+    *ms = best;
     return r;
   };
   for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
@@ -80,7 +88,7 @@ extern "C" dg_status dg_autotune(dg_mesh* m, int nsteps, int* choice) {
     if (e != cudaSuccess) break;
     *knob[c] = !cur;
     e = trial(&t_alt);
-    if (e != cudaSuccess || !(t_alt < t_cur)) *knob[c] = cur;
+    if (e != cudaSuccess || !(t_alt < 0.98f * t_cur)) *knob[c] = cur;   // switch on a clear gain only
   }
   m->profiling = prof;
   cudaFree(qs);
