@@ -55,7 +55,12 @@ struct G2 {
   static constexpr bool LAT = T != DG_WEDGE;                            // lattice-point face exchange
   static constexpr int TN2 = 0;
   static constexpr int NFX = LAT ? NTRI * NFN + NQUAD * NQ : NF * NQ;   // face flux points
-  static constexpr int OPS = VOL + TN + TQ + TN2 + NQ * NFN;
+  // pyramid N <= 4: the volume loop reads D^a[m][n] (a = r, s, t) and D^t[n][m] as one float4
+  // (the .w of the operator entry) and D^r[n][m], D^s[n][m] as a float2 from PV2, laid out
+  // [m][n] so that the lanes' reads are contiguous: 6 words instead of two float4 per product
+  static constexpr bool PK = T == DG_PYR && N <= 4;
+  static constexpr int PV2 = PK ? 2 * NP * NP : 0;
+  static constexpr int OPS = VOL + PV2 + TN + TQ + TN2 + NQ * NFN;
   static constexpr int IOPS = 12 * NFN + 8 * NQ + (T == DG_TET ? 4 * NFN : 0);
   static constexpr int OPS_B = ((OPS * 4 + 15) / 16) * 16;
   static constexpr int IOPS_B = ((IOPS * 4 + 15) / 16) * 16;
@@ -150,7 +155,8 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
   const float* V1 = sop + NQ * C::NT * 4;                        // wedge [N1][N1] (l, j)
   const float* D1 = V1 + C::N1 * C::N1;
   const float* wq = D1 + C::N1 * C::N1;                          // wedge weights [NQ][N1]
-  const float* Tn = sop + C::VOL;                                // [NTRI][NFN][NP]
+  const float2* P2 = reinterpret_cast<const float2*>(sop + C::VOL);   // pyramid N <= 4 [NP][NP]
+  const float* Tn = sop + C::VOL + C::PV2;                      // [NTRI][NFN][NP]
   const float* Tq = Tn + C::TN;                                  // [NQUAD][NQ][NP]
   const float* E = Tq + C::TQ;                                   // [NQ][NFN]
   constexpr bool LAT = C::LAT;
@@ -458,6 +464,20 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
 #pragma unroll
           for (int r = 0; r < R; ++r)
             if (lane + 32 * r < NP) pyr_out(r, s6[r]);
+        } else if constexpr (C::PK) {   // operator entry + its transpose in 6 words
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int n = lane + 32 * r;
+            if (n >= NP) break;
+            float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll C::UNR
+            for (int m = 0; m < NP; ++m) {
+              const float4 dc = DV4[m * NP + n], w = W4[m];
+              const float2 d2 = P2[m * NP + n];
+              pyr_acc(a, dc, f4(d2.x, d2.y, dc.w, 0.f), w);
+            }
+            pyr_out(r, a);
+          }
         } else {   // one row at a time
 #pragma unroll
           for (int r = 0; r < R; ++r) {

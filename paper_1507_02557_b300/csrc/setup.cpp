@@ -1051,17 +1051,23 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
         };
         std::vector<double> gg(3 * Np);
         if (t == TET || t == PYR) {
-          // DV4[n][m] = (D^r, D^s, D^t)[n][m], row n = node / test function
+          // DV4[n][m] = (D^r, D^s, D^t)[n][m], row n = node / test function; pyramid .w = D^t[m][n]
           for (int n = 0; n < Np; ++n)
             for (int mm = 0; mm < Np; ++mm) {
               if (t == TET) {
                 // ops holds DT[a][m][n]
                 for (int a = 0; a < 3; ++a) o2.push_back(ops[(a * Np + mm) * Np + n]);
+                o2.push_back(0.f);
               } else {
                 for (int a = 0; a < 3; ++a) o2.push_back(ops[(a * Np + n) * Np + mm]);
+                o2.push_back(ops[(2 * Np + mm) * Np + n]);
               }
-              o2.push_back(0.f);
             }
+          // pyramid N <= 4: P2[m][n] = (D^r, D^s)[n][m] (the gen2 kernel reads it from shared memory)
+          if (t == PYR && N <= 4)
+            for (int mm = 0; mm < Np; ++mm)
+              for (int n = 0; n < Np; ++n)
+                for (int a = 0; a < 2; ++a) o2.push_back(ops[(a * Np + n) * Np + mm]);
         }
         if (t == TET) {
           std::vector<int> fnode(4 * nfn, -1);
