@@ -198,3 +198,35 @@ def test_mrab3_is_third_order():
             qr = o.lsrk_step(qr, T / nref)
         errs.append(np.linalg.norm(q - qr) / np.linalg.norm(qr))
     assert 6.0 < errs[0] / errs[1] < 11.0, errs
+
+
+@pytest.mark.parametrize("level", [1, 2])
+def test_mrab3_on_one_level_is_single_rate_ab3(mesh, level):
+    """Sec. 2.4 reading: with every element on one level the multi-rate scheme is plain
+    Adams-Bashforth 3 (coefficients 23/12, -16/12, 5/12 from integrating the quadratic through the
+    last three rhs values): all coarse, one AB3 step of 2h per coarse step; all fine, two AB3 steps
+    of h.  The start-up history (LSRK steps, rhs at 0, 2h, 3h) is the one AB3 needs at 4h."""
+    from oracle.dg import MRAB3
+    N = 2
+    o = DGOracle(mesh, N)
+    lev = [np.full(k, level, dtype=int) for k in o.K]
+    q0 = random_state(o.ndof, 9)
+    h = 1e-3
+    mr = MRAB3(o, lev)
+    q, hist = mr.start(q0, h)
+    for _ in range(3):
+        q, hist = mr.step(q, hist, h)
+    # plain AB3 from the same start-up
+    qa = q0.copy()
+    rs = {}
+    for k in range(4):
+        if k in (0, 2, 3):
+            rs[k] = o.rhs(qa)
+        qa = o.lsrk_step(qa, h)
+    H = 2 * h if level == 1 else h
+    hist_a = [rs[2], rs[0]] if level == 1 else [rs[3], rs[2]]
+    for _ in range(3 if level == 1 else 6):
+        r = o.rhs(qa)
+        qa = qa + H * (23 * r - 16 * hist_a[0] + 5 * hist_a[1]) / 12
+        hist_a = [r, hist_a[0]]
+    assert np.abs(q - qa).max() < 1e-13 * np.abs(qa).max()
