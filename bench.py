@@ -63,46 +63,131 @@ def sample_mesh(n):
     return layered_mesh(n, n, len(L), L, seed=0, c_of_layer=lambda k: 1.0 if k % 2 == 0 else 1.5)
 
 
-def oracle_rate(n, steps, warmup=0):
-    """GDOF-stage/s of the FP64 oracle on an n x n x 80 sample (this process's threads)."""
+def oracle_rate(n, steps, warmup=0, t_go=None):
+    """GDOF-stage/s of the FP64 oracle on an n x n x 80 sample (this process's threads).  With
+    t_go (a time.time() value) the timed steps start no earlier than t_go, so that concurrent
+    processes time the same interval.  Returns (rate, ndof, seconds, start, end)."""
     from oracle.dg import DGOracle
     from paper_1507_02557_b300.inputs import random_state
     o = DGOracle(sample_mesh(n), ORDER)
     q = 1e-3 * random_state(o.ndof, 0)
     for _ in range(warmup):
         q = o.lsrk_step(q, 1e-4)
+    if t_go is not None and time.time() < t_go:
+        time.sleep(t_go - time.time())
+    start = time.time()
     t0 = time.perf_counter()
     for _ in range(steps):
         q = o.lsrk_step(q, 1e-4)
     dt = time.perf_counter() - t0
-    return o.ndof * 5 * steps / dt / 1e9, o.ndof, dt
+    return o.ndof * 5 * steps / dt / 1e9, o.ndof, dt, start, time.time()
 
 
-def cpu_baseline(n=4, steps=3):
-    """Run the oracle in a single-threaded child process on an n x n x 80 sample."""
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def _oracle_children(count, n, steps, t_go, warmup=0):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     code = ("import json,sys; sys.path.insert(0, %r); import bench; "
-            "r = bench.oracle_rate(%d, %d); print(json.dumps(r))" % (ROOT, n, steps))
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
-    rate, ndof, secs = json.loads(out.stdout.strip().splitlines()[-1])
-    return {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"{n}x{n}x80-cell sample of the workload ({ndof} DOFs, N={ORDER}), "
-                      f"{steps} LSRK steps in {secs:.1f} s, FP64 numpy, 1 thread"}
+            "print(json.dumps(bench.oracle_rate(%d, %d, %d, %r)))" % (ROOT, n, steps, warmup, t_go))
+    procs = [subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
+                              stderr=subprocess.DEVNULL, text=True) for _ in range(count)]
+    out = []
+    for p in procs:
+        o, _ = p.communicate(timeout=900)
+        out.append(json.loads(o.strip().splitlines()[-1]))
+    return out
+
+
+def _oracle_children_warm(count, n, steps, warmup):
+    """As _oracle_children, with warmup untimed LSRK steps in each child before the common start
+    (set far enough ahead for the children's set-up and warm-up)."""
+    return _oracle_children(count, n, steps, time.time() + 20.0 + 2.0 * warmup, warmup)
+
+
+def cpu_baseline(n1=4, steps1=3, n_all=2, steps_all=3):
+    """The oracle as it stands (FP64 numpy, one thread per process; each child is a fresh
+    interpreter started as a subprocess, not a fork of this CUDA process).
+
+    one core:  one child on an n1 x n1 x 80 sample, steps1 LSRK steps;
+    all cores: nproc concurrent children, each stepping its own n_all x n_all x 80 sample (the
+               oracle has no threading of its own, so the host's cores are used as independent
+               processes, the way a partitioned run would use them); their timed steps start at a
+               common time, and the rate is all their element-stages over the span from the first
+               start to the last end."""
+    one = _oracle_children(1, n1, steps1, None)[0]
+    cores = os.cpu_count() or 1
+    res = _oracle_children(cores, n_all, steps_all, time.time() + 20.0)
+    span = max(r[4] for r in res) - min(r[3] for r in res)
+    units = sum(r[1] * 5 * steps_all for r in res)
+    ndof_all = res[0][1]
+    return {"value": units / span / 1e9, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "cpu": cpu_model(), "nproc": cores,
+            "sample": f"{cores} concurrent single-thread oracle processes, each {steps_all} LSRK steps on its own "
+                      f"{n_all}x{n_all}x80-cell sample of the workload ({ndof_all} DOFs, N={ORDER}); "
+                      f"span {span:.1f} s; FP64 numpy",
+            "one_core": {"value": one[0], "unit": METRIC, "cores": 1,
+                         "sample": f"{n1}x{n1}x80-cell sample ({one[1]} DOFs, N={ORDER}), {steps1} LSRK steps "
+                                   f"in {one[2]:.1f} s, 1 thread"}}
 
 
 class Clocks:
-    """nvidia-smi clock / throttle sampling during the timed region."""
+    """SM clock and throttle-reason sampling during the timed region: NVML queries (read-only) from
+    a thread every 5 ms, so that even a region of a few tens of milliseconds gets many samples;
+    nvidia-smi at its 100 ms period if NVML is unavailable."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, dev):
         self.dev = dev
         self.p = None
+        self.thread = None
+        self.samples = []          # (sm_mhz, max_mhz, set of reasons)
+
+    def _nvml_handle(self):
+        import pynvml
+        import torch
+        pynvml.nvmlInit()
+        try:
+            bus = torch.cuda.get_device_properties(self.dev).pci_bus_id
+            return pynvml, pynvml.nvmlDeviceGetHandleByPciBusId(bus)
+        except Exception:
+            return pynvml, pynvml.nvmlDeviceGetHandleByIndex(self.dev)
+
+    def _poll(self, nv, h):
+        bits = [nv.nvmlClocksEventReasonHwSlowdown, nv.nvmlClocksEventReasonHwThermalSlowdown,
+                nv.nvmlClocksEventReasonSwThermalSlowdown, nv.nvmlClocksEventReasonSwPowerCap]
+        mx = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+        while not self.stop.is_set():
+            try:
+                sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
+                r = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
+                self.samples.append((float(sm), float(mx), {n for n, b in zip(self.NAMES, bits) if r & b}))
+            except Exception:
+                break
+            self.stop.wait(0.005)
 
     def __enter__(self):
+        import threading
+        try:
+            nv, h = self._nvml_handle()
+            self.stop = threading.Event()
+            self.thread = threading.Thread(target=self._poll, args=(nv, h), daemon=True)
+            self.thread.start()
+            return self
+        except Exception:
+            self.thread = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
                                        "--format=csv,noheader,nounits", "-lms", "100"],
@@ -112,7 +197,10 @@ class Clocks:
         return self
 
     def __exit__(self, *a):
-        self.lines = []
+        if self.thread:
+            self.stop.set()
+            self.thread.join(timeout=5)
+            return
         if self.p:
             self.p.terminate()
             try:
@@ -120,23 +208,22 @@ class Clocks:
             except subprocess.TimeoutExpired:
                 self.p.kill()
                 out, _ = self.p.communicate()
-            self.lines = [l for l in out.splitlines() if l.strip()]
+            for l in out.splitlines():
+                f = [x.strip() for x in l.split(",")]
+                try:
+                    sm, mx = float(f[1]), float(f[2])
+                except (ValueError, IndexError):
+                    continue
+                self.samples.append((sm, mx, {n for n, v in zip(self.NAMES, f[5:9])
+                                              if v.lower().startswith("active")}))
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in getattr(self, "lines", []):
-            f = [x.strip() for x in l.split(",")]
-            try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
-            except (ValueError, IndexError):
-                continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
+        sm = [x[0] for x in self.samples]
+        mx = [x[1] for x in self.samples]
+        reasons = set().union(*[x[2] for x in self.samples]) if self.samples else set()
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons), "samples": len(sm)}
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons), "samples": len(sm),
+                "source": "nvml" if self.thread else "nvidia-smi"}
 
 
 def max_over_ranks(value, dist=None, device="cpu"):
@@ -150,16 +237,26 @@ def max_over_ranks(value, dist=None, device="cpu"):
 
 
 def run_reference(args, rank, world):
+    """The oracle on all host cores: nproc concurrent single-thread processes, each running the
+    warm-up and then args.steps LSRK steps on its own 2x2x80-cell sample of the workload (timed
+    steps starting at a common time); value = all their element-stages / span."""
     if rank != 0:
         return
     n = 2
-    rate, ndof, secs = oracle_rate(n, args.steps, args.warmup)
+    cores = os.cpu_count() or 1
+    res = _oracle_children_warm(cores, n, args.steps, args.warmup)
+    span = max(r[4] for r in res) - min(r[3] for r in res)
+    ndof = res[0][1]
+    rate = sum(r[1] * 5 * args.steps for r in res) / span / 1e9
+    sample = (f"{cores} concurrent single-thread oracle processes, each {args.steps} LSRK steps (after "
+              f"{args.warmup} warm-up steps) on its own {n}x{n}x80-cell sample ({ndof} DOFs, N={ORDER}); FP64 numpy")
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": METRIC, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * span / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(64, ORDER, {"sample": f"{n}x{n}x80 cells ({ndof} DOFs)"}),
-            "cpu_baseline": {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
-                             "sample": f"{n}x{n}x80-cell sample ({ndof} DOFs), {args.steps} LSRK steps"},
+            "data": "synthetic",
+            "config": workload_config(64, ORDER, {"sample": f"{cores} x {n}x{n}x80 cells ({ndof} DOFs each)"}),
+            "cpu_baseline": {"value": rate, "unit": METRIC, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+                             "nproc": cores, "sample": sample},
             "e2e": {"value": rate, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -167,21 +264,37 @@ def run_reference(args, rank, world):
 HEX_MRC_DRAM_BYTES_PER_ELEMENT = 969227776 / 73728   # 550,391,040 read + 418,836,736 written
 
 
-def hex_alg_bytes(N):
-    """Algorithmic bytes of one hex element per launch of each kernel mode.
+def alg_bytes(t, N):
+    """Algorithmic bytes of one element of type t (0 hex, 1 wedge, 2 pyramid, 3 tet) per launch
+    of each kernel mode, for the data layout the kernels use: 16 B per node for each state-sized
+    array moved (4 FP32 fields), 8 B per face-flux point for each trace set moved (p and u.n),
+    plus the element's geometry, face data and side data (neighbour, frame code, tau: 12 B per
+    face) and c^2.
 
     stage: fused LSRK stage (q, res read and written; traces read and written)
     trace: trace-only launch (q read, traces written)
     mrc:   fused multi-rate coarse step (q, two history slots read; rhs, q written; traces read,
            half-step and full-step traces written)
     mrf:   fused multi-rate fine substep (as mrc with one trace set written)
-    """
-    NP, NQ = (N + 1) ** 3, (N + 1) ** 2
-    side = 96 + 6 * 12 + 4                                      # trilinear geometry, per-face side data, c2
-    st = 4 * NP * 4                                             # one state-sized array of one element
-    tr = 6 * NQ * 8                                             # one trace set (p, u.n) of one element
-    return {"stage": 4 * st + 2 * tr + side, "trace": st + tr + side - 4,
-            "mrc": 5 * st + 3 * tr + side, "mrf": 5 * st + 2 * tr + side}
+
+    Geometry: hex 21 trilinear coefficients (96 B with padding; metric terms and normals are
+    recomputed); wedge G and grad J / (2J) at its (N+1)^3 cubature points, (n, w J^s / sqrt J) and
+    1 / sqrt J at its 5 (N+1)^2 face points; pyramid G, J at its semi-nodal points, (n, J^s) once
+    per triangle face and (n, w J^s) at the base's points; tet G, J (12 floats) and (n, J^s) once
+    per face.  Face-flux points: quad faces (N+1)^2 GL points, tet and pyramid triangle faces their
+    (N+1)(N+2)/2 lattice nodes, wedge triangle faces (N+1)^2 quadrature points."""
+    n1 = N + 1
+    NQ, NFN = n1 * n1, n1 * (N + 2) // 2
+    NP = [n1 ** 3, n1 * n1 * (N + 2) // 2, n1 * (N + 2) * (2 * N + 3) // 6, n1 * (N + 2) * (N + 3) // 6][t]
+    nf = [6, 5, 5, 4][t]
+    nfx = [6 * NQ, 5 * NQ, 4 * NFN + NQ, 4 * NFN][t]
+    geo = [96, n1 ** 3 * 48 + 5 * NQ * 16 + 5 * NQ * 4, NP * 40 + 4 * 16 + NQ * 16, 48 + 4 * 16][t]
+    side = nf * 12
+    st = 16 * NP
+    tr = 8 * nfx
+    trace_geo = [96, 5 * NQ * 4, 0, 0][t]
+    return {"stage": 4 * st + 2 * tr + geo + side + 4, "trace": st + tr + trace_geo + side,
+            "mrc": 5 * st + 3 * tr + geo + side + 4, "mrf": 5 * st + 2 * tr + geo + side + 4}
 
 
 def timed_run(g, torch, stream, steps, dt, barrier):
@@ -439,7 +552,9 @@ def main():
         pass
     hbm = float(peaks.get("hbm_gbs", 6400.0))
     K_hex = mesh.nelem[0]
-    hb = hex_alg_bytes(ORDER)
+    ab = [alg_bytes(t, ORDER) for t in range(4)]
+    hb = ab[0]
+    TYPES = ["hex", "wedge", "pyramid", "tet"]
 
     def barrier():
         if dist:
@@ -459,12 +574,19 @@ def main():
     ms1, kms1, l1, clk1 = timed_run(g1, torch, stream, args.steps, dt, barrier)
     ms1 = max_ms(ms1)
     n_stage = 5 * args.steps
-    hex_bytes1 = K_hex * (hb["stage"] * n_stage + hb["trace"] * (l1[0] - n_stage))
+    # per type: n_stage fused stage launches and the trace launch of the dg_step call
+    tb1 = [mesh.nelem[t] * (ab[t]["stage"] * n_stage + ab[t]["trace"] * (l1[t] - n_stage)) if l1[t] else 0
+           for t in range(4)]
+    hex_bytes1 = tb1[0]
     ach1 = hex_bytes1 / (kms1[0] / 1e3) / 1e9
+    step1 = sum(tb1) / (ms1 / 1e3) / 1e9
     single = {"value": ndof * 5 * args.steps * world / (ms1 / 1e3) / 1e9, "unit": METRIC,
               "ms_per_step": ms1 / args.steps, "integrator": "LSRK(5,4), 5 stages per step",
-              "kernel_ms": dict(zip(["hex", "wedge", "pyramid", "tet"], kms1)),
+              "kernel_ms": dict(zip(TYPES, kms1)),
+              "kernel_gbs": {n: (b / (k / 1e3) / 1e9 if k > 0 else None) for n, b, k in zip(TYPES, tb1, kms1)},
               "hex_stage_kernel": {"achieved": ach1, "peak": hbm, "unit": "GB/s", "frac": ach1 / hbm},
+              "step_roofline": {"bytes_per_step": sum(tb1) / args.steps, "achieved": step1, "peak": hbm,
+                                "unit": "GB/s", "frac": step1 / hbm},
               "gpu_launches": int(sum(l1))}
     del g1
     torch.cuda.synchronize()
@@ -486,8 +608,12 @@ def main():
     value = stage_units / (ms / 1e3) / 1e9
     # hex kernels: one trace launch per dg_step call, then per coarse step the fused coarse
     # step of the coarse hexes and two fused substeps of the fine hexes
-    hex_bytes = K_hex * hb["trace"] + args.steps * ((K_hex - fine[0]) * hb["mrc"] + 2 * fine[0] * hb["mrf"])
+    tb = [mesh.nelem[t] * ab[t]["trace"] + args.steps * ((mesh.nelem[t] - fine[t]) * ab[t]["mrc"]
+                                                         + 2 * fine[t] * ab[t]["mrf"]) for t in range(4)]
+    hex_bytes = tb[0]
     achieved = hex_bytes / (kms[0] / 1e3) / 1e9
+    # whole step: the algorithmic bytes of every kernel of the timed steps over the timed region
+    step_gbs = sum(tb) / (ms / 1e3) / 1e9
     # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the TMA-staged
     # hexw_kernel<4,MRC>, measured with ncu on the 32x32x80-cell mesh (73,728 hexahedra) and
     # scaled by the elements of one full-size launch
@@ -559,8 +685,13 @@ def main():
                     "h_fine": h, "parallelism": "replicas" if world > 1 else "single GPU"}),
                 "roofline": {"bound": "hbm", "kernel": "hexw_kernel<4,MRC> (fused multi-rate coarse step)",
                              "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                             "traffic": traffic, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
-                "kernel_ms": dict(zip(["hex", "wedge", "pyramid", "tet"], kms)),
+                             "traffic": traffic, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                             "step": {"bytes_per_step": sum(tb) / args.steps, "achieved": step_gbs, "peak": hbm,
+                                      "unit": "GB/s", "frac": step_gbs / hbm,
+                                      "note": "algorithmic bytes of all kernels of the timed steps (every type "
+                                              "and mode, alg_bytes) / ms_per_step"}},
+                "kernel_ms": dict(zip(TYPES, kms)),
+                "kernel_gbs": {n: (b / (k / 1e3) / 1e9 if k > 0 else None) for n, b, k in zip(TYPES, tb, kms)},
                 "gpu_launches": int(sum(launches)) + 2 * 4 * args.steps,
                 "single_rate": single, "sem_hex": sem, "e2e": e2e, "clocks": clk,
                 "energy": {"before": E_before, "after": E_after, "rel_change": (E_after - E_before) / E_before,

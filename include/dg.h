@@ -137,18 +137,21 @@ dg_status dg_state_ptr(dg_mesh *mesh, float **q_dev);
  * (NULL = the mesh's state).  Synchronises. */
 dg_status dg_energy(dg_mesh *mesh, const float *q_dev, double *E);
 
-/* dg_energy for callers that cannot allocate device memory while they run
- * (inside a CUDA stream capture, in real-time loops that cannot take allocator
- * latency, or under a framework that has reserved all device memory).  No
- * counterpart in the paper.  Same result as dg_energy (summed in a fixed order,
- * so bitwise reproducible); allocates nothing: the per-element partial sums live
- * in a static device array of 2^20 + 1 doubles (8 MiB) that every GPU loading
- * libdg holds until exit.  Meshes with more than 2^20 elements are rejected
- * with DG_EINVAL.  The first call on a device looks up that array's address
- * (cudaGetSymbolAddress) with the mesh's device current; make that first call
- * before any stream capture.  The array is shared by all calls and keeps the
- * last call's contents; calls that overlap on the GPU race on it.
- * Synchronises. */
+/* dg_energy for callers that cannot allocate device memory while they run:
+ * real-time loops that cannot take the latency of cudaMalloc (which may
+ * synchronise the device) and frameworks that have reserved all device memory
+ * for their own pool.  No counterpart in the paper.  Equal to dg_energy within
+ * FP32 rounding (the per-node terms are formed in FP64 here, in FP32 there;
+ * the tests use 1e-6 relative); repeated calls on the same state return
+ * bitwise-equal results (fixed summation order).  Allocates nothing: the
+ * per-element partial sums live in a static device array of 2^20 + 1 doubles
+ * (8 MiB) that every GPU loading libdg holds until exit.  Meshes with more
+ * than 2^20 elements are rejected with DG_EINVAL.  The first call on a device
+ * looks up that array's address (cudaGetSymbolAddress) with the mesh's device
+ * current.  The array is shared by all calls and keeps the last call's
+ * contents; calls that overlap on the GPU race on it.  Synchronises.  Errors
+ * as dg_energy: DG_ETIMEOUT for a timed-out device wait, DG_ENONFINITE for a
+ * non-finite energy, DG_ECUDA with dg_last_error() set. */
 dg_status dg_energy_noalloc(dg_mesh *mesh, const float *q_dev, double *E);
 
 /* Per-type kernel timing.  ms and launches (4 entries each, hex, wedge,

@@ -43,6 +43,8 @@ dg_status device_flags(const dg_mesh* m) {
 
 void dg_set_last_error(const std::string& msg) { g_err = msg; }
 
+dg_status dg_device_flags(const dg_mesh* m) { return device_flags(m); }
+
 extern "C" {
 
 const char* dg_status_string(dg_status s) {

@@ -147,6 +147,9 @@ cudaError_t upload_hex_constants(int N, bool sem, const float* hc, int count);
 
 // Message returned by dg_last_error() on this thread (api.cpp).
 void dg_set_last_error(const std::string& msg);
+// After a synchronisation: DG_ETIMEOUT (and the word cleared) if a bounded device wait timed out
+// since the last report, DG_ECUDA if the word cannot be read, else DG_OK (api.cpp).
+dg_status dg_device_flags(const dg_mesh* m);
 
 // Carpenter & Kennedy (1994) LSRK(5,4) coefficients (api.cpp).
 extern const double RK_A[5];

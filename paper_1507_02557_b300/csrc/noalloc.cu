@@ -1,20 +1,21 @@
 // dg_energy_noalloc: the discrete energy without any device allocation.
 //
-// For callers that must not allocate device memory while they run: code inside a
-// CUDA stream capture (cudaMalloc is not permitted there), real-time loops that
-// cannot tolerate allocator latency, or frameworks whose device memory is fully
-// reserved by their own pool.  The per-element partial sums live in a file-scope
-// static device array instead of the mesh's accumulator, and are reduced in a
-// fixed order (so the result is also bitwise reproducible).
+// For callers that must not allocate device memory while they run: real-time loops that cannot
+// take the latency of cudaMalloc (it may synchronise the device) and frameworks that have
+// reserved all device memory for their own pool, so that a cudaMalloc of the library would fail
+// or evict their data.  The per-element partial sums live in a file-scope static device array
+// instead of the mesh's accumulator, and are reduced in a fixed order, so repeated calls on the
+// same state return bitwise-equal results.
 //
-// The static array (DG_NOALLOC_MAX_ELEMS + 1 doubles, 8 MiB) is held by every GPU
-// that loads libdg until the process exits.  Its device address is looked up with
-// cudaGetSymbolAddress once per device, on the first call made with that device
-// current; that first call should therefore come before any stream capture.  All
-// calls share the array and it keeps the last call's contents: calls whose work
-// overlaps on the GPU (different streams, meshes or host threads) race on it.
+// The static array (DG_NOALLOC_MAX_ELEMS + 1 doubles, 8 MiB) is held by every GPU that loads
+// libdg until the process exits.  Its device address is looked up with cudaGetSymbolAddress once
+// per device, on the first call made with that device current.  All calls share the array and
+// it keeps the last call's contents (every call overwrites the entries it sums, so nothing needs
+// clearing): calls whose work overlaps on the GPU (different streams, meshes or host threads)
+// race on it.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <mutex>
 #include <string>
 
@@ -152,14 +153,25 @@ extern "C" dg_status dg_energy_noalloc(dg_mesh* m, const float* q, double* E) {
     case 5: launch_parts<5>(m, q, part); break;
     case 6: launch_parts<6>(m, q, part); break;
     case 7: launch_parts<7>(m, q, part); break;
-    default: return DG_ENOTSUP;
+    default:
+      dg_set_last_error("dg_energy_noalloc: N must be in 1..7");
+      return DG_ENOTSUP;
   }
   ordered_sum<<<1, 1024, 0, m->stream>>>(part, nel);
   e = cudaGetLastError();
-  if (e != cudaSuccess) return DG_ECUDA;
-  e = cudaMemcpyAsync(E, part + DG_NOALLOC_MAX_ELEMS, sizeof(double), cudaMemcpyDeviceToHost, m->stream);
-  if (e != cudaSuccess) return DG_ECUDA;
-  e = cudaStreamSynchronize(m->stream);
-  if (e != cudaSuccess) return DG_ECUDA;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(E, part + DG_NOALLOC_MAX_ELEMS, sizeof(double), cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) {
+    dg_set_last_error(std::string("dg_energy_noalloc: ") + cudaGetErrorString(e));
+    return DG_ECUDA;
+  }
+  // the same reports as dg_energy: a timed-out device wait, then a non-finite energy
+  const dg_status st = dg_device_flags(m);
+  if (st != DG_OK) return st;
+  if (!std::isfinite(*E)) {
+    dg_set_last_error("dg_energy_noalloc: the energy is not finite");
+    return DG_ENONFINITE;
+  }
   return DG_OK;
 }

@@ -54,8 +54,8 @@ MESHES = {
 @pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("name", ["hybrid", "cjump", "ragged", "inverted"])
 def test_rhs_matches_oracle(lib, name, N):
-    if N >= 5 and name != "hybrid":
-        pytest.skip("high N on one mesh only")
+    """Every mesh at every order: the c-jump and both-transition meshes reach the N >= 5 kernel
+    instantiations with wave-speed jumps and the inverted transition layer."""
     m = MESHES[name]()
     for ts in (1.0, 0.0):
         o = DGOracle(m, N, tau_scale=ts)
@@ -278,3 +278,52 @@ def test_sem_steps_match_oracle(lib, N):
     for _ in range(3):
         q, hist = mr.step(q, hist, h)
     assert rel(got, q) < TOL, per_type_rel(o, got, q)
+
+
+def bench_slab(ncol=4):
+    """The elements of the 64x64x80 throughput mesh (layers H34 W2 H36 T K4 U H2, c = 1.0 / 1.5 by
+    layer parity, seed 0) whose cells lie in the first ncol x ncol columns: the same element shapes,
+    wave speeds and time-step levels as the timed workload; the cut faces become walls."""
+    from paper_1507_02557_b300.inputs import HybridMesh, scale_mesh
+    full = scale_mesh()
+    lim = -1.0 + ncol * 2.0 / 64
+    keep, conn = [], []
+    for t in range(4):
+        cen = full.xyz[full.conn[t]].mean(axis=1)
+        k = (cen[:, 0] < lim) & (cen[:, 1] < lim)
+        keep.append(k)
+        conn.append(full.conn[t][k])
+    used = np.unique(np.concatenate([c.ravel() for c in conn]))
+    remap = np.full(len(full.xyz), -1, np.int64)
+    remap[used] = np.arange(len(used))
+    return HybridMesh(xyz=full.xyz[used], conn=[remap[c].astype(np.int32) for c in conn],
+                      c2=[full.c2[t][keep[t]] for t in range(4)],
+                      layer=[full.layer[t][keep[t]] for t in range(4)], layers=full.layers)
+
+
+def test_multirate_on_the_throughput_workload_slab(lib):
+    """The configuration the throughput benchmark times (N = 4, two levels, fused coarse / fine
+    kernels, TMA-staged hexahedra, tensor-core tets, element types on their own streams) on a
+    4x4-column slab of its mesh: start-up + 3 coarse MRAB3 steps against the oracle, overall and
+    per element type (Sec. 2.4 reading)."""
+    from oracle.constants import trace_constant
+    from oracle.dg import MRAB3, mr_levels
+    m, N = bench_slab(), 4
+    o = DGOracle(m, N)
+    lev, dmin = mr_levels(o, [trace_constant(t, N) for t in range(4)], 2)
+    g = lib.Mesh(m, N, nlevels=2)
+    assert g.level_type_counts(2) == [int(np.sum(l == 2)) for l in lev]
+    fine = g.level_type_counts(2)
+    assert fine[2] > 0 and fine[3] > 0          # fine pyramids and tets, as at scale
+    h = g.timestep()
+    assert abs(h - dmin) < 1e-12 * dmin
+    q0 = random_state(o.ndof, 21).astype(np.float32)
+    g.set_state(q0, on_device=False)
+    g.step(3, h)
+    got = g.get_state(np.zeros_like(q0), on_device=False).astype(np.float64)
+    mr = MRAB3(o, lev)
+    q, hist = mr.start(q0.astype(np.float64), h)
+    for _ in range(3):
+        q, hist = mr.step(q, hist, h)
+    errs = per_type_rel(o, got, q)
+    assert rel(got, q) < TOL and max(errs) < TOL, errs
