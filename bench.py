@@ -22,7 +22,9 @@ mesh after mesh through dg_step and once through one dg_batch (a captured CUDA g
 branch per mesh); also the subset of the meshes with n <= 12.  And ("differentiation"): 400 LSRK
 steps on a 32x32x40-cell mesh at N = 4 with a Ricker point source and 64 receivers, the receiver
 misfit's gradient w.r.t. c^2 and the source amplitude through the checkpointed adjoint, and
-central differences along 20 random c^2 directions.  And ("high_order"): the throughput mesh at N = 5 and N = 7, single-rate LSRK.
+central differences along 20 random c^2 directions.  And ("high_order"): the throughput mesh at
+N = 5 and N = 7, single-rate LSRK, with the tet and pyramid volume products in FP32 and on the
+tensor cores in split BF16 / FP16, and the modes' errors against the oracle and the exact mode.
 
 Under torchrun (N > 1) every rank advances its own replica of the mesh (no
 exchange): value = sum over ranks, time = max over ranks ("replicas only").
@@ -142,7 +144,7 @@ def cpu_baseline(n1=4, steps1=3, n_all=2, steps_all=3):
 class Clocks:
     """SM clock and throttle-reason sampling during the timed region: NVML queries (read-only) from
     a thread every 5 ms, so that even a region of a few tens of milliseconds gets many samples;
-    nvidia-smi at its 100 ms period if NVML is unavailable."""
+    nvidia-smi every 20 ms if NVML is unavailable."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -186,11 +188,12 @@ class Clocks:
             self.thread = threading.Thread(target=self._poll, args=(nv, h), daemon=True)
             self.thread.start()
             return self
-        except Exception:
+        except Exception as e:   # fall back to nvidia-smi, and say why
             self.thread = None
+            self.nvml_error = repr(e)[:200]
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                       "--format=csv,noheader,nounits", "-lms", "20"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
@@ -223,7 +226,8 @@ class Clocks:
         reasons = set().union(*[x[2] for x in self.samples]) if self.samples else set()
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons), "samples": len(sm),
-                "source": "nvml" if self.thread else "nvidia-smi"}
+                "source": "nvml" if self.thread else "nvidia-smi",
+                **({"nvml_error": self.nvml_error} if getattr(self, "nvml_error", None) else {})}
 
 
 def max_over_ranks(value, dist=None, device="cpu"):
@@ -374,24 +378,67 @@ def batch_run(dg, torch, stream, barrier, world, steps=6):
     return out
 
 
+PREC_NAMES = {0: "fp32", 1: "bf16x3", 2: "fp16x3"}
+
+
 def high_order_run(dg, torch, stream, barrier, world, mesh, max_ms, steps=5):
-    """The throughput mesh at N = 5 and N = 7 (75.9M / 177.8M DOFs), single-rate LSRK(5,4):
-    GDOF-stage/s and the kernel time per element type."""
+    """The throughput mesh at N = 5 and N = 7 (75.9M / 177.8M DOFs), single-rate LSRK(5,4), with
+    the tet and pyramid volume products in FP32 on the CUDA cores (precision 0) and on the tensor
+    cores in split BF16 / FP16 (precision 1, 2): GDOF-stage/s and the kernel time per element type."""
     from paper_1507_02557_b300.inputs import random_state
     out = {}
     for N in (5, 7):
-        g = dg.Mesh(mesh, N, stream=stream.cuda_stream)
-        g.set_state((1e-3 * random_state(g.ndof, 11)).astype(np.float32), on_device=False)
-        dt = g.timestep()
-        g.step(3, dt)
-        ms, kms, _, _ = timed_run(g, torch, stream, steps, dt, barrier)
-        ms = max_ms(ms)
-        out["N%d" % N] = {"ndof": g.ndof, "value": g.ndof * 5 * steps * world / (ms / 1e3) / 1e9,
-                          "unit": METRIC, "ms_per_step": ms / steps,
-                          "kernel_ms_per_step": {k: v / steps for k, v in
-                                                 zip(["hex", "wedge", "pyramid", "tet"], kms)}}
-        del g
-        torch.cuda.synchronize()
+        res = {}
+        for prec in (0, 1, 2):
+            g = dg.Mesh(mesh, N, stream=stream.cuda_stream, precision=prec)
+            g.set_state((1e-3 * random_state(g.ndof, 11)).astype(np.float32), on_device=False)
+            dt = g.timestep()
+            g.step(3, dt)
+            ms, kms, _, _ = timed_run(g, torch, stream, steps, dt, barrier)
+            ms = max_ms(ms)
+            res[PREC_NAMES[prec]] = {"value": g.ndof * 5 * steps * world / (ms / 1e3) / 1e9, "unit": METRIC,
+                                     "ms_per_step": ms / steps,
+                                     "kernel_ms_per_step": {k: v / steps for k, v in
+                                                            zip(["hex", "wedge", "pyramid", "tet"], kms)}}
+            ndof = g.ndof
+            del g
+            torch.cuda.synchronize()
+        res["ndof"] = ndof
+        for k in ("bf16x3", "fp16x3"):
+            res[k]["over_fp32"] = res[k]["value"] / res["fp32"]["value"]
+        out["N%d" % N] = res
+    return out
+
+
+def precision_accuracy(dg, torch):
+    """Errors of the three precision modes on the 4x4x5-cell hybrid mesh (c = 1) at N = 5 and 7:
+    LSRK(5,4) steps from the oracle's projection of the standing mode to t = 0.01; relative L2
+    difference from the FP64 oracle's state after the same steps, and the L2 error against the
+    exact standing mode (the oracle's and each mode's)."""
+    from oracle.dg import DGOracle, standing_mode
+    from paper_1507_02557_b300.inputs import small_hybrid_mesh
+    m = small_hybrid_mesh()
+    out = {"workload": "4x4x5 cells HWHTK (c = 1), standing mode, LSRK(5,4) to t = 0.01", "T": 0.01}
+    for N in (5, 7):
+        o = DGOracle(m, N)
+        q0 = o.project(standing_mode, 0.0)
+        g = dg.Mesh(m, N)
+        n = int(np.ceil(0.01 / g.timestep()))
+        dt = 0.01 / n
+        q = q0.copy()
+        for _ in range(n):
+            q = o.lsrk_step(q, dt)
+        res = {"steps": n, "exact_l2": {"oracle_fp64": o.l2_error(q, standing_mode, 0.01)}, "oracle_rel_l2": {}}
+        for prec in (0, 1, 2):
+            g = dg.Mesh(m, N, precision=prec)
+            g.set_state(q0.astype(np.float32), on_device=False)
+            g.step(n, dt)
+            got = g.get_state(np.zeros(q0.shape, np.float32), on_device=False).astype(np.float64)
+            res["oracle_rel_l2"][PREC_NAMES[prec]] = float(np.linalg.norm(got - q) / np.linalg.norm(q))
+            res["exact_l2"][PREC_NAMES[prec]] = o.l2_error(got, standing_mode, 0.01)
+        for k in ("bf16x3", "fp16x3"):
+            res[k + "_error_over_fp32"] = res["exact_l2"][k] / res["exact_l2"]["fp32"]
+        out["N%d" % N] = res
     return out
 
 
@@ -674,6 +721,8 @@ def main():
     batch = None if args.no_batch else batch_run(dg, torch, stream, barrier, world)
     diff = None if args.no_extras else differentiation_run(dg, torch, stream, barrier, world)
     high = None if args.no_extras else high_order_run(dg, torch, stream, barrier, world, mesh, max_ms)
+    if high and rank == 0:
+        high["accuracy"] = precision_accuracy(dg, torch)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,

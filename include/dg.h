@@ -77,7 +77,13 @@ typedef struct {
   double tau_scale;        /* 1 = upwind, 0 = central flux */
   int nlevels;             /* 1 = single-rate LSRK(5,4); 2 = two-level multi-rate AB3 */
   double cfl;              /* C of Eq. (dtK); <= 0 selects 0.5 */
-  int precision;           /* 0 = FP32 (only value built) */
+  int precision;           /* volume products of tets and pyramids: 0 = FP32 (CUDA cores; tets at
+                              N <= 4 on the tensor cores in TF32 x 3); 1 = BF16 x 3, 2 = FP16 x 3:
+                              16-bit hi + lo split operands on the tensor cores, FP32 accumulation
+                              (about 2^-17 / 2^-22 relative per product); hexahedra, wedges and all
+                              face terms stay FP32.  1, 2 apply on meshes with the lattice face
+                              exchange (no wedge triangle face against a tet or pyramid); the
+                              adjoint refuses them (DG_ENOTSUP) */
 } dg_mesh_desc;
 
 /* Build the mesh on the current CUDA device: face matching, geometric factors,

@@ -70,8 +70,8 @@ dg_status dg_mesh_create(const dg_mesh_desc* d, void* stream, dg_mesh** out) {
     g_err = "N must be in 1..7";
     return DG_ENOTSUP;
   }
-  if ((d->hex_basis != 0 && d->hex_basis != 1) || d->nlevels > 2 || d->precision != 0) {
-    g_err = "only GL hexahedra, one or two time-step levels and FP32 are built";
+  if ((d->hex_basis != 0 && d->hex_basis != 1) || d->nlevels > 2 || d->precision < 0 || d->precision > 2) {
+    g_err = "hex_basis 0 / 1, one or two time-step levels and precision 0 / 1 / 2 are built";
     return DG_ENOTSUP;
   }
   if (d->nverts <= 0 || !d->xyz) return DG_EINVAL;
@@ -437,8 +437,8 @@ dg_status dg_adjoint_step(dg_mesh* m, int nsteps, double dt, double t0, float* l
     g_err = "receiver residuals need receivers (dg_set_receivers)";
     return DG_EINVAL;
   }
-  if (m->nlevels != 1 || m->hex_sem || m->pyr_form != 0) {
-    g_err = "adjoint built for single-rate LSRK with GL hexahedra and skew-form pyramids";
+  if (m->nlevels != 1 || m->hex_sem || m->pyr_form != 0 || m->precision != 0) {
+    g_err = "adjoint built for single-rate LSRK with GL hexahedra, skew-form pyramids and FP32 products";
     return DG_ENOTSUP;
   }
   if (!(dt > 0)) dt = m->dt_min;

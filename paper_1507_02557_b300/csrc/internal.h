@@ -45,6 +45,24 @@ struct TmaArr {
 };
 bool tma_map_1d(TmaArr& t, const float* base, int64_t n, int box);   // kernels.cu
 
+// Tensor-core volume terms (precision 1 = BF16 x 3, 2 = FP16 x 3) of tets ([0]) and pyramids ([1]):
+// per element X = [W_r | W_s | W_t | p] (4 blocks of npk 16-bit values, hi and lo parts, scaled by
+// a power of two per row; xis = 1 / scale), Y = B X in FP32 (4 blocks of npp), B = the fixed block
+// operator (FP32 copy and its scaled hi / lo parts; bis = 1 / its scale).  Layout in kernels_prec.cu.
+struct PrecDev {
+  unsigned short *xh = nullptr, *xl = nullptr, *bh = nullptr, *bl = nullptr;
+  float* xis = nullptr;
+  float* y = nullptr;
+  float* b32 = nullptr;
+  int npk = 0, npp = 0;
+  float bis = 1.f;
+};
+// 2D TMA descriptors of X (hi, lo: boxes of 8 values x 128 rows) and B (hi, lo: 8 x npp)
+struct PrecMaps {
+  CUtensorMap xh, xl, bh, bl;
+};
+bool prec_maps(PrecMaps& M, const PrecDev& P, int64_t rows);   // kernels.cu
+
 // A selection of elements per type (multi-rate level): list = NULL means 0..count-1.
 struct Sel {
   const int* list[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -92,6 +110,11 @@ struct dg_mesh {
   bool type_streams = false;
   // kernel choices (dg_autotune): TMA staging of the fused N = 4 hex kernels, tensor-core tets
   bool use_hex_tma = true, use_tet_tc = true;
+  // precision of the tet and pyramid volume products: 0 = FP32 (SIMT, or TF32 x 3 tensor-core tets
+  // for N <= 4), 1 = BF16 x 3, 2 = FP16 x 3 on the tensor cores (kernels_prec.cu)
+  int precision = 0;
+  dgk::PrecDev prec[2];
+  dgk::PrecMaps prec_maps[2];
   cudaStream_t tstream[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t tev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   // adjoint (adjoint.cu): host data kept by the setup, device copies made on first use
@@ -143,6 +166,12 @@ cudaError_t launch_ab(dg_mesh* m, const Sel& sel, const float* qin, float* qout,
                       const float* r1, const float* r2, float h0, float h1, float h2);
 // Hex constants (1D D, V^f, GL weights and nodes) of order N <= 4 into constant memory.
 cudaError_t upload_hex_constants(int N, bool sem, const float* hc, int count);
+struct Args;
+// Tensor-core volume terms of type t (DG_TET / DG_PYR) for the elements of A (precision > 0): pack
+// X, Y = B X; sets A.vol, A.vol_np for the type's warp kernel (kernels_prec.cu).
+cudaError_t launch_prec_volume(dg_mesh* m, int t, Args& A, cudaStream_t s);
+// Scaled 16-bit hi / lo parts of the FP32 operator b into P.bh, P.bl (kernels_prec.cu).
+cudaError_t prec_split_operator(PrecDev& P, const float* b, bool bf, cudaStream_t s);
 }  // namespace dgk
 
 // Message returned by dg_last_error() on this thread (api.cpp).

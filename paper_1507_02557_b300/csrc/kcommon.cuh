@@ -55,6 +55,11 @@ struct Args {
   const float* h2;
   float ab0, ab1, ab2, pr0, pr1, pr2;
   float* tout2;
+  // tensor-core volume terms (precision > 0, tets and pyramids): row li of vol holds, for the
+  // element of list index li, [sum_a D^a w_a | D^r p | D^s p | D^t p] (pyramid: the first block
+  // with the transposes (D^a)^T), each block vol_np floats wide; NULL = computed in the kernel
+  const float* vol;
+  int vol_np;
 };
 
 __device__ __forceinline__ void flux(bool wall, float pm, float unm, float P, float UN, float tp,

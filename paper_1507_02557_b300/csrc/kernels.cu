@@ -967,6 +967,24 @@ bool tma_map_1d(TmaArr& t, const float* base, int64_t n, int box) {
   return t.ok;
 }
 
+// 2D descriptors of the tensor-core volume operands: X [rows][4 npk] and B [4 npp][4 npk], 16-bit,
+// copied in boxes of 8 values (16 bytes: one K-major core-matrix row) x 128 (X) or npp (B) rows
+bool prec_maps(PrecMaps& M, const PrecDev& P, int64_t rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc || rows <= 0 || rows >= (1LL << 31)) return false;
+  auto map2 = [&](CUtensorMap* m, const void* base, int64_t nrow, int box_rows) {
+    const cuuint64_t dim[2] = {static_cast<cuuint64_t>(4 * P.npk), static_cast<cuuint64_t>(nrow)};
+    const cuuint64_t stride[1] = {static_cast<cuuint64_t>(4 * P.npk * 2)};
+    const cuuint32_t boxd[2] = {8, static_cast<cuuint32_t>(box_rows)};
+    const cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(base), dim, stride, boxd, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  return map2(&M.xh, P.xh, rows, 128) && map2(&M.xl, P.xl, rows, 128) && map2(&M.bh, P.bh, 4 * P.npp, P.npp) &&
+         map2(&M.bl, P.bl, 4 * P.npp, P.npp);
+}
+
 // the registered array holding p (with p's offset in floats), or null
 static const TmaArr* tma_find(const dg_mesh* m, const float* p, long long* off) {
   for (const TmaArr& t : m->tma)
@@ -1384,8 +1402,8 @@ static void launch_hex_fast(dg_mesh* m, const Args& A, cudaStream_t s) {
 }
 
 template <int MODE>
-static void launch_type(dg_mesh* m, const Args& A, int t) {
-  if (A.K == 0) return;
+static void launch_type(dg_mesh* m, const Args& A0, int t) {
+  if (A0.K == 0) return;
   if (MODE >= MODE_MRC && m->N > 4) return;   // fused multi-rate kernels exist for N <= 4 only
   cudaStream_t s = m->stream;
   int e0 = -1;
@@ -1393,11 +1411,16 @@ static void launch_type(dg_mesh* m, const Args& A, int t) {
     e0 = ev_take(m);
     cudaEventRecord(m->ev_pool[e0], s);
   }
+  // precision > 0: the volume products of tets and pyramids on the tensor cores in split 16-bit
+  // form, then the type's warp kernel with those products as input (lattice-exchange meshes)
+  Args A = A0;
+  const bool tcv = m->precision > 0 && (t == DG_TET || t == DG_PYR) && MODE != MODE_TRACE && m->tri_lat;
+  if (tcv) launch_prec_volume(m, t, A, s);
   switch (m->N) {
 #define DG_CASE(NN)                                                   \
   case NN:                                                            \
     if (t == DG_HEX) { if (NN <= 4) launch_hex_fast<(NN <= 4 ? NN : 4), MODE>(m, A, s); else launch_hex_n<NN, (MODE > 2 ? 1 : MODE)>(A, s); } \
-    else if (DG_TET_TC && t == DG_TET && m->tri_lat && m->use_tet_tc && launch_tet_tc<MODE>(NN, A, s)) {}   \
+    else if (DG_TET_TC && !tcv && t == DG_TET && m->tri_lat && m->use_tet_tc && launch_tet_tc<MODE>(NN, A, s)) {}   \
     else if ((t == DG_WEDGE || m->tri_lat) && launch_gen2<MODE>(t, NN, A, s)) {}   \
     else if (t == DG_WEDGE) launch_gen_n<DG_WEDGE, NN, (MODE > 2 ? 1 : MODE)>(A, s);   \
     else if (t == DG_PYR) launch_gen_n<DG_PYR, NN, (MODE > 2 ? 1 : MODE)>(A, s);       \

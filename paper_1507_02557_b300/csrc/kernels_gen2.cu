@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
         float G[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) G[i] = g[i];
-        for (int n = lane; n < NP; n += 32) {
+        for (int n = lane; n < NP && !A.vol; n += 32) {
           const float4 v = q4[n];
           W4[n] = f4(G[0] * v.y + G[1] * v.z + G[2] * v.w, G[3] * v.y + G[4] * v.z + G[5] * v.w,
                      G[6] * v.y + G[7] * v.z + G[8] * v.w, v.x);
@@ -380,7 +380,16 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
           acc[r] = f4(-div, -c2 * (G[0] * a[3] + G[3] * a[4] + G[6] * a[5]),
                       -c2 * (G[1] * a[3] + G[4] * a[4] + G[7] * a[5]), -c2 * (G[2] * a[3] + G[5] * a[4] + G[8] * a[5]));
         };
-        if constexpr (C::CHUNK) {   // all rows accumulate across the block's operator chunks
+        if (A.vol) {   // products from the tensor-core pass (row li: sum_a D^a w_a, D^r p, D^s p, D^t p)
+          const float* vr = A.vol + li * 4 * (int64_t)A.vol_np;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int n = lane + 32 * r;
+            if (n >= NP) break;
+            const float a[6] = {vr[n], 0.f, 0.f, vr[A.vol_np + n], vr[2 * A.vol_np + n], vr[3 * A.vol_np + n]};
+            tet_out(r, a);
+          }
+        } else if constexpr (C::CHUNK) {   // all rows accumulate across the block's operator chunks
           float s6[R][6];
 #pragma unroll
           for (int r = 0; r < R; ++r)
@@ -416,7 +425,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
         }
       } else if (T == DG_PYR) {
         const float* geo = A.geo + e * NP * 10;
-        for (int m = lane; m < NP; m += 32) {
+        for (int m = lane; m < NP && !A.vol; m += 32) {
           const float* g = geo + m * 10;
           const float4 v = q4[m];
           const float J = g[9];
@@ -438,7 +447,16 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
           acc[r] = f4((a[0] + a[1] + a[2]) / g[9], -c2 * (g[0] * a[3] + g[3] * a[4] + g[6] * a[5]),
                       -c2 * (g[1] * a[3] + g[4] * a[4] + g[7] * a[5]), -c2 * (g[2] * a[3] + g[5] * a[4] + g[8] * a[5]));
         };
-        if constexpr (C::CHUNK) {   // all rows accumulate across the block's operator chunks
+        if (A.vol) {   // products from the tensor-core pass (row li: sum_a (D^a)^T J G u_a, D^r p, D^s p, D^t p)
+          const float* vr = A.vol + li * 4 * (int64_t)A.vol_np;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int n = lane + 32 * r;
+            if (n >= NP) break;
+            const float a[6] = {vr[n], 0.f, 0.f, vr[A.vol_np + n], vr[2 * A.vol_np + n], vr[3 * A.vol_np + n]};
+            pyr_out(r, a);
+          }
+        } else if constexpr (C::CHUNK) {   // all rows accumulate across the block's operator chunks
           float s6[R][6];
 #pragma unroll
           for (int r = 0; r < R; ++r)

@@ -491,6 +491,7 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
     m->tau_scale = d->tau_scale;
     m->cfl = d->cfl > 0 ? d->cfl : 0.5;
     m->pyr_form = d->pyr_form;
+    m->precision = d->precision;
     const bool sem = d->hex_basis == 1;   // SEM hexahedra: GLL nodes, GLL points on quad faces
     m->hex_sem = sem;
     Basis B[4];
@@ -1246,6 +1247,37 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
         td.iops2 = upload(i2, owned);
         td.nops2 = (int)o2.size();
         td.niops2 = (int)i2.size();
+        if (d->precision > 0 && (t == TET || t == PYR) && td.K > 0 && !g_host_only) {
+          // tensor-core volume products (kernels_prec.cu): the block operator B [4 npp][4 npk] from
+          // D^a[x][y] = o2[(x Np + y) 4 + a]: block 0 (sum_a D^a W_a; pyramid (D^a)^T), blocks
+          // 1..3 (D^a p)
+          dgk::PrecDev& P = m->prec[t == TET ? 0 : 1];
+          P.npk = (Np + 15) / 16 * 16;
+          P.npp = P.npk;
+          const int npk = P.npk, npp = P.npp;
+          std::vector<float> b((size_t)4 * npp * 4 * npk, 0.f);
+          float bmax = 0.f;
+          for (int n = 0; n < Np; ++n)
+            for (int mm = 0; mm < Np; ++mm)
+              for (int a = 0; a < 3; ++a) {
+                const float dnm = o2[((size_t)n * Np + mm) * 4 + a], dmn = o2[((size_t)mm * Np + n) * 4 + a];
+                b[(size_t)n * 4 * npk + a * npk + mm] = t == TET ? dnm : dmn;
+                b[(size_t)((1 + a) * npp + n) * 4 * npk + 3 * npk + mm] = dnm;
+                bmax = std::max(bmax, std::fabs(dnm));
+              }
+          P.bis = bmax > 0.f ? std::ldexp(1.f, std::ilogb(bmax) - 14) : 1.f;   // operator scaled into [2^14, 2^15)
+          const int64_t rows = (td.K + 127) / 128 * 128;
+          P.b32 = upload(b, owned);
+          P.bh = alloc_zero<unsigned short>(b.size(), owned);
+          P.bl = alloc_zero<unsigned short>(b.size(), owned);
+          P.xh = alloc_zero<unsigned short>((size_t)rows * 4 * npk, owned);
+          P.xl = alloc_zero<unsigned short>((size_t)rows * 4 * npk, owned);
+          P.xis = alloc_zero<float>((size_t)rows, owned);
+          P.y = alloc_zero<float>((size_t)rows * 4 * npp, owned);
+          if (dgk::prec_split_operator(P, P.b32, d->precision == 1, nullptr) != cudaSuccess ||
+              !dgk::prec_maps(m->prec_maps[t == TET ? 0 : 1], P, rows))
+            throw SetupError(DG_ECUDA, "tensor-core operands: operator split or TMA descriptors failed");
+        }
       }
     }
 

@@ -86,7 +86,7 @@ def _ptr(x):
     return x.ctypes.data_as(_vp)
 
 
-def _desc(mesh, N, tau_scale, pyr_form, cfl, keep, nlevels=1, hex_basis=0):
+def _desc(mesh, N, tau_scale, pyr_form, cfl, keep, nlevels=1, hex_basis=0, precision=0):
     d = Desc()
     xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
     keep.append(xyz)
@@ -100,7 +100,7 @@ def _desc(mesh, N, tau_scale, pyr_form, cfl, keep, nlevels=1, hex_basis=0):
         d.conn[t] = cn.ctypes.data_as(C.POINTER(C.c_int32))
         d.c2[t] = c2.ctypes.data_as(C.POINTER(C.c_double))
     d.N, d.hex_basis, d.pyr_form = N, hex_basis, pyr_form
-    d.tau_scale, d.nlevels, d.cfl, d.precision = tau_scale, nlevels, cfl, 0
+    d.tau_scale, d.nlevels, d.cfl, d.precision = tau_scale, nlevels, cfl, precision
     return d
 
 
@@ -121,14 +121,18 @@ def host_check(mesh, N, tau_scale=1.0, pyr_form=0, cfl=0.5, nlevels=1, levels=Fa
 class Mesh:
     """A dg_mesh on the current CUDA device (see include/dg.h)."""
 
-    def __init__(self, mesh, N, tau_scale=1.0, pyr_form=0, cfl=0.5, stream=None, nlevels=1, hex_basis=0):
+    def __init__(self, mesh, N, tau_scale=1.0, pyr_form=0, cfl=0.5, stream=None, nlevels=1, hex_basis=0,
+                 precision=0):
+        """precision: 0 = FP32 products; 1 = BF16 x 3, 2 = FP16 x 3 split products on the tensor cores
+        for the tet and pyramid volume terms."""
         keep = []
-        d = _desc(mesh, N, tau_scale, pyr_form, cfl, keep, nlevels, hex_basis)
+        d = _desc(mesh, N, tau_scale, pyr_form, cfl, keep, nlevels, hex_basis, precision)
         h = _vp()
         _check(_lib.dg_mesh_create(C.byref(d), _vp(stream or 0), C.byref(h)))
         self._h = h
         self.N = N
         self.nlevels = nlevels
+        self.precision = precision
         n = C.c_int64()
         _check(_lib.dg_ndof(h, C.byref(n)))
         self.ndof = n.value
