@@ -502,3 +502,70 @@ class MRAB3:
         out[F] = qn[F] + h * (AB3[0] * rh[F] + AB3[1] * r[F] + AB3[2] * f1[F])
         out[Cm] = q[Cm] + 2 * h * (AB3[0] * r[Cm] + AB3[1] * c1[Cm] + AB3[2] * c2[Cm])
         return out, ([r, c1], [rh, r])
+
+
+# ---------------------------------------------------------------------- multi-rate LSRK
+def lsrk_stability_coefficients():
+    """rho_0..rho_5 of R(z) = sum rho_i z^i, the amplification of LSRK(5,4) on y' = lambda y
+    (the 2N-storage recursion applied to polynomials in z)."""
+    poly = np.polynomial.polynomial
+    y, res = np.array([1.0]), np.array([0.0])
+    for a, b in zip(LSRK_A, LSRK_B):
+        res = poly.polyadd(a * res, poly.polymul([0.0, 1.0], y))
+        y = poly.polyadd(y, b * res)
+    return np.concatenate([y, np.zeros(6 - len(y))])[:6]
+
+
+class MRLSRK:
+    """Two-level multi-rate LSRK(5,4) (reading of Sec. 2.4 for a Runge-Kutta integrator), a local
+    time-stepping scheme in the manner of the LTS-RK methods of Grote, Mehlin & Mitkova (2015):
+    the coarse region's influence over a coarse step is a polynomial in time built from operator
+    powers at t_n, and the fine region is integrated by LSRK(5,4) substeps against it.
+
+    Fine step h, coarse step H = 2h, P = restriction to the fine elements' DOFs, B = M^{-1} A.
+    Per coarse step from y_n:
+      z_0 = y_n, z_j = B z_{j-1} (j = 1..4);   u_j = B (I - P) z_j (j = 0..4);
+      W(tau) = sum_j rho_{j+1} tau^{j+1} u_j, with R(z) = sum rho_i z^i the LSRK(5,4) amplification;
+      v(0) = 0, v' = B P (y_n + W(tau) + v), integrated by two LSRK(5,4) steps of h;
+      y_{n+1} = y_n + W(H) + v(H).
+    W' = sum_j (j+1) rho_{j+1} tau^j u_j agrees with the Taylor expansion of B (I - P) y(t_n + tau)
+    through tau^3, so the scheme is fourth order.  With no fine element (P = 0), v = 0 and
+    y_{n+1} = R(H B) y_n, one LSRK(5,4) step of H; with only fine elements (P = I), u_j = 0 and
+    the scheme is two LSRK(5,4) steps of h.  B P v and u_j vanish outside the fine elements and
+    the coarse elements that share a face with one.
+    """
+
+    def __init__(self, dg, level):
+        self.dg = dg
+        mask = np.zeros((4, dg.ndof), dtype=bool)
+        mv = dg.split(mask)
+        for t in range(4):
+            mv[t][:] = (level[t] == 2)[None, :, None]
+        self.fine = mask
+        self.rho = lsrk_stability_coefficients()
+
+    def step(self, y, h):
+        dg, F, rho = self.dg, self.fine, self.rho
+        H = 2.0 * h
+        z = [y]
+        for _ in range(4):
+            z.append(dg.rhs(z[-1]))
+        u = []
+        for zj in z:
+            zc = zj.copy()
+            zc[F] = 0.0
+            u.append(dg.rhs(zc))
+        W = lambda tau: sum(rho[j + 1] * tau ** (j + 1) * u[j] for j in range(5))
+
+        def fine_rhs(v, tau):
+            x = y + W(tau) + v
+            x[~F] = 0.0
+            return dg.rhs(x)
+
+        v = np.zeros_like(y)
+        for s in range(2):
+            res = np.zeros_like(y)
+            for a, b, c in zip(LSRK_A, LSRK_B, LSRK_C):
+                res = a * res + h * fine_rhs(v, (s + c) * h)
+                v = v + b * res
+        return y + W(H) + v

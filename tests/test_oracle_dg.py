@@ -230,3 +230,58 @@ def test_mrab3_on_one_level_is_single_rate_ab3(mesh, level):
         qa = qa + H * (23 * r - 16 * hist_a[0] + 5 * hist_a[1]) / 12
         hist_a = [r, hist_a[0]]
     assert np.abs(q - qa).max() < 1e-13 * np.abs(qa).max()
+
+
+def _two_level(N=2):
+    from oracle.dg import mr_levels
+    m = layered_mesh(3, 3, 5, "HWHTK", seed=3, c_of_layer=lambda k: 1.0 if k % 2 == 0 else 1.5)
+    o = DGOracle(m, N)
+    lev, dmin = mr_levels(o, [trace_constant(t, N) for t in range(4)], 2)
+    return o, lev, dmin
+
+
+@pytest.mark.parametrize("level", [1, 2])
+def test_mrlsrk_on_one_level_is_lsrk(level):
+    """Multi-rate LSRK with every element coarse is one LSRK(5,4) step of 2h (the coarse
+    polynomial integrates to R(2h B) y); with every element fine it is two LSRK(5,4) steps of h."""
+    from oracle.dg import MRLSRK
+    o, _, dmin = _two_level()
+    lev = [np.full(k, level, dtype=int) for k in o.K]
+    y = random_state(o.ndof, 12)
+    got = MRLSRK(o, lev).step(y, dmin)
+    want = o.lsrk_step(y, 2 * dmin) if level == 1 else o.lsrk_step(o.lsrk_step(y, dmin), dmin)
+    assert np.abs(got - want).max() < 1e-12 * np.abs(want).max()
+
+
+def test_mrlsrk_is_fourth_order():
+    """Two levels (fine pyramids, tets and wedges next to coarse hexahedra): halving h divides the
+    error against a small-step LSRK(5,4) reference by about 16."""
+    from oracle.dg import MRLSRK
+    o, lev, dmin = _two_level()
+    q0 = o.project(standing_mode, 0.0)
+    T = 16 * dmin
+    errs = []
+    for h in (dmin, dmin / 2):
+        mr = MRLSRK(o, lev)
+        q = q0.copy()
+        for _ in range(int(round(T / (2 * h)))):
+            q = mr.step(q, h)
+        errs.append(q)
+    ref = q0.copy()
+    for _ in range(64):
+        ref = o.lsrk_step(ref, T / 64)
+    e = [np.linalg.norm(x - ref) / np.linalg.norm(ref) for x in errs]
+    assert 12.0 < e[0] / e[1] < 22.0, e
+
+
+def test_mrlsrk_energy_nonincreasing_under_upwind():
+    """Upwind flux, two levels at the multi-rate step: the discrete energy does not grow."""
+    from oracle.dg import MRLSRK
+    o, lev, dmin = _two_level()
+    mr = MRLSRK(o, lev)
+    q = random_state(o.ndof, 3)
+    E = [o.energy(q)]
+    for _ in range(6):
+        q = mr.step(q, dmin)
+        E.append(o.energy(q))
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(E, E[1:])), E
