@@ -320,9 +320,13 @@ def timed_run(g, torch, stream, steps, dt, barrier):
     return ev0.elapsed_time(ev1), kms, launches, clk.summary()
 
 
-def batch_run(dg, torch, stream, barrier, world, steps=6):
-    """The many-mesh workload: GDOF-stage/s of per-mesh dg_step calls (eager) and of one dg_batch
-    (graph), wall clock between device synchronisations, all meshes' states resident."""
+def batch_run(dg, torch, stream, barrier, world, steps=100, eager_steps=6, cmp_steps=30):
+    """The many-mesh workload (256 meshes, 100 steps): GDOF-stage/s of per-mesh dg_step calls
+    (eager, eager_steps) and of one dg_batch graph: packed (same-order meshes merged into one
+    combined mesh per order: one launch per type and stage for the group; 100 steps, the workload's
+    count) and unpacked (a graph branch per mesh, cmp_steps), then after the per-mesh autotuner
+    (packed, cmp_steps) and the batch autotuner's pick.  Wall clock between device
+    synchronisations, all meshes' states resident."""
     from paper_1507_02557_b300.inputs import batch_mesh, batch_specs, random_state
     specs = batch_specs()
     t0 = time.perf_counter()
@@ -336,39 +340,45 @@ def batch_run(dg, torch, stream, barrier, world, steps=6):
            "steps": steps, "setup_s": setup_s, "unit": METRIC}
     for name, sel in (("all", [True] * len(specs)), ("n_le_12", [sp[0] <= 12 for sp in specs])):
         ms = [g for g, k in zip(meshes, sel) if k]
-        units = sum(g.ndof for g in ms) * 5 * steps * world
+        dof = sum(g.ndof for g in ms)
+        rate = lambda n, s: dof * 5 * n * world / s / 1e9
+        t1 = time.perf_counter()
         b = dg.Batch(ms, stream=stream.cuda_stream)
+        barrier()
+        res = {"meshes": len(ms), "dof": dof, "batch_create_s": time.perf_counter() - t1}
 
-        def eager():
+        def timed(f, n):
+            f(3 if n >= 3 else n)       # warm-up (graph capture)
+            barrier()
+            t = time.perf_counter()
+            f(n)
+            barrier()
+            return rate(n, time.perf_counter() - t)
+
+        def eager(n):
             for g in ms:
-                g.step(steps)
+                g.step(n)
 
-        def graph():
-            b.step(steps)
-
-        res = {"meshes": len(ms), "dof": sum(g.ndof for g in ms)}
-        for arm, f in (("eager", eager), ("graph", graph)):
-            f()
-            barrier()
-            t1 = time.perf_counter()
-            f()
-            barrier()
-            res[arm] = units / (time.perf_counter() - t1) / 1e9
+        res["eager"] = timed(eager, eager_steps)
+        res["graph"] = timed(b.step, steps)
+        b.set_packing(0)
+        res["graph_unpacked"] = timed(b.step, cmp_steps)
+        b.set_packing(1)
         res["graph_over_eager"] = res["graph"] / res["eager"]
+        res["packed_over_unpacked"] = res["graph"] / res["graph_unpacked"]
         res["graph_replays_captures"] = list(b.stats())
+        t1 = time.perf_counter()
+        res["batch_autotune_packed"] = b.autotune(3)
+        res["batch_autotune_s"] = time.perf_counter() - t1
         b.close()
-        # the same graph after dg_autotune picked each mesh's kernel choices
+        # the same after dg_autotune picked each mesh's kernel choices (meshes whose choices now
+        # differ land in different groups)
         t1 = time.perf_counter()
         picks = [g.autotune(2) for g in ms]
         res["autotune_s"] = time.perf_counter() - t1
         res["autotune_picks"] = {k: sum(p[k] for p in picks) for k in ms[0].CHOICES}
         b = dg.Batch(ms, stream=stream.cuda_stream)
-        graph()
-        barrier()
-        t1 = time.perf_counter()
-        graph()
-        barrier()
-        res["graph_tuned"] = units / (time.perf_counter() - t1) / 1e9
+        res["graph_tuned"] = timed(b.step, cmp_steps)
         b.close()
         for g in ms:
             g.set_choices()
@@ -538,7 +548,7 @@ def run_case(args, dg, torch, mesh):
     """--case: warm-up steps, then the timed steps (lsrk) or one adjoint window (adjoint); one JSON
     line with the wall time (not a bench value)."""
     from paper_1507_02557_b300.inputs import random_state
-    g = dg.Mesh(mesh, args.order)
+    g = dg.Mesh(mesh, args.order, precision=args.precision, nlevels=args.nlevels)
     g.set_state((1e-3 * random_state(g.ndof, 1)).astype(np.float32), on_device=False)
     dt = g.timestep()
     g.step(args.warmup, dt)
@@ -552,6 +562,7 @@ def run_case(args, dg, torch, mesh):
         g.adjoint_step(args.steps, lam, grad, dt)
     torch.cuda.synchronize()
     print(json.dumps({"case": args.case, "order": args.order, "cells": args.cells, "ndof": g.ndof,
+                      "precision": args.precision, "nlevels": args.nlevels,
                       "steps": args.steps, "wall_s": time.perf_counter() - t0}), flush=True)
 
 
@@ -569,6 +580,8 @@ def main():
                     help="run one small case only (for profiling): LSRK steps at --order, or one adjoint "
                          "window of --steps steps with the c^2 gradient, on the --cells x --cells x 80 mesh")
     ap.add_argument("--order", type=int, default=ORDER)
+    ap.add_argument("--precision", type=int, default=0, help="--case: 0 FP32, 1 BF16 x 3, 2 FP16 x 3 products")
+    ap.add_argument("--nlevels", type=int, default=1, help="--case lsrk: 1 single rate, 2 multi-rate AB3")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -699,6 +712,28 @@ def main():
                                      "h2d_bytes_per_step": 4 * ndof * 4, "d2h_bytes_per_step": 8}
     del g1
 
+    # ---- multi-rate LSRK(5,4) (integrator 1) on the same workload, beside MRAB3: per coarse step
+    # five full rhs evaluations (z_j = B^j y), five on S (u_j) and ten on S (the fine correction's
+    # stages), S = fine elements and the coarse elements next to them
+    mr_lsrk = None
+    if not args.no_extras:
+        gl = dg.Mesh(mesh, ORDER, stream=stream.cuda_stream, nlevels=2, integrator=1)
+        gl.set_state(q0, on_device=False)
+        s_count = gl.mr_s_counts()
+        ndof_s = sum(c * n for c, n in zip(s_count, npe))
+        l_steps = max(3, min(args.steps, 10))
+        gl.step(args.warmup, h)
+        ms_l, kms_l, _, _ = timed_run(gl, torch, stream, l_steps, h, barrier)
+        ms_l = max_ms(ms_l)
+        mr_lsrk = {"value": (5 * ndof + 15 * ndof_s) * l_steps * world / (ms_l / 1e3) / 1e9, "unit": METRIC,
+                   "steps": l_steps, "ms_per_coarse_step": ms_l / l_steps, "ndof_S": ndof_s,
+                   "kernel_ms": dict(zip(TYPES, kms_l)),
+                   "time_per_simulated_time_over_mrab3": (ms_l / l_steps) / (ms / args.steps),
+                   "note": "value counts the rhs element evaluations performed (5 full + 15 on S per coarse step); "
+                           "the ratio compares wall time per coarse step 2h with the MRAB3 headline"}
+        del gl
+        torch.cuda.synchronize()
+
     # ---- SEM hexahedra (GLL nodes, GLL points on quad faces): the same multi-rate workload, for
     # the cost comparison of the two hex bases (per-DOF time of the hex kernels)
     del g
@@ -742,7 +777,7 @@ def main():
                 "kernel_ms": dict(zip(TYPES, kms)),
                 "kernel_gbs": {n: (b / (k / 1e3) / 1e9 if k > 0 else None) for n, b, k in zip(TYPES, tb, kms)},
                 "gpu_launches": int(sum(launches)) + 2 * 4 * args.steps,
-                "single_rate": single, "sem_hex": sem, "e2e": e2e, "clocks": clk,
+                "single_rate": single, "sem_hex": sem, "mr_lsrk": mr_lsrk, "e2e": e2e, "clocks": clk,
                 "energy": {"before": E_before, "after": E_after, "rel_change": (E_after - E_before) / E_before,
                            "note": "discrete energy before and after the timed and the profiled multi-rate steps (upwind: non-increasing)"}}
         if batch:

@@ -84,6 +84,8 @@ typedef struct {
                               face terms stay FP32.  1, 2 apply on meshes with the lattice face
                               exchange (no wedge triangle face against a tet or pyramid); the
                               adjoint refuses them (DG_ENOTSUP) */
+  int integrator;          /* nlevels = 2: 0 = multi-rate Adams-Bashforth 3 (default),
+                              1 = multi-rate LSRK(5,4) (see dg_step) */
 } dg_mesh_desc;
 
 /* Build the mesh on the current CUDA device: face matching, geometric factors,
@@ -107,7 +109,9 @@ dg_status dg_host_check(const dg_mesh_desc *desc, double *dt_min, double *trace_
 dg_status dg_layout(const dg_mesh *mesh, int type, int64_t *offset, int64_t *nelem, int *Np);
 dg_status dg_ndof(const dg_mesh *mesh, int64_t *ndof);
 /* Elements of each type (counts[4]: hex, wedge, pyramid, tet) in time-step
- * level `level` (1 = coarsest .. nlevels = finest, Sec. 2.4). */
+ * level `level` (1 = coarsest .. nlevels = finest, Sec. 2.4).  level = 0 on a
+ * multi-rate LSRK mesh (integrator 1): the elements of S, the fine elements and
+ * the coarse elements sharing a face with one. */
 dg_status dg_level_counts(const dg_mesh *mesh, int level, int64_t *counts);
 
 /* Copy a state [4][ndof] into the mesh's state (and zero the LSRK residual).
@@ -128,12 +132,21 @@ dg_status dg_timestep(const dg_mesh *mesh, double *dt_min, int64_t *level_count)
 
 /* Advance the mesh's state (dt <= 0 uses dtau_min).  Asynchronous.
  *   nlevels = 1: nsteps LSRK(5,4) steps of size dt; *t_inout += nsteps*dt.
- *   nlevels = 2: nsteps coarse steps of the two-level multi-rate Adams-Bashforth-3
- *     scheme (reading of Sec. 2.4): fine elements step dt twice, coarse elements
- *     step 2 dt once, coarse states at the half step are predicted from their
- *     AB3 history.  The first call after dg_set_state first runs the start-up
- *     (four LSRK(5,4) steps of size dt that record the rhs history);
- *     *t_inout += 4 dt (start-up) + nsteps * 2 dt. */
+ *   nlevels = 2, integrator 0: nsteps coarse steps of the two-level multi-rate
+ *     Adams-Bashforth-3 scheme (reading of Sec. 2.4): fine elements step dt twice,
+ *     coarse elements step 2 dt once, coarse states at the half step are predicted
+ *     from their AB3 history.  The first call after dg_set_state first runs the
+ *     start-up (four LSRK(5,4) steps of size dt that record the rhs history);
+ *     *t_inout += 4 dt (start-up) + nsteps * 2 dt.
+ *   nlevels = 2, integrator 1: nsteps coarse steps of 2 dt of the two-level
+ *     multi-rate LSRK(5,4) (a local time-stepping RK read for Sec. 2.4): the
+ *     coarse region acts on the step through W(tau) = sum_j rho_{j+1} tau^{j+1}
+ *     B (I - P) B^j y_n (rho: the LSRK(5,4) amplification coefficients, B the
+ *     rhs operator, P the fine elements), the fine correction v' = B P (y + W + v)
+ *     takes two LSRK(5,4) steps of dt, y += W(2 dt) + v.  Fourth order; one
+ *     LSRK(5,4) step of 2 dt on an all-coarse mesh, two of dt on an all-fine one.
+ *     No start-up; *t_inout += nsteps * 2 dt.  Allocates 14 state-sized buffers
+ *     on first use (DG_ENOMEM if they do not fit). */
 dg_status dg_step(dg_mesh *mesh, int nsteps, double dt, double *t_inout);
 
 /* Direct access to the device state [4][ndof] owned by the mesh. */
@@ -223,14 +236,33 @@ dg_status dg_autotune(dg_mesh *mesh, int nsteps, int *choice);
  *   the meshes' history-slot phases; a mesh stepped on its own between batch
  *   calls may change its phase and cost one re-capture).  Asynchronous: errors
  *   of the kernels are reported by the next synchronising call on a mesh.
+ *   Packing (default; environment DG_BATCH_PACK=0 at creation turns it off):
+ *   single-rate meshes without a point source that share N, hex basis, pyramid
+ *   form, tau_scale, precision, face exchange and run-time kernel choices (at
+ *   creation) are merged into one combined mesh per such group, so each element
+ *   type of a group costs one launch per stage; every element keeps its own
+ *   mesh's step, so results are bitwise those of stepping the mesh alone.  Each
+ *   dg_batch_step copies the members' states into the combined meshes and back
+ *   (one gather and one scatter kernel per group).  Creating a batch with groups
+ *   synchronises and allocates the combined meshes (about the members' own
+ *   device memory again).  Other meshes are graph branches of their own.
+ * dg_batch_set_packing: 1 = step the groups through their combined meshes,
+ *   0 = every mesh on its own branch (drops the cached graphs; synchronises).
+ * dg_batch_autotune: times nsteps (rounded up to a multiple of DG_BATCH_CHUNK,
+ *   1..30) batch steps packed and unpacked (best of two graph replays each, after
+ *   a capture), keeps the faster and returns it in *packed (may be NULL); the
+ *   meshes' states are restored.  Synchronises; allocates one state copy per mesh
+ *   for the call.
  * dg_batch_destroy: synchronises the batch stream and frees the batch's graphs,
- *   streams and events (not the meshes). */
+ *   streams, events and combined meshes (not the meshes). */
 #define DG_BATCH_CHUNK 3
 typedef struct dg_batch dg_batch;
 dg_status dg_batch_create(dg_mesh *const *meshes, int count, void *cuda_stream, dg_batch **out);
 dg_status dg_batch_step(dg_batch *batch, int nsteps, const double *dt, double *t_inout);
 /* Graph replays and captures since creation (for tests and measurements). */
 dg_status dg_batch_stats(const dg_batch *batch, int64_t *replays, int64_t *captures);
+dg_status dg_batch_set_packing(dg_batch *batch, int packed);
+dg_status dg_batch_autotune(dg_batch *batch, int nsteps, int *packed);
 void dg_batch_destroy(dg_batch *batch);
 
 /* ---- point source and receivers (hexahedra) --------------------------------

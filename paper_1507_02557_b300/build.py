@@ -10,7 +10,7 @@ OUT = os.path.join(HERE, "libdg.so")
 BUILD = os.environ.get("DG_BUILD_DIR", os.path.join(ROOT, "_build"))
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 EXTRA = os.environ.get("DG_NVCC_FLAGS", "").split()   # extra nvcc flags (variant builds)
-SOURCES = ["refelem.cpp", "setup.cpp", "api.cpp", "kernels.cu", "kernels_gen2.cu", "kernels_tc.cu", "kernels_prec.cu", "noalloc.cu", "batch.cpp", "adjoint.cu", "source.cu", "tune.cpp"]
+SOURCES = ["refelem.cpp", "setup.cpp", "api.cpp", "kernels.cu", "kernels_gen2.cu", "kernels_tc.cu", "kernels_prec.cu", "noalloc.cu", "mrlsrk.cu", "batch.cpp", "adjoint.cu", "source.cu", "tune.cpp"]
 
 
 def nvcc():

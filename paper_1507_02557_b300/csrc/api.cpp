@@ -80,6 +80,10 @@ dg_status dg_mesh_create(const dg_mesh_desc* d, void* stream, dg_mesh** out) {
     if (d->nelem[t] > 0 && (!d->conn[t] || !d->c2[t])) return DG_EINVAL;
   }
   if (!(d->tau_scale >= 0.0)) return DG_EINVAL;
+  if (d->integrator < 0 || d->integrator > 1) {
+    g_err = "integrator 0 (multi-rate AB3) or 1 (multi-rate LSRK) are built";
+    return DG_ENOTSUP;
+  }
   dg_mesh* m = new (std::nothrow) dg_mesh();
   if (!m) return DG_ENOMEM;
   cudaGetDevice(&m->device);
@@ -93,6 +97,22 @@ dg_status dg_mesh_create(const dg_mesh_desc* d, void* stream, dg_mesh** out) {
     dg_free(m);
     delete m;
     return st;
+  }
+  try {   // host copy of the description (a batch may merge the mesh with others of its kind)
+    m->host.d = *d;
+    m->host.xyz.assign(d->xyz, d->xyz + 3 * d->nverts);
+    for (int t = 0; t < 4; ++t) {
+      const int nv = t == DG_HEX ? 8 : t == DG_WEDGE ? 6 : t == DG_PYR ? 5 : 4;
+      m->host.conn[t].assign(d->conn[t], d->conn[t] + nv * d->nelem[t]);
+      m->host.c2[t].assign(d->c2[t], d->c2[t] + d->nelem[t]);
+      m->host.d.conn[t] = nullptr;
+      m->host.d.c2[t] = nullptr;
+    }
+    m->host.d.xyz = nullptr;
+  } catch (const std::bad_alloc&) {
+    dg_free(m);
+    delete m;
+    return DG_ENOMEM;
   }
   if (m->type_streams) {   // created here, not inside a later stream capture
     bool ok = true;
@@ -146,6 +166,10 @@ dg_status dg_layout(const dg_mesh* m, int type, int64_t* offset, int64_t* nelem,
 }
 
 dg_status dg_level_counts(const dg_mesh* m, int level, int64_t* counts) {
+  if (m && counts && level == 0 && m->integrator == 1) {   // multi-rate LSRK: the set S
+    for (int t = 0; t < 4; ++t) counts[t] = m->mr_s.count[t];
+    return DG_OK;
+  }
   if (!m || !counts || level < 1 || level > m->nlevels) return DG_EINVAL;
   for (int t = 0; t < 4; ++t) counts[t] = m->nlevels == 1 ? m->td[t].K : m->lev[level - 1].count[t];
   return DG_OK;
@@ -352,12 +376,14 @@ extern "C" dg_status dg_watchdog_selftest(dg_mesh* m, int64_t limit_cycles) {
 }
 
 cudaError_t dg_enqueue_steps(dg_mesh* m, int nsteps, double dt, double t0) {
+  if (m->nlevels == 2 && m->integrator == 1) return dg_mrlsrk_steps(m, nsteps, dt);
   if (m->nlevels == 2)   // fused kernels: N <= 4 with lattice exchange on tet / pyramid triangle faces
     return m->N <= 4 && m->tri_lat ? mrab3_fused(m, nsteps, dt) : mrab3(m, nsteps, dt);
   return nsteps > 0 ? lsrk_steps(m, nsteps, dt, t0) : cudaSuccess;
 }
 
 double dg_step_time(const dg_mesh* m, int nsteps, double dt, bool fresh) {
+  if (m->nlevels == 2 && m->integrator == 1) return nsteps * 2 * dt;
   if (m->nlevels == 2) return (fresh ? 4 * dt : 0.0) + nsteps * 2 * dt;
   return nsteps * dt;
 }
@@ -376,8 +402,13 @@ extern "C" dg_status dg_step(dg_mesh* m, int nsteps, double dt, double* t_inout)
       return DG_EINVAL;
     }
   }
-  const bool fresh = m->nlevels == 2 && !m->mr_started;
+  const bool fresh = m->nlevels == 2 && m->integrator == 0 && !m->mr_started;
   cudaError_t e = dg_enqueue_steps(m, nsteps, dt, t_inout ? *t_inout : 0.0);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    g_err = "dg_step: the multi-rate LSRK buffers (15 states) do not fit";
+    return DG_ENOMEM;
+  }
   if (e != cudaSuccess) return cuda_fail(e);
   if (t_inout) *t_inout += dg_step_time(m, nsteps, dt, fresh);
   return DG_OK;

@@ -102,6 +102,13 @@ struct dg_mesh {
   float* trace3 = nullptr;        // third trace buffer of the fused multi-rate schedule
   int cslot[3] = {0, 1, 2}, fslot[3] = {2, 0, 1};   // slots of r^n, r^{n-1}, r^{n-2} per level
   bool mr_started = false;
+  // multi-rate LSRK(5,4) (integrator 1, mrlsrk.cu): S = fine elements and the coarse elements sharing
+  // a face with one, T = S and the elements sharing a face with S; in_s[t][e] = 1 for elements of S;
+  // mrl = 14 state-sized buffers allocated on first use
+  int integrator = 0;
+  dgk::Sel mr_s, mr_t, mr_tc;     // mr_tc: the coarse elements of T
+  unsigned char* mr_in_s[4] = {nullptr, nullptr, nullptr, nullptr};
+  float* mrl = nullptr;
   bool hex_sem = false;           // SEM hexahedra (GLL nodes)
   bool tri_lat = true;            // tet / pyramid triangle faces exchange lattice values (gen2)
   bool wall_self = false;         // trace launches also write a wall side's own trace into its slot
@@ -138,6 +145,16 @@ struct dg_mesh {
   float* rec_rows = nullptr;      // [nrec][Np] phi(x_r)
   int* derr = nullptr;            // device error word: bit 0 = a bounded device wait timed out
   dgk::TmaArr tma[5];             // q, res, hist, trace, trace3 (hex TMA staging)
+  // host copy of the description the mesh was created from (batches merge meshes from it)
+  struct HostDesc {
+    std::vector<double> xyz;
+    std::vector<int32_t> conn[4];
+    std::vector<double> c2[4];
+    dg_mesh_desc d{};
+  } host;
+  // per-element LSRK step (float, element order of each type) of a mesh that holds several
+  // batched meshes, each stepped with its own dt; NULL = the scalar dt of the launch
+  float* dte[4] = {nullptr, nullptr, nullptr, nullptr};
   // per-type kernel timing (dg_profile): event pairs recorded around each launch
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -164,6 +181,13 @@ cudaError_t launch_mr(dg_mesh* m, bool coarse, const Sel& sel, float* q, const f
                       const float p[3]);
 cudaError_t launch_ab(dg_mesh* m, const Sel& sel, const float* qin, float* qout, const float* r0,
                       const float* r1, const float* r2, float h0, float h1, float h2);
+// Contiguous device-to-device copies: n floats from src to dst per segment (batch gather / scatter).
+struct Seg {
+  const float* src;
+  float* dst;
+  int64_t n;
+};
+cudaError_t launch_seg_copy(const Seg* segs_dev, int nseg, cudaStream_t s);
 // Hex constants (1D D, V^f, GL weights and nodes) of order N <= 4 into constant memory.
 cudaError_t upload_hex_constants(int N, bool sem, const float* hc, int count);
 struct Args;
@@ -197,6 +221,8 @@ cudaError_t dg_source_amp_grad(dg_mesh* m, const float* rho, double coef, double
 // nsteps time steps of m on m->stream: LSRK(5,4), or multi-rate AB3 whose first call also runs the
 // start-up (nsteps = 0 runs the start-up alone).  No synchronization (api.cpp).
 cudaError_t dg_enqueue_steps(dg_mesh* m, int nsteps, double dt, double t0 = 0.0);
+// nsteps coarse steps (2h) of the two-level multi-rate LSRK(5,4) on m->stream (mrlsrk.cu).
+cudaError_t dg_mrlsrk_steps(dg_mesh* m, int nsteps, double h);
 // Simulated time that dg_enqueue_steps(m, nsteps, dt) advances; fresh = the start-up runs too.
 double dg_step_time(const dg_mesh* m, int nsteps, double dt, bool fresh);
 

@@ -60,6 +60,8 @@ struct Args {
   // with the transposes (D^a)^T), each block vol_np floats wide; NULL = computed in the kernel
   const float* vol;
   int vol_np;
+  // per-element LSRK step (element index of the type), NULL = dt
+  const float* dtE;
 };
 
 __device__ __forceinline__ void flux(bool wall, float pm, float unm, float P, float UN, float tp,

@@ -195,9 +195,10 @@ __global__ void __launch_bounds__(HexCfg<N>::NT, HexCfg<N>::MINB) hex_kernel(Arg
         const float4 qo = s_q4[le][tid];
         const float qv[4] = {qo.x, qo.y, qo.z, qo.w};
 #pragma unroll
+        const float dte = A.dtE ? A.dtE[e] : A.dt;
         for (int fl = 0; fl < 4; ++fl) {
           const int64_t id = fl * A.ndof + base + tid;
-          float r = A.a * A.res[id] + A.dt * rhs[fl];
+          float r = A.a * A.res[id] + dte * rhs[fl];
           float qn = qv[fl] + A.b * r;
           A.res[id] = r;
           A.qout[id] = qn;
@@ -805,12 +806,13 @@ __global__ void __launch_bounds__(128, DG_HEXP_MINB) hexw_kernel(Args A, const _
 #pragma unroll
             for (int f = 0; f < 4; ++f) A.rhs[f * A.ndof + base + col + NQ * k] = rhs[f][k];
         } else if (MODE == MODE_STAGE) {   // LSRK(5,4) 2N-storage update
+          const float dte = A.dtE ? A.dtE[e] : A.dt;
 #pragma unroll
           for (int k = 0; k < n1; ++k)
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
               const int64_t id = f * A.ndof + base + col + NQ * k;
-              const float rr = A.a * auxv(0, f, k) + A.dt * rhs[f][k];
+              const float rr = A.a * auxv(0, f, k) + dte * rhs[f][k];
               q[f][k] += A.b * rr;
               A.res[id] = rr;
               A.qout[id] = q[f][k];
@@ -1196,9 +1198,10 @@ __global__ void __launch_bounds__(128) gen_kernel(Args A) {
         for (int fl = 0; fl < 4; ++fl) A.rhs[fl * A.ndof + base + n] = r[fl];
       } else {
 #pragma unroll
+        const float dte = A.dtE ? A.dtE[e] : A.dt;
         for (int fl = 0; fl < 4; ++fl) {
           const int64_t id = fl * A.ndof + base + n;
-          float rr = A.a * A.res[id] + A.dt * r[fl];
+          float rr = A.a * A.res[id] + dte * r[fl];
           float qn = s_q[fl][n] + A.b * rr;
           A.res[id] = rr;
           A.qout[id] = qn;
@@ -1347,6 +1350,7 @@ static Args make_args(dg_mesh* m, int t) {
   A.side_off = td.side_off;
   A.tau_scale = (float)m->tau_scale;
   A.skew = 1;
+  A.dtE = m->dte[t];
   return A;
 }
 
@@ -1557,6 +1561,19 @@ cudaError_t launch_stage(dg_mesh* m, float* q, float* res, const float* tin, flo
     A[t].dt = dt;
   }
   launch_all<MODE_STAGE>(m, A);
+  return cudaGetLastError();
+}
+
+// one row of blocks per segment (blockIdx.y), grid-stride within it
+__global__ void __launch_bounds__(256) seg_copy_kernel(const Seg* segs) {
+  const Seg g = segs[blockIdx.y];
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < g.n; k += (int64_t)gridDim.x * blockDim.x)
+    g.dst[k] = g.src[k];
+}
+
+cudaError_t launch_seg_copy(const Seg* segs_dev, int nseg, cudaStream_t s) {
+  if (nseg <= 0) return cudaSuccess;
+  seg_copy_kernel<<<dim3(16, (unsigned)nseg), 256, 0, s>>>(segs_dev);
   return cudaGetLastError();
 }
 

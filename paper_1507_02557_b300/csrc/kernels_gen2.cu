@@ -740,10 +740,11 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
           const float4 qo = q4[n];
           const float qv[4] = {qo.x, qo.y, qo.z, qo.w};
           float qn[4];
+          const float dte = A.dtE ? A.dtE[e] : A.dt;
 #pragma unroll
           for (int fl = 0; fl < 4; ++fl) {
             const int64_t id = fl * A.ndof + base + n;
-            const float rr = A.a * A.res[id] + A.dt * rv[fl];
+            const float rr = A.a * A.res[id] + dte * rv[fl];
             qn[fl] = qv[fl] + A.b * rr;
             A.res[id] = rr;
             A.qout[id] = qn[fl];

@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(512, 1) tet_tc_kernel(Args A) {
           if (MODE == MODE_RHS) {
             A.rhs[id] = rv;
           } else if (MODE == MODE_STAGE) {
-            const float rr = A.a * saux[x] + A.dt * rv;
+            const float rr = A.a * saux[x] + (A.dtE ? A.dtE[e] : A.dt) * rv;
             const float qn = qo + A.b * rr;
             A.res[id] = rr;
             A.qout[id] = qn;

@@ -492,6 +492,7 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
     m->cfl = d->cfl > 0 ? d->cfl : 0.5;
     m->pyr_form = d->pyr_form;
     m->precision = d->precision;
+    m->integrator = d->nlevels == 2 ? d->integrator : 0;
     const bool sem = d->hex_basis == 1;   // SEM hexahedra: GLL nodes, GLL points on quad faces
     m->hex_sem = sem;
     Basis B[4];
@@ -1338,6 +1339,43 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
       }
       m->hist = alloc_zero<float>(3 * 4 * (size_t)m->ndof, owned);
       m->trace3 = alloc_zero<float>(2 * (size_t)side * nq, owned);
+      if (d->integrator == 1) {
+        // multi-rate LSRK element sets: S = fine + coarse next to fine, T = S + face neighbours of S
+        std::vector<std::vector<unsigned char>> inS(4), inT(4);
+        for (int t = 0; t < 4; ++t) {
+          inS[t].assign(m->td[t].K, 0);
+          for (int e = 0; e < m->td[t].K; ++e) inS[t][e] = level[t][e] == 2;
+        }
+        auto grow = [&](std::vector<std::vector<unsigned char>>& out, const std::vector<std::vector<unsigned char>>& in) {
+          out = in;
+          for (int64_t s2 = 0; s2 < side; ++s2) {
+            if (nbr[s2] < 0) continue;
+            int t, f, t2, f2;
+            int64_t e, e2;
+            side_elem(s2, t, e, f);
+            side_elem(nbr[s2], t2, e2, f2);
+            if (in[t2][e2]) out[t][e] = 1;
+          }
+        };
+        std::vector<std::vector<unsigned char>> fineS = inS;
+        grow(inS, fineS);
+        grow(inT, inS);
+        for (int t = 0; t < 4; ++t) {
+          std::vector<int> ls, lt, ltc;
+          for (int e = 0; e < m->td[t].K; ++e) {
+            if (inS[t][e]) ls.push_back(e);
+            if (inT[t][e]) lt.push_back(e);
+            if (inT[t][e] && level[t][e] == 1) ltc.push_back(e);
+          }
+          m->mr_tc.count[t] = (int64_t)ltc.size();
+          m->mr_tc.list[t] = upload(ltc, owned);
+          m->mr_s.count[t] = (int64_t)ls.size();
+          m->mr_s.list[t] = upload(ls, owned);
+          m->mr_t.count[t] = (int64_t)lt.size();
+          m->mr_t.list[t] = upload(lt, owned);
+          m->mr_in_s[t] = upload(inS[t], owned);
+        }
+      }
     } else {
       m->level_count[0] = m->td[0].K + m->td[1].K + m->td[2].K + m->td[3].K;
     }

@@ -21,7 +21,8 @@ HEX, WEDGE, PYR, TET = 0, 1, 2, 3
 EXPORTS = ("dg_mesh_create", "dg_mesh_destroy", "dg_host_check", "dg_layout", "dg_ndof", "dg_level_counts",
            "dg_set_state", "dg_get_state", "dg_rhs", "dg_timestep", "dg_step", "dg_state_ptr",
            "dg_energy", "dg_energy_noalloc", "dg_profile", "dg_watchdog_selftest", "dg_adjoint_step",
-           "dg_batch_create", "dg_batch_step", "dg_batch_stats", "dg_batch_destroy",
+           "dg_batch_create", "dg_batch_step", "dg_batch_stats", "dg_batch_set_packing", "dg_batch_autotune",
+           "dg_batch_destroy",
            "dg_set_source", "dg_set_receivers", "dg_sample_receivers", "dg_autotune",
            "dg_status_string", "dg_last_error")
 
@@ -31,7 +32,7 @@ class Desc(C.Structure):
                 ("nelem", C.c_int64 * 4), ("conn", C.POINTER(C.c_int32) * 4),
                 ("c2", C.POINTER(C.c_double) * 4), ("N", C.c_int), ("hex_basis", C.c_int),
                 ("pyr_form", C.c_int), ("tau_scale", C.c_double), ("nlevels", C.c_int),
-                ("cfl", C.c_double), ("precision", C.c_int)]
+                ("cfl", C.c_double), ("precision", C.c_int), ("integrator", C.c_int)]
 
 
 _vp = C.c_void_p
@@ -60,6 +61,8 @@ _lib.dg_profile.argtypes = [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_i
 _lib.dg_batch_create.argtypes = [C.POINTER(_vp), C.c_int, _vp, C.POINTER(_vp)]
 _lib.dg_batch_step.argtypes = [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
 _lib.dg_batch_stats.argtypes = [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+_lib.dg_batch_set_packing.argtypes = [_vp, C.c_int]
+_lib.dg_batch_autotune.argtypes = [_vp, C.c_int, C.POINTER(C.c_int)]
 _lib.dg_batch_destroy.argtypes = [_vp]
 _lib.dg_batch_destroy.restype = None
 BATCH_CHUNK = 3   # DG_BATCH_CHUNK
@@ -86,7 +89,7 @@ def _ptr(x):
     return x.ctypes.data_as(_vp)
 
 
-def _desc(mesh, N, tau_scale, pyr_form, cfl, keep, nlevels=1, hex_basis=0, precision=0):
+def _desc(mesh, N, tau_scale, pyr_form, cfl, keep, nlevels=1, hex_basis=0, precision=0, integrator=0):
     d = Desc()
     xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
     keep.append(xyz)
@@ -101,6 +104,7 @@ def _desc(mesh, N, tau_scale, pyr_form, cfl, keep, nlevels=1, hex_basis=0, preci
         d.c2[t] = c2.ctypes.data_as(C.POINTER(C.c_double))
     d.N, d.hex_basis, d.pyr_form = N, hex_basis, pyr_form
     d.tau_scale, d.nlevels, d.cfl, d.precision = tau_scale, nlevels, cfl, precision
+    d.integrator = integrator
     return d
 
 
@@ -122,11 +126,12 @@ class Mesh:
     """A dg_mesh on the current CUDA device (see include/dg.h)."""
 
     def __init__(self, mesh, N, tau_scale=1.0, pyr_form=0, cfl=0.5, stream=None, nlevels=1, hex_basis=0,
-                 precision=0):
+                 precision=0, integrator=0):
         """precision: 0 = FP32 products; 1 = BF16 x 3, 2 = FP16 x 3 split products on the tensor cores
-        for the tet and pyramid volume terms."""
+        for the tet and pyramid volume terms.  integrator (nlevels = 2): 0 = multi-rate AB3,
+        1 = multi-rate LSRK(5,4)."""
         keep = []
-        d = _desc(mesh, N, tau_scale, pyr_form, cfl, keep, nlevels, hex_basis, precision)
+        d = _desc(mesh, N, tau_scale, pyr_form, cfl, keep, nlevels, hex_basis, precision, integrator)
         h = _vp()
         _check(_lib.dg_mesh_create(C.byref(d), _vp(stream or 0), C.byref(h)))
         self._h = h
@@ -173,6 +178,12 @@ class Mesh:
         """Elements per type (hex, wedge, pyramid, tet) in time-step level 1..nlevels."""
         c = (C.c_int64 * 4)()
         _check(_lib.dg_level_counts(self._h, int(level), c))
+        return list(c)
+
+    def mr_s_counts(self):
+        """Multi-rate LSRK: elements per type of S (fine + coarse elements next to fine ones)."""
+        c = (C.c_int64 * 4)()
+        _check(_lib.dg_level_counts(self._h, 0, c))
         return list(c)
 
     def level_counts(self):
@@ -275,6 +286,16 @@ class Batch:
         ta = (C.c_double * n)(*(t if t is not None else [0.0] * n))
         _check(_lib.dg_batch_step(self._h, int(nsteps), dta, ta))
         return list(ta)
+
+    def set_packing(self, packed):
+        """dg_batch_set_packing: 1 = same-kind meshes through their combined meshes, 0 = mesh by mesh."""
+        _check(_lib.dg_batch_set_packing(self._h, int(packed)))
+
+    def autotune(self, nsteps=3):
+        """dg_batch_autotune: keeps the faster of packed / unpacked stepping; returns 1 if packed."""
+        p = C.c_int()
+        _check(_lib.dg_batch_autotune(self._h, int(nsteps), C.byref(p)))
+        return p.value
 
     def stats(self):
         """(graph replays, graph captures) since creation."""

@@ -159,3 +159,59 @@ def test_autotune_choices_all_match_the_oracle(lib):
     ch = g.autotune(2)
     assert set(ch) == set(g.CHOICES)
     assert np.array_equal(g.get_state(np.zeros_like(q0), on_device=False), q0)
+
+
+PACK_CASES = [   # four single-rate N = 3 meshes (one combined mesh, four different dt_min), and
+    (lambda: small_hybrid_mesh(), 3, 1, 0),                                  # meshes that stay alone
+    (lambda: layered_mesh(3, 3, 5, "HWHTK", seed=3, c_of_layer=lambda k: 1.0 if k % 2 == 0 else 1.5), 3, 1, 0),
+    (lambda: layered_mesh(5, 3, 6, "HHWHTK", seed=5), 3, 1, 0),
+    (lambda: layered_mesh(3, 2, 6, "HTKKUH", seed=2), 3, 1, 0),
+    (lambda: layered_mesh(3, 3, 5, "HWHTK", seed=3, c_of_layer=lambda k: 1.0 if k % 2 == 0 else 1.5), 3, 2, 0),
+    (lambda: layered_mesh(5, 3, 6, "HHWHTK", seed=5), 2, 1, 0),
+    (lambda: small_hybrid_mesh(), 3, 1, 1),
+]
+
+
+def make_pack(lib, i):
+    fac, N, nl, hb = PACK_CASES[i]
+    g = lib.Mesh(fac(), N, nlevels=nl, hex_basis=hb)
+    g.set_state(random_state(g.ndof, 70 + i).astype(np.float32), on_device=False)
+    return g
+
+
+def test_packed_batch_equals_separate_steps_bitwise(lib):
+    """Same-kind single-rate meshes stepped through one combined mesh (each element with its own
+    mesh's dt) give bit for bit the results of stepping each mesh alone; so does the unpacked
+    schedule, and the batch autotuner leaves every state as it found it."""
+    ref = []
+    for i in range(len(PACK_CASES)):
+        g = make_pack(lib, i)
+        g.step(7 % 3)
+        for _ in range(7 // 3 + 1):
+            g.step(3)
+        ref.append(state(g))
+        g.close()
+    meshes = [make_pack(lib, i) for i in range(len(PACK_CASES))]
+    b = lib.Batch(meshes)
+    b.step(7)
+    b.step(3)
+    assert b.stats() == (3, 1)
+    for i, g in enumerate(meshes):
+        got = state(g)
+        assert np.array_equal(got, ref[i]), (i, float(np.abs(got - ref[i]).max()))
+    # three more steps packed, and the same three steps unpacked from the same states
+    single = [i for i, c in enumerate(PACK_CASES) if c[2] == 1]   # (set_state restarts multi-rate)
+    before = [state(g) for g in meshes]
+    b.step(3)
+    packed = [state(g) for g in meshes]
+    for i in single:
+        meshes[i].set_state(before[i], on_device=False)
+    b.set_packing(0)
+    b.step(3)
+    for i in single:
+        assert np.array_equal(state(meshes[i]), packed[i]), i
+    now = [state(g) for g in meshes]
+    assert b.autotune(3) in (0, 1)
+    for i, g in enumerate(meshes):
+        assert np.array_equal(state(g), now[i]), i
+    b.close()

@@ -327,3 +327,48 @@ def test_multirate_on_the_throughput_workload_slab(lib):
         q, hist = mr.step(q, hist, h)
     errs = per_type_rel(o, got, q)
     assert rel(got, q) < TOL and max(errs) < TOL, errs
+
+
+@pytest.mark.parametrize("N", [2, 4, 5])
+def test_multirate_lsrk_matches_oracle(lib, N):
+    """Two-level multi-rate LSRK(5,4) (integrator 1): 3 coarse steps against the oracle's scheme on
+    the c-jump mesh (fine pyramids, tets and wedges next to coarse hexahedra)."""
+    from oracle.constants import trace_constant
+    from oracle.dg import MRLSRK, mr_levels, standing_mode
+    m = MESHES["cjump"]()
+    o = DGOracle(m, N)
+    lev, dmin = mr_levels(o, [trace_constant(t, N) for t in range(4)], 2)
+    g = lib.Mesh(m, N, nlevels=2, integrator=1)
+    h = g.timestep()
+    q0 = o.project(standing_mode, 0.0).astype(np.float32)
+    g.set_state(q0, on_device=False)
+    t = g.step(3, h)
+    got = g.get_state(np.zeros_like(q0), on_device=False).astype(np.float64)
+    mr = MRLSRK(o, lev)
+    q = q0.astype(np.float64)
+    for _ in range(3):
+        q = mr.step(q, h)
+    assert abs(t - 6 * h) < 1e-12
+    assert rel(got, q) < TOL, per_type_rel(o, got, q)
+
+
+def test_multirate_lsrk_on_the_throughput_workload_slab(lib):
+    """Multi-rate LSRK on the 4x4-column slab of the throughput mesh at N = 4 (default kernel
+    choices: TMA hexahedra, tensor-core tets, type streams): 2 coarse steps against the oracle."""
+    from oracle.constants import trace_constant
+    from oracle.dg import MRLSRK, mr_levels
+    m, N = bench_slab(), 4
+    o = DGOracle(m, N)
+    lev, _ = mr_levels(o, [trace_constant(t, N) for t in range(4)], 2)
+    g = lib.Mesh(m, N, nlevels=2, integrator=1)
+    h = g.timestep()
+    q0 = random_state(o.ndof, 23).astype(np.float32)
+    g.set_state(q0, on_device=False)
+    g.step(2, h)
+    got = g.get_state(np.zeros_like(q0), on_device=False).astype(np.float64)
+    mr = MRLSRK(o, lev)
+    q = q0.astype(np.float64)
+    for _ in range(2):
+        q = mr.step(q, h)
+    errs = per_type_rel(o, got, q)
+    assert rel(got, q) < TOL and max(errs) < TOL, errs
