@@ -46,7 +46,7 @@ TypeView view(const dg_mesh* m, int t) {
 template <int T>
 __device__ float node_mass(const TypeView& V, const float* hexc, int N, int64_t e, int n) {
   if (T == DG_WEDGE) return 1.f;
-  if (T == DG_PYR) return V.geo[(e * V.Np + n) * 10 + 9];
+  if (T == DG_PYR) return V.geo[(e * 10 + 9) * V.Np + n];
   const int n1 = N + 1, i = n % n1, j = (n / n1) % n1, k = n / (n1 * n1);
   const float* w1 = hexc + n1 * n1 + 2 * n1;
   const float* r1 = w1 + n1;

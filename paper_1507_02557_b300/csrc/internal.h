@@ -21,7 +21,9 @@ struct TypeDev {
   int64_t side_off = 0;       // first global side index of the type (side = off + e*nf + f)
   float* c2 = nullptr;        // [K]
   float* geo = nullptr;       // hex [K][24] trilinear coefficients; tet [K][12] G,J;
-                              // pyramid [K][Np][10] G,J; wedge [K][nc][12] G, grad J/(2J)
+                              // pyramid [K][10][Np] G,J; wedge [K][12][nc] G, grad J/(2J)
+                              // (component-major within an element: lanes on consecutive
+                              // nodes / points read consecutive words)
   float4* sgeo = nullptr;     // non-hex: [K*nf][nq] (n, w_q J^s [/sqrt J for the wedge])
   float* sisq = nullptr;      // wedge: [K*nf][nq] 1/sqrt(J) at face points
   float* ops = nullptr;       // volume operators (type-specific layout, see setup.cpp)

@@ -1072,15 +1072,16 @@ __global__ void __launch_bounds__(128) gen_kernel(Args A) {
     } else if (T == DG_PYR) {
       // Alg. pyr_vol (skew): u^a_m = J_m sum_d G_ad(m) u_d(m); p-eq (1/J) sum_a (D^a)^T u^a;
       // u-eq -c^2 sum_a G_ad (D^a p)  (J cancels with M^{-1} = 1/J)
-      const float* geo = A.geo + e * NP * 10;
+      const float* geo = A.geo + e * NP * 10;   // [10][NP]: component c of node m at c * NP + m
       for (int x = tid; x < 3 * NP; x += NT) {
         int a = x / NP, m = x % NP;
-        const float* g = geo + m * 10;
-        s_w[a][m] = g[9] * (g[3 * a] * s_q[1][m] + g[3 * a + 1] * s_q[2][m] + g[3 * a + 2] * s_q[3][m]);
+        const float* g = geo + m;
+        s_w[a][m] = g[9 * NP] * (g[3 * a * NP] * s_q[1][m] + g[(3 * a + 1) * NP] * s_q[2][m] +
+                                 g[(3 * a + 2) * NP] * s_q[3][m]);
       }
       __syncthreads();
       for (int n = tid; n < NP; n += NT) {
-        const float* g = geo + n * 10;
+        const float* g = geo + n;
         float pint = 0.f, dp[3];
         for (int a = 0; a < 3; ++a) {
           const float* D = A.ops + a * NP * NP;            // D[m][n] = D^a_{mn}
@@ -1093,15 +1094,16 @@ __global__ void __launch_bounds__(128) gen_kernel(Args A) {
           pint += s1;
           dp[a] = s2;
         }
-        s_r[0][n] = pint / g[9];
-        for (int d = 0; d < 3; ++d) s_r[1 + d][n] = -c2 * (g[d] * dp[0] + g[3 + d] * dp[1] + g[6 + d] * dp[2]);
+        s_r[0][n] = pint / g[9 * NP];
+        for (int d = 0; d < 3; ++d)
+          s_r[1 + d][n] = -c2 * (g[d * NP] * dp[0] + g[(3 + d) * NP] * dp[1] + g[(6 + d) * NP] * dp[2]);
       }
     } else {
       // Alg. wedge_vol1/2 (LSC-DG skew form) at the (N+1)^3 cubature points, M = I
       const float* V = A.ops;                              // [NC][NP]
       const float* VT = A.ops + 4 * NC * NP;               // [NP][NC]
       const float* wq = A.ops + 8 * NC * NP;
-      const float* geo = A.geo + e * NC * 12;
+      const float* geo = A.geo + e * NC * 12;   // [12][NC]: component c of point q at c * NC + q
       for (int q = tid; q < NC; q += NT) {
         float P = 0.f, Pa[3] = {0.f, 0.f, 0.f}, U[3] = {0.f, 0.f, 0.f};
         for (int m = 0; m < NP; ++m) {
@@ -1113,17 +1115,18 @@ __global__ void __launch_bounds__(128) gen_kernel(Args A) {
 #pragma unroll
           for (int a = 0; a < 3; ++a) Pa[a] += VT[(1 + a) * NC * NP + m * NC + q] * s_q[0][m];
         }
-        const float* g = geo + q * 12;
+        const float* g = geo + q;
         const float w = wq[q];
         float UJ = 0.f;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          float Ad = g[d] * Pa[0] + g[3 + d] * Pa[1] + g[6 + d] * Pa[2] - P * g[9 + d];
+          float Ad = g[d * NC] * Pa[0] + g[(3 + d) * NC] * Pa[1] + g[(6 + d) * NC] * Pa[2] - P * g[(9 + d) * NC];
           s_w[d][q] = w * Ad;
-          UJ += U[d] * g[9 + d];
+          UJ += U[d] * g[(9 + d) * NC];
         }
 #pragma unroll
-        for (int a = 0; a < 3; ++a) s_w[3 + a][q] = w * (g[3 * a] * U[0] + g[3 * a + 1] * U[1] + g[3 * a + 2] * U[2]);
+        for (int a = 0; a < 3; ++a)
+          s_w[3 + a][q] = w * (g[3 * a * NC] * U[0] + g[(3 * a + 1) * NC] * U[1] + g[(3 * a + 2) * NC] * U[2]);
         s_w[6][q] = w * UJ;
       }
       __syncthreads();
@@ -1189,7 +1192,7 @@ __global__ void __launch_bounds__(128) gen_kernel(Args A) {
       }
       float iM = 1.f;
       if (T == DG_TET) iM = 1.f / s_e[9];
-      if (T == DG_PYR) iM = 1.f / A.geo[(e * NP + n) * 10 + 9];
+      if (T == DG_PYR) iM = 1.f / A.geo[(e * 10 + 9) * NP + n];
       float r[4];
 #pragma unroll
       for (int fl = 0; fl < 4; ++fl) r[fl] = s_r[fl][n] + (fl == 0 ? 1.f : c2) * iM * sum[fl];
@@ -1283,7 +1286,7 @@ __global__ void __launch_bounds__(256) energy_kernel(Args A, const float* chol, 
       } else if (T == DG_WEDGE) {
         term = wsq;
       } else {
-        term = A.geo[(e * NP + n) * 10 + 9] * wsq;
+        term = A.geo[(e * 10 + 9) * NP + n] * wsq;
       }
     }
     loc += (double)term;

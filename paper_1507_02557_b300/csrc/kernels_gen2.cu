@@ -424,9 +424,14 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
           }
         }
       } else if (T == DG_PYR) {
-        const float* geo = A.geo + e * NP * 10;
+        const float* geo = A.geo + e * NP * 10;   // [10][NP]: component c of node m at c * NP + m
+        auto geo_at = [&](int m, float (&g)[10]) {   // lanes read consecutive nodes: coalesced
+#pragma unroll
+          for (int c = 0; c < 10; ++c) g[c] = geo[c * NP + m];
+        };
         for (int m = lane; m < NP && !A.vol; m += 32) {
-          const float* g = geo + m * 10;
+          float g[10];
+          geo_at(m, g);
           const float4 v = q4[m];
           const float J = g[9];
           W4[m] = f4(J * (g[0] * v.y + g[1] * v.z + g[2] * v.w), J * (g[3] * v.y + g[4] * v.z + g[5] * v.w),
@@ -443,7 +448,8 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
           a[5] = fmaf(dr.z, w.w, a[5]);
         };
         auto pyr_out = [&](int r, const float* a) {
-          const float* g = geo + (lane + 32 * r) * 10;
+          float g[10];
+          geo_at(lane + 32 * r, g);
           acc[r] = f4((a[0] + a[1] + a[2]) / g[9], -c2 * (g[0] * a[3] + g[3] * a[4] + g[6] * a[5]),
                       -c2 * (g[1] * a[3] + g[4] * a[4] + g[7] * a[5]), -c2 * (g[2] * a[3] + g[5] * a[4] + g[8] * a[5]));
         };
@@ -514,7 +520,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
         float4* Ys4 = W4 + NT * N1;       // phase 1: [NT][N1] sum_j D1 p (x); phase 2: ZB
         float4* X1 = W4 + 2 * NT * N1;    // [WXN] w (A0, A1, A2, UJ)
         float4* X2 = X1 + C::WXN;         // [WXN] w (GU0, GU1, GU2, 0)
-        const float* geo = A.geo + e * NC * 12;
+        const float* geo = A.geo + e * NC * 12;   // [12][NC]: component c of point q at c * NC + q
         for (int x = lane; x < NT * N1; x += 32) {
           const int mt = x / N1, l = x % N1;
           float4 y = f4(0.f, 0.f, 0.f, 0.f);
@@ -550,7 +556,9 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
             U1 = fmaf(v.x, y.z, U1);
             U2 = fmaf(v.x, y.w, U2);
           }
-          const float* g = geo + qc * 12;
+          float g[12];   // lanes read consecutive cubature points: coalesced
+#pragma unroll
+          for (int c = 0; c < 12; ++c) g[c] = geo[c * NC + qc];
           const float w = wq[qt * N1 + l];
           const float A0 = g[0] * Pr + g[3] * Ps + g[6] * Pt - P * g[9];
           const float A1 = g[1] * Pr + g[4] * Ps + g[7] * Pt - P * g[10];
@@ -714,7 +722,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
         }
         float iM = 1.f;
         if (T == DG_TET) iM = 1.f / A.geo[e * 12 + 9];
-        if (T == DG_PYR) iM = 1.f / A.geo[(e * NP + n) * 10 + 9];
+        if (T == DG_PYR) iM = 1.f / A.geo[(e * 10 + 9) * NP + n];
         acc[r].x += iM * sum.x;
         acc[r].y += c2 * iM * sum.y;
         acc[r].z += c2 * iM * sum.z;

@@ -124,8 +124,8 @@ __global__ void __launch_bounds__(256) pack_kernel(Args A, PrecDev P) {
       if (blk == 3) return A.q[base + m];
       const float u = A.q[A.ndof + base + m], v = A.q[2 * A.ndof + base + m], w = A.q[3 * A.ndof + base + m];
       if (T == DG_TET) return gt[3 * blk] * u + gt[3 * blk + 1] * v + gt[3 * blk + 2] * w;
-      const float* g = A.geo + (e * NP + m) * 10;
-      return g[9] * (g[3 * blk] * u + g[3 * blk + 1] * v + g[3 * blk + 2] * w);
+      const float* g = A.geo + e * 10 * NP + m;   // [10][NP] per element
+      return g[9 * NP] * (g[3 * blk * NP] * u + g[(3 * blk + 1) * NP] * v + g[(3 * blk + 2) * NP] * w);
     };
     float mx = 0.f;
     for (int k = lane; k < kx; k += 32) mx = fmaxf(mx, fabsf(value(k)));

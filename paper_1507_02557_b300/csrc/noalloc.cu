@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(128) element_energy(const float* q, int64_t nd
     } else if (T == DG_WEDGE) {
       loc += wsq;
     } else if (T == DG_PYR) {
-      loc += (double)geo[(e * NP + n) * 10 + 9] * wsq;
+      loc += (double)geo[(e * 10 + 9) * NP + n] * wsq;
     } else {
       double s = 0.0;
       for (int m = 0; m < NP; ++m) {

@@ -696,8 +696,8 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
             map_jacobian(PYR, xv, rst, F);
             double J = inverse_metric(F, G);
             if (!(J > 0)) flag("pyramid with J <= 0");
-            for (int i = 0; i < 9; ++i) ge[10 * n + i] = (float)G[i];
-            ge[10 * n + 9] = (float)J;
+            for (int i = 0; i < 9; ++i) ge[i * Np + n] = (float)G[i];   // [10][Np]: component-major
+            ge[9 * Np + n] = (float)J;
             jinvmax[t][e] = std::max(jinvmax[t][e], 1.0 / J);
           }
         } else {  // wedge
@@ -707,10 +707,10 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
             if (!(J > 0)) flag("wedge with J <= 0");
             double gJ[3];
             wedge_grad_J(xv, &wedge_pts[3 * q], gJ);
-            for (int i = 0; i < 9; ++i) ge[12 * q + i] = (float)G[i];
+            for (int i = 0; i < 9; ++i) ge[i * td.nc + q] = (float)G[i];   // [12][nc]: component-major
             for (int dd = 0; dd < 3; ++dd) {
               double gx = G[0 + dd] * gJ[0] + G[3 + dd] * gJ[1] + G[6 + dd] * gJ[2];
-              ge[12 * q + 9 + dd] = (float)(gx / (2.0 * J));
+              ge[(9 + dd) * td.nc + q] = (float)(gx / (2.0 * J));
             }
           }
         }
