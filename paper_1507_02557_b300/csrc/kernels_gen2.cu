@@ -45,7 +45,17 @@ struct G2 {
   static constexpr int NQUAD = NF - NTRI;
   static constexpr int NC = T == DG_WEDGE ? (N + 1) * (N + 1) * (N + 1) : 0;
   static constexpr int N1 = N + 1, NT = NFN;                            // wedge: 1D points, triangle modes
-  static constexpr int VOL = T == DG_WEDGE ? NQ * NT * 4 + 2 * N1 * N1 + NQ * N1 : NP * NP * 4;
+  // pyramid: work items of the sum-factorised volume products (level pairs (q, k) with k <= q + 1,
+  // (k + 1)(q + 1) items each) and the factor tables FE, FD [N1]^4, CR, CC, AH [N1]^2
+  static constexpr int pyr_items() {
+    int s = 0;
+    for (int q = 0; q <= N; ++q)
+      for (int k = 0; k <= (q + 1 < N ? q + 1 : N); ++k) s += (k + 1) * (q + 1);
+    return s;
+  }
+  static constexpr int NIT = T == DG_PYR ? pyr_items() : 0;
+  static constexpr int VOL = T == DG_WEDGE ? NQ * NT * 4 + 2 * N1 * N1 + NQ * N1
+                             : T == DG_PYR ? 2 * N1 * N1 * N1 * N1 + 3 * N1 * N1 : NP * NP * 4;
   static constexpr int NKL = (N + 1) * (N + 2) / 2;                   // pyramid (level k, index l <= k)
   // tet: lattice lift; pyramid: EF [4][NKL] | PF [4][NFN][NKL] | PF2 [4][NFN][NKL]; wedge: Vtl [2][NFN][NT]
   static constexpr int TN = T == DG_WEDGE ? NTRI * NFN * NT
@@ -58,10 +68,9 @@ struct G2 {
   // pyramid N <= 4: the volume loop reads D^a[m][n] (a = r, s, t) and D^t[n][m] as one float4
   // (the .w of the operator entry) and D^r[n][m], D^s[n][m] as a float2 from PV2, laid out
   // [m][n] so that the lanes' reads are contiguous: 6 words instead of two float4 per product
-  static constexpr bool PK = T == DG_PYR && N <= 4;
-  static constexpr int PV2 = PK ? 2 * NP * NP : 0;
+  static constexpr int PV2 = 0;
   static constexpr int OPS = VOL + PV2 + TN + TQ + TN2 + NQ * NFN;
-  static constexpr int IOPS = 12 * NFN + 8 * NQ + (T == DG_TET ? 4 * NFN : 0);
+  static constexpr int IOPS = 12 * NFN + 8 * NQ + (T == DG_TET ? 4 * NFN : 0) + (T == DG_PYR ? N1 * N1 + NIT : 0);
   static constexpr int OPS_B = ((OPS * 4 + 15) / 16) * 16;
   static constexpr int IOPS_B = ((IOPS * 4 + 15) / 16) * 16;
   // per-warp float4 buffers: q4, W4 (wedge: Y/Z pair + X1,X2), F4, G4 (local-order moments),
@@ -77,14 +86,14 @@ struct G2 {
   // tet / pyramid: the volume operator transposed, (D^T)[m][n] = D[n][m] as float4, follows the
   // operators in global memory at float offset OPS_T (host layout size NOPS)
   static constexpr int OPS_T = ((OPS + 3) / 4) * 4;
-  static constexpr int NOPS = OPS_T + (T == DG_WEDGE ? 0 : VOL);
+  static constexpr int NOPS = OPS_T + (T == DG_TET ? VOL : 0);
   // one block per SM.  Warps per block: 16 (pyramid 22, which fill the shared memory at N = 4),
   // fewer where the per-warp buffers do not fit.  The operators sit in shared memory while at
   // least 6 warps fit beside them (N <= 4: all of them); otherwise the kernel reads them from
   // global memory through L1, the volume operator in its transposed copy so that the lanes'
   // reads of one column are contiguous.
   static constexpr int SMEM_CAP = 226 * 1024;
-  static constexpr int NW_DEF = T == DG_PYR ? 22 : 16;
+  static constexpr int NW_DEF = T == DG_PYR ? 28 : 16;
   static constexpr int WB_B = WB * 16;
   static constexpr int NW_SM = (SMEM_CAP - OPS_B - IOPS_B) / WB_B;
   static constexpr bool OPS_SMEM =
@@ -96,8 +105,8 @@ struct G2 {
   // per step on the throughput mesh).  Pyramids stage D and D^T per chunk: at N = 6 (10-row
   // chunks) that pays (17.7 -> 15.5 ms); at N = 7 the chunks are 7 rows and the block barriers
   // cost more than the L2 reads saved (29.9 -> 36.1 ms), so there they read through L1.
-  static constexpr bool CHUNK = !OPS_SMEM && (T == DG_TET || (T == DG_PYR && N == 6));
-  static constexpr int NOPV = T == DG_PYR ? 2 : 1;
+  static constexpr bool CHUNK = !OPS_SMEM && T == DG_TET;
+  static constexpr int NOPV = 1;
   static constexpr int CM0 = 49152 / (NP * 16 * NOPV);
   static constexpr int CM = CM0 < 4 ? 4 : (CM0 > NP ? NP : CM0);
   static constexpr int CHUNK_B = CHUNK ? CM * NP * 16 * NOPV : 0;
@@ -106,6 +115,7 @@ struct G2 {
   static constexpr int SMEM = (OPS_SMEM ? OPS_B : 0) + IOPS_B + CHUNK_B + NW * WB_B;
   static constexpr int R = (NP + 31) / 32;
   static_assert(N > 4 || (OPS_SMEM && NW == NW_DEF), "N <= 4 keeps its operators and warps in shared memory");
+  static_assert(T != DG_PYR || 3 * NIT <= 4 * (WB - NP - WV), "pyramid product scratch exceeds the free warp buffers");
   static_assert(NW >= 1, "per-warp buffers exceed the shared memory");
 };
 
@@ -438,15 +448,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
                      J * (g[6] * v.y + g[7] * v.z + g[8] * v.w), v.x);
         }
         __syncwarp();
-        // (D^a)^T against J G u (skew part), D^a against p
-        auto pyr_acc = [&](float* a, const float4& dc, const float4& dr, const float4& w) {
-          a[0] = fmaf(dc.x, w.x, a[0]);
-          a[1] = fmaf(dc.y, w.y, a[1]);
-          a[2] = fmaf(dc.z, w.z, a[2]);
-          a[3] = fmaf(dr.x, w.w, a[3]);
-          a[4] = fmaf(dr.y, w.w, a[4]);
-          a[5] = fmaf(dr.z, w.w, a[5]);
-        };
+        // a[0] = sum_a ((D^a)^T J G u_a)[n] (skew part), a[3..5] = (D^a p)[n]
         auto pyr_out = [&](int r, const float* a) {
           float g[10];
           geo_at(lane + 32 * r, g);
@@ -462,55 +464,113 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
             const float a[6] = {vr[n], 0.f, 0.f, vr[A.vol_np + n], vr[2 * A.vol_np + n], vr[3 * A.vol_np + n]};
             pyr_out(r, a);
           }
-        } else if constexpr (C::CHUNK) {   // all rows accumulate across the block's operator chunks
-          float s6[R][6];
-#pragma unroll
-          for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) s6[r][c] = 0.f;
-          float4* schT = sch + C::CM * NP;
-          for (int m0 = 0; m0 < NP; m0 += C::CM) {
-            const int mc = NP - m0 < C::CM ? NP - m0 : C::CM;
-            __syncthreads();
-            for (int x = threadIdx.x; x < mc * NP; x += blockDim.x) {
-              sch[x] = __ldg(DV4 + (size_t)m0 * NP + x);
-              schT[x] = __ldg(DT4 + (size_t)m0 * NP + x);
+        } else {
+          // Sum-factorised skew volume terms (factor tables of the level pairs (q, k), see the host
+          // layout): node (i, j, k) = off_k + j (k + 1) + i with off_k = k (k + 1)(2k + 1) / 6.
+          constexpr int N1 = C::N1, NIT = C::NIT;
+          const float* FE = sop;                                   // [q][k][l][i]
+          const float* FD = FE + N1 * N1 * N1 * N1;
+          const float* CR = FD + N1 * N1 * N1 * N1;
+          const float* CC = CR + N1 * N1;
+          const float* AH = CC + N1 * N1;
+          const int* PB = sio + 12 * NFN + 8 * NQ;                 // [q][k] first item of the pair
+          const int* IT = PB + N1 * N1;                            // items q | k<<4 | a<<8 | b<<12
+          float* TT = reinterpret_cast<float*>(F4);                // scratch: the free face buffers
+          auto off = [](int k) { return k * (k + 1) * (2 * k + 1) / 6; };
+          auto lev = [&](int n) {
+            int k = 0;
+            while (off(k + 1) <= n) ++k;
+            return k;
+          };
+          // (A) T[q][k][i][b] = sum_j E[q][k][b][j] p(i,j,k); T' with E' (b: test-level index)
+          for (int x = lane; x < NIT; x += 32) {
+            const int it = IT[x], q = it & 15, k = (it >> 4) & 15, i = (it >> 8) & 15, b = (it >> 12) & 15;
+            const float* fe = FE + ((q * N1 + k) * N1 + b) * N1;
+            const float* fd = FD + ((q * N1 + k) * N1 + b) * N1;
+            const float4* pk = q4 + off(k) + i;
+            float t = 0.f, td = 0.f;
+            for (int j = 0; j <= k; ++j) {
+              const float pv = pk[j * (k + 1)].x;
+              t = fmaf(fe[j], pv, t);
+              td = fmaf(fd[j], pv, td);
             }
-            __syncthreads();
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-              const int n = lane + 32 * r;
-              if (n >= NP) break;
-#pragma unroll 4
-              for (int mm = 0; mm < mc; ++mm) pyr_acc(s6[r], sch[mm * NP + n], schT[mm * NP + n], W4[m0 + mm]);
-            }
+            TT[x] = t;
+            TT[NIT + x] = td;
           }
-#pragma unroll
-          for (int r = 0; r < R; ++r)
-            if (lane + 32 * r < NP) pyr_out(r, s6[r]);
-        } else if constexpr (C::PK) {   // operator entry + its transpose in 6 words
+          __syncwarp();
+          // (B) test node n = (l, b, q): D^r p, D^s p, D^t p
+          float yg[R][3];
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const int n = lane + 32 * r;
-            if (n >= NP) break;
-            float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll C::UNR
-            for (int m = 0; m < NP; ++m) {
-              const float4 dc = DV4[m * NP + n], w = W4[m];
-              const float2 d2 = P2[m * NP + n];
-              pyr_acc(a, dc, f4(d2.x, d2.y, dc.w, 0.f), w);
+            yg[r][0] = yg[r][1] = yg[r][2] = 0.f;
+            if (n >= NP) continue;
+            const int q = lev(n), rem = n - off(q), b = rem / (q + 1), l = rem - b * (q + 1);
+            float yr = 0.f, ys = 0.f, yc = 0.f;
+            for (int k = 0; k <= (q + 1 < N ? q + 1 : N); ++k) {
+              const int base = PB[q * N1 + k];
+              const float cr = CR[q * N1 + k], cc = CC[q * N1 + k];
+              const float* fe = FE + ((q * N1 + k) * N1 + l) * N1;
+              const float* fd = FD + ((q * N1 + k) * N1 + l) * N1;
+              float sr = 0.f, ss = 0.f, sc = 0.f;
+              for (int i = 0; i <= k; ++i) {
+                const float t = TT[base + i * (q + 1) + b], td = TT[NIT + base + i * (q + 1) + b];
+                sr = fmaf(fd[i], t, sr);
+                ss = fmaf(fe[i], td, ss);
+                sc = fmaf(fe[i], t, sc);
+              }
+              yr = fmaf(cr, sr, yr);
+              ys = fmaf(cr, ss, ys);
+              yc = fmaf(cc, sc, yc);
             }
-            pyr_out(r, a);
+            yg[r][0] = yr;
+            yg[r][1] = ys;
+            yg[r][2] = AH[q * N1 + l] * yr + AH[q * N1 + b] * ys + yc;
           }
-        } else {   // one row at a time
+          __syncwarp();
+          // (C) W_r + (1+a_l)/2 W_t, W_s + (1+a_b)/2 W_t, W_t at each node (in place), then
+          // A1[q][k][j][l] = sum_b E[q][k][b][j] (..)_r(l,b,q), A2 with E' and (..)_s, A3 with E and W_t
+          for (int m = lane; m < NP; m += 32) {
+            const int q = lev(m), rem = m - off(q), b = rem / (q + 1), l = rem - b * (q + 1);
+            const float4 w = W4[m];
+            W4[m] = f4(fmaf(AH[q * N1 + l], w.z, w.x), fmaf(AH[q * N1 + b], w.z, w.y), w.z, w.w);
+          }
+          __syncwarp();
+          for (int x = lane; x < NIT; x += 32) {
+            const int it = IT[x], q = it & 15, k = (it >> 4) & 15, j = (it >> 8) & 15, l = (it >> 12) & 15;
+            const float4* wq4 = W4 + off(q) + l;
+            float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+            for (int b = 0; b <= q; ++b) {
+              const float e1 = FE[((q * N1 + k) * N1 + b) * N1 + j], d1 = FD[((q * N1 + k) * N1 + b) * N1 + j];
+              const float4 w = wq4[b * (q + 1)];
+              a1 = fmaf(e1, w.x, a1);
+              a2 = fmaf(d1, w.y, a2);
+              a3 = fmaf(e1, w.z, a3);
+            }
+            TT[x] = a1;
+            TT[NIT + x] = a2;
+            TT[2 * NIT + x] = a3;
+          }
+          __syncwarp();
+          // (D) trial node m = (i, j, k): sum over the test levels q >= k - 1
 #pragma unroll
           for (int r = 0; r < R; ++r) {
-            const int n = lane + 32 * r;
-            if (n >= NP) break;
-            float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll C::UNR
-            for (int m = 0; m < NP; ++m)
-              pyr_acc(a, DV4[m * NP + n], C::OPS_SMEM ? DV4[n * NP + m] : __ldg(DT4 + m * NP + n), W4[m]);
+            const int m = lane + 32 * r;
+            if (m >= NP) break;
+            const int k = lev(m), rem = m - off(k), j = rem / (k + 1), i = rem - j * (k + 1);
+            float z = 0.f;
+            for (int q = (k > 0 ? k - 1 : 0); q <= N; ++q) {
+              const int base = PB[q * N1 + k] + j * (q + 1);
+              const float cr = CR[q * N1 + k], cc = CC[q * N1 + k];
+              float s1 = 0.f, s3 = 0.f;
+              for (int l = 0; l <= q; ++l) {
+                const float e1 = FE[((q * N1 + k) * N1 + l) * N1 + i], d1 = FD[((q * N1 + k) * N1 + l) * N1 + i];
+                s1 = fmaf(d1, TT[base + l], fmaf(e1, TT[NIT + base + l], s1));
+                s3 = fmaf(e1, TT[2 * NIT + base + l], s3);
+              }
+              z = fmaf(cr, s1, fmaf(cc, s3, z));
+            }
+            const float a[6] = {z, 0.f, 0.f, yg[r][0], yg[r][1], yg[r][2]};
             pyr_out(r, a);
           }
         }

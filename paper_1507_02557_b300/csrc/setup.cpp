@@ -922,6 +922,7 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
         td.L = upload(L, owned);
         // volume operators
         std::vector<float> ops;
+        std::vector<double> Mc, Cc;   // pyramid level-pair c-integrals (sum-factorised operators)
         if (t == TET) {
           // DT[a][m][n] = d l_m / d r_a (x_n)
           std::vector<double> g(3 * Np);
@@ -937,7 +938,8 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
           const Basis& Bp = B[t];
           std::vector<double> c, wc;
           gauss_jacobi(2 * N + 4, 0, 0, c, wc);
-          std::vector<double> Mc(n1 * n1, 0.0), Cc(n1 * n1, 0.0);
+          Mc.assign(n1 * n1, 0.0);
+          Cc.assign(n1 * n1, 0.0);
           for (int n = 0; n <= N; ++n)
             for (int k = 0; k <= N; ++k) {
               double s1 = 0, s2 = 0;
@@ -1052,24 +1054,60 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
             rst[c] = l[0] * vert_rst(t, fv[0])[c] + l[1] * vert_rst(t, fv[1])[c] + l[2] * vert_rst(t, fv[2])[c];
         };
         std::vector<double> gg(3 * Np);
-        if (t == TET || t == PYR) {
-          // DV4[n][m] = (D^r, D^s, D^t)[n][m], row n = node / test function; pyramid .w = D^t[m][n]
+        if (t == TET) {
+          // DV4[n][m] = (D^r, D^s, D^t, 0)[n][m], row n = node / test function (ops holds DT[a][m][n])
           for (int n = 0; n < Np; ++n)
             for (int mm = 0; mm < Np; ++mm) {
-              if (t == TET) {
-                // ops holds DT[a][m][n]
-                for (int a = 0; a < 3; ++a) o2.push_back(ops[(a * Np + mm) * Np + n]);
-                o2.push_back(0.f);
-              } else {
-                for (int a = 0; a < 3; ++a) o2.push_back(ops[(a * Np + n) * Np + mm]);
-                o2.push_back(ops[(2 * Np + mm) * Np + n]);
+              for (int a = 0; a < 3; ++a) o2.push_back(ops[(a * Np + mm) * Np + n]);
+              o2.push_back(0.f);
+            }
+        }
+        if (t == PYR) {
+          // Sum-factorised volume operators (Sec. 2.3.4): the semi-nodal basis is a product of 1D
+          // Lagrange factors per level, so with test level q, trial level k,
+          //   D^r[(l,p,q),(i,j,k)] = E'qk[l][i] Eqk[p][j] cr[q][k],  D^s: E[l][i] E'[p][j] cr,
+          //   D^t = (1+a_l)/2 D^r + (1+a_p)/2 D^s + E[l][i] E[p][j] cc[q][k],
+          // Eqk[l][i] = sqrt(w^q_l / w^k_i) l^k_i(a^q_l), E' with the derivative of l^k_i (the GL rule
+          // of level q integrates the a and b factors exactly), cr = Mc (nonzero for |q - k| <= 1),
+          // cc = Cc (nonzero for k <= q + 1).  Layout: FE[n1][n1][n1][n1] (q, k, l, i) | FD (same) |
+          // CR[n1][n1] | CC[n1][n1] | AH[n1][n1] = (1 + a^q_l)/2.
+          const Basis& Bp = B[t];
+          std::vector<float> fe((size_t)n1 * n1 * n1 * n1, 0.f), fd(fe.size(), 0.f), cr(n1 * n1, 0.f),
+              cc(n1 * n1, 0.f), ah(n1 * n1, 0.f);
+          std::vector<double> lk(n1), dlk(n1);
+          for (int q = 0; q <= N; ++q) {
+            for (int l = 0; l <= q; ++l) ah[q * n1 + l] = (float)(0.5 * (1 + Bp.lev_x[q][l]));
+            for (int k = 0; k <= N; ++k) {
+              if (std::abs(q - k) <= 1) cr[q * n1 + k] = (float)Mc[q * n1 + k];
+              if (k <= q + 1) cc[q * n1 + k] = (float)Cc[q * n1 + k];
+              for (int l = 0; l <= q; ++l) {
+                lagrange(Bp.lev_x[k], Bp.lev_x[q][l], lk.data(), dlk.data());
+                for (int i = 0; i <= k; ++i) {
+                  const double f = std::sqrt(Bp.lev_w[q][l] / Bp.lev_w[k][i]);
+                  fe[((size_t)(q * n1 + k) * n1 + l) * n1 + i] = (float)(f * lk[i]);
+                  fd[((size_t)(q * n1 + k) * n1 + l) * n1 + i] = (float)(f * dlk[i]);
+                }
               }
             }
-          // pyramid N <= 4: P2[m][n] = (D^r, D^s)[n][m] (the gen2 kernel reads it from shared memory)
-          if (t == PYR && N <= 4)
-            for (int mm = 0; mm < Np; ++mm)
-              for (int n = 0; n < Np; ++n)
-                for (int a = 0; a < 2; ++a) o2.push_back(ops[(a * Np + n) * Np + mm]);
+          }
+          o2.insert(o2.end(), fe.begin(), fe.end());
+          o2.insert(o2.end(), fd.begin(), fd.end());
+          o2.insert(o2.end(), cr.begin(), cr.end());
+          o2.insert(o2.end(), cc.begin(), cc.end());
+          o2.insert(o2.end(), ah.begin(), ah.end());
+          // work items of the factorised products (ints after the face tables): PB[q][k] = first item
+          // of level pair (q, k) (-1: no pair), then items (q, k, a, b) packed q | k << 4 | a << 8 |
+          // b << 12 for the pairs with k <= q + 1, a < k + 1 (trial-level index), b < q + 1
+          // (test-level index), a-major within a pair
+          std::vector<int> pb(n1 * n1, -1), it;
+          for (int q = 0; q <= N; ++q)
+            for (int k = 0; k <= std::min(q + 1, N); ++k) {
+              pb[q * n1 + k] = (int)it.size();
+              for (int a = 0; a <= k; ++a)
+                for (int b = 0; b <= q; ++b) it.push_back(q | (k << 4) | (a << 8) | (b << 12));
+            }
+          i2.insert(i2.end(), pb.begin(), pb.end());
+          i2.insert(i2.end(), it.begin(), it.end());
         }
         if (t == TET) {
           std::vector<int> fnode(4 * nfn, -1);
@@ -1235,9 +1273,9 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
           }
         }
         for (double v : E) o2.push_back((float)v);
-        if (t != WEDGE) {
+        if (t != WEDGE) while (o2.size() % 4) o2.push_back(0.f);   // the kernels' size check (OPS_T)
+        if (t == TET) {
           // the volume operator transposed (float4 rows), 16-byte aligned after the operators
-          while (o2.size() % 4) o2.push_back(0.f);
           std::vector<float> dt4((size_t)Np * Np * 4);
           for (int n = 0; n < Np; ++n)
             for (int mm = 0; mm < Np; ++mm)
@@ -1258,10 +1296,14 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
           const int npk = P.npk, npp = P.npp;
           std::vector<float> b((size_t)4 * npp * 4 * npk, 0.f);
           float bmax = 0.f;
+          // D^a[x][y]: tets from DV4 (o2), pyramids from the dense host operators (ops: D[a][x][y])
+          auto dop = [&](int a, int x, int y) -> float {
+            return t == TET ? o2[((size_t)x * Np + y) * 4 + a] : ops[((size_t)a * Np + x) * Np + y];
+          };
           for (int n = 0; n < Np; ++n)
             for (int mm = 0; mm < Np; ++mm)
               for (int a = 0; a < 3; ++a) {
-                const float dnm = o2[((size_t)n * Np + mm) * 4 + a], dmn = o2[((size_t)mm * Np + n) * 4 + a];
+                const float dnm = dop(a, n, mm), dmn = dop(a, mm, n);
                 b[(size_t)n * 4 * npk + a * npk + mm] = t == TET ? dnm : dmn;
                 b[(size_t)((1 + a) * npp + n) * 4 * npk + 3 * npk + mm] = dnm;
                 bmax = std::max(bmax, std::fabs(dnm));
