@@ -141,6 +141,56 @@ def cpu_baseline(n1=4, steps1=3, n_all=2, steps_all=3):
                                    f"in {one[2]:.1f} s, 1 thread"}}
 
 
+class _CNvml:
+    """The few read-only NVML queries the clock sampler needs, from the driver's libnvidia-ml
+    through ctypes (for hosts without the Python bindings).  Constants from the public NVML API."""
+
+    NVML_CLOCK_SM = 1
+    nvmlClocksEventReasonSwPowerCap = 0x4
+    nvmlClocksEventReasonHwSlowdown = 0x8
+    nvmlClocksEventReasonSwThermalSlowdown = 0x20
+    nvmlClocksEventReasonHwThermalSlowdown = 0x40
+
+    def __init__(self):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+
+    def _ok(self, rc, what):
+        if rc != 0:
+            raise RuntimeError(f"{what}: NVML error {rc}")
+
+    def nvmlInit(self):
+        self._ok(self.lib.nvmlInit_v2(), "nvmlInit_v2")
+
+    def nvmlDeviceGetHandleByPciBusId(self, bus):
+        h = self.ct.c_void_p()
+        self._ok(self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), self.ct.byref(h)), "handle by bus id")
+        return h
+
+    def nvmlDeviceGetHandleByIndex(self, i):
+        h = self.ct.c_void_p()
+        self._ok(self.lib.nvmlDeviceGetHandleByIndex_v2(self.ct.c_uint(i), self.ct.byref(h)), "handle by index")
+        return h
+
+    def nvmlDeviceGetClockInfo(self, h, kind):
+        v = self.ct.c_uint()
+        self._ok(self.lib.nvmlDeviceGetClockInfo(h, self.ct.c_int(kind), self.ct.byref(v)), "clock")
+        return v.value
+
+    def nvmlDeviceGetMaxClockInfo(self, h, kind):
+        v = self.ct.c_uint()
+        self._ok(self.lib.nvmlDeviceGetMaxClockInfo(h, self.ct.c_int(kind), self.ct.byref(v)), "max clock")
+        return v.value
+
+    def nvmlDeviceGetCurrentClocksEventReasons(self, h):
+        v = self.ct.c_ulonglong()
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self._ok(fn(h, self.ct.byref(v)), "clock event reasons")
+        return v.value
+
+
 class Clocks:
     """SM clock and throttle-reason sampling during the timed region: NVML queries (read-only) from
     a thread every 5 ms, so that even a region of a few tens of milliseconds gets many samples;
@@ -158,8 +208,11 @@ class Clocks:
         self.samples = []          # (sm_mhz, max_mhz, set of reasons)
 
     def _nvml_handle(self):
-        import pynvml
         import torch
+        try:
+            import pynvml
+        except ImportError:   # the driver's NVML library through ctypes, same read-only queries
+            pynvml = _CNvml()
         pynvml.nvmlInit()
         try:
             bus = torch.cuda.get_device_properties(self.dev).pci_bus_id
