@@ -16,8 +16,12 @@
 // tcgen05.st); the operator (hi, lo) sits in shared memory in the K-major canonical layout; one
 // thread issues D = X_hi Op_hi + X_hi Op_lo + X_lo Op_hi (3 x K/8 MMAs of 128 x NPP x 8) and
 // commits them to an mbarrier; the accumulators come back with tcgen05.ld and go through shared
-// memory so that the update and the trace writes are coalesced.  The waits are bounded (~1 s of SM
-// clock); on a timeout the block reports through the device error word and stops.
+// memory so that the update and the trace writes are coalesced.  Two staging buffers: the copies
+// of tile i+1 (state, side data, inbox values) are issued as soon as tile i's flux phase is done,
+// so they land while tile i's operands, products, update and traces run; tile i's residual /
+// history rows are loaded into registers before its products and used by its update.  The waits
+// are bounded (~1 s of SM clock); on a timeout the block reports through the device error word,
+// lets its copies in flight complete and stops.
 #include <cuda_runtime.h>
 
 #include "kcommon.cuh"
@@ -85,19 +89,22 @@ struct TetTC {
   static constexpr int XHI = 0, XLO = KP, DCOL = 2 * KP;  // tensor-memory columns
   static constexpr int TCOLS = pow2_cols(DCOL + NPP);
   static_assert(DCOL + NPP <= 512, "tile does not fit tensor memory");
+  static constexpr int NJ = (NP + 3) / 4;                 // values per thread of a (element, field) row
   static constexpr int OPB = NPP * KP * 4;                // one operator copy (bytes)
   static constexpr int S_OPH = 0, S_OPL = a128(OPB);
-  static constexpr int S_Q = S_OPL + a128(OPB);           // [TE][4][NP] state
-  static constexpr int S_R = S_Q + a128(TE * 4 * NP * 4);  // [TE][4][NP] rhs (MRC: new state)
+  static constexpr int S_R = S_OPL + a128(OPB);            // [TE][4][NP] rhs (MRC: new state); -w_a before
   static constexpr int S_F = S_R + a128(TE * 4 * NP * 4);  // [TE][4 comps][KL + 1] lattice fluxes
-  static constexpr int S_G = S_F + a128(TE * 4 * (KL + 1) * 4);   // [TE][16]: G[9], J, -, -, c^2
-  static constexpr int S_SD = S_G + TE * 16 * 4;          // [TE][4] code, [TE][4] nbr, [TE][4] tau, [TE] element
-  static constexpr int S_I = S_SD + TE * 13 * 4;          // tperm [6][NFN], fnode [4][NFN]
-  static constexpr int S_N = a128(S_I + 10 * NFN * 4);    // [TE][4] float4 (n, J^s) of the faces
-  static constexpr int S_IN = S_N + TE * 4 * 16;          // [TE][4][2][NFN] inbox lattice values
-  static constexpr int S_AUX = a128(S_IN + TE * 8 * NFN * 4);   // [2][TE][4][NP] residual / history
-  static constexpr int S_BAR = S_AUX + 2 * TE * 4 * NP * 4;
+  static constexpr int S_I = S_F + a128(TE * 4 * (KL + 1) * 4);   // tperm [6][NFN], fnode [4][NFN]
+  static constexpr int S_BUF = a128(S_I + 10 * NFN * 4);   // two tile buffers: tile i+1 lands while i runs
+  static constexpr int B_Q = 0;                             // [TE][4][NP] state
+  static constexpr int B_G = a128(TE * 4 * NP * 4);         // [TE][16]: G[9], J, -, -, c^2
+  static constexpr int B_SD = B_G + TE * 16 * 4;            // [TE][4] code, [TE][4] nbr, [TE][4] tau, [TE] element
+  static constexpr int B_N = a128(B_SD + TE * 13 * 4);      // [TE][4] float4 (n, J^s) of the faces
+  static constexpr int B_IN = B_N + TE * 4 * 16;            // [TE][4][2][NFN] inbox lattice values
+  static constexpr int BUFB = a128(B_IN + TE * 8 * NFN * 4);
+  static constexpr int S_BAR = S_BUF + 2 * BUFB;
   static constexpr int SMEM = S_BAR + 16;
+  static_assert(SMEM <= 227 * 1024, "tet tile buffers exceed shared memory");
 };
 
 __device__ __forceinline__ void cpa4(void* sdst, const void* gsrc) {
@@ -107,27 +114,92 @@ __device__ __forceinline__ void cpa16(void* sdst, const void* gsrc) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(sdst)), "l"(gsrc) : "memory");
 }
 
+// One tile's staging buffer in shared memory.
+template <int N>
+struct TetBuf {
+  float* q;
+  float* g;
+  int *code, *nb, *e;
+  float* tau;
+  float4* n;
+  float* in;
+  __device__ TetBuf(unsigned char* base) {
+    using C = TetTC<N>;
+    q = reinterpret_cast<float*>(base + C::B_Q);
+    g = reinterpret_cast<float*>(base + C::B_G);
+    code = reinterpret_cast<int*>(base + C::B_SD);
+    nb = code + 4 * C::TE;
+    tau = reinterpret_cast<float*>(nb + 4 * C::TE);
+    e = reinterpret_cast<int*>(tau + 4 * C::TE);
+    n = reinterpret_cast<float4*>(base + C::B_N);
+    in = reinterpret_cast<float*>(base + C::B_IN);
+  }
+};
+
+// Every global read of a tile except the residual / history, as asynchronous copies (one commit
+// group): state, metrics and c^2, side data, face (n, J^s), inbox lattice values.  Rows
+// (element, field) of NP contiguous values, 4 threads per row; absent elements are zero-filled.
+template <int N>
+__device__ __forceinline__ void tet_issue_tile(const Args& A, const TetBuf<N>& B, int tid) {
+  using C = TetTC<N>;
+  constexpr int NP = C::NP, NFN = C::NFN, NQ = C::NQ, TE = C::TE;
+  {
+    const int row = tid >> 2, sub = tid & 3, el = row >> 2, f = row & 3;
+    const int e = B.e[el];
+    if (e >= 0) {
+      const float* src = A.q + f * A.ndof + A.dof_off + (int64_t)e * NP;
+      for (int n = sub; n < NP; n += 4) cpa4(B.q + row * NP + n, src + n);
+    } else {
+      for (int n = sub; n < NP; n += 4) B.q[row * NP + n] = 0.f;
+    }
+  }
+  if (tid < TE * 16) {
+    const int el = tid >> 4, i = tid & 15;
+    const int e = B.e[el];
+    if (i < 13) {
+      if (e >= 0) cpa4(B.g + el * 16 + i, i < 12 ? A.geo + (int64_t)e * 12 + i : A.c2 + e);
+      else B.g[el * 16 + i] = i == 9 ? 1.f : 0.f;
+    }
+  }
+  if (tid < TE * 4) {
+    const int e = B.e[tid >> 2];
+    if (e >= 0) {
+      const int64_t gs = A.side_off + (int64_t)e * 4 + (tid & 3);
+      cpa4(B.code + tid, A.code + gs);
+      cpa4(B.nb + tid, A.nbr + gs);
+      cpa4(B.tau + tid, A.tau + gs);
+      cpa16(B.n + tid, A.sgeo2 + ((int64_t)e * 4 + (tid & 3)) * NQ);
+    } else {
+      B.code[tid] = 0;
+      B.nb[tid] = -1;
+      B.tau[tid] = 1.f;
+      B.n[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  {   // inbox lattice slots: rows (element, face, plane) of NFN values, 2 threads per row
+    const int row = tid >> 1, sub = tid & 1, el = row >> 3, f = (row >> 1) & 3, pl = row & 1;
+    const int e = B.e[el];
+    if (e >= 0) {
+      const float* src = A.tin + pl * A.plane + (A.side_off + (int64_t)e * 4 + f) * NQ;
+      for (int c = sub; c < NFN; c += 2) cpa4(B.in + row * NFN + c, src + c);
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 template <int N, int MODE>
 __global__ void __launch_bounds__(512, 1) tet_tc_kernel(Args A) {
   using C = TetTC<N>;
   constexpr int NP = C::NP, NFN = C::NFN, NQ = C::NQ, TE = C::TE, NT = C::NT, KV = C::KV, KL = C::KL, KP = C::KP,
-                NPP = C::NPP;
+                NPP = C::NPP, NJ = C::NJ;
+  constexpr int NAUX = MODE == MODE_STAGE ? 1 : (MODE == MODE_MRC || MODE == MODE_MRF) ? 2 : 0;
   extern __shared__ __align__(1024) unsigned char sm[];
   float* opH = reinterpret_cast<float*>(sm + C::S_OPH);
   float* opL = reinterpret_cast<float*>(sm + C::S_OPL);
-  float* sq = reinterpret_cast<float*>(sm + C::S_Q);
   float* sr = reinterpret_cast<float*>(sm + C::S_R);
   float* sfc = reinterpret_cast<float*>(sm + C::S_F);
-  float* sg = reinterpret_cast<float*>(sm + C::S_G);
-  int* scode = reinterpret_cast<int*>(sm + C::S_SD);
-  int* snb = scode + 4 * TE;
-  float* stau = reinterpret_cast<float*>(snb + 4 * TE);
-  int* se = reinterpret_cast<int*>(stau + 4 * TE);
   int* stp = reinterpret_cast<int*>(sm + C::S_I);
   int* sfn = stp + 6 * NFN;
-  float4* sn = reinterpret_cast<float4*>(sm + C::S_N);
-  float* sin_ = reinterpret_cast<float*>(sm + C::S_IN);
-  float* saux = reinterpret_cast<float*>(sm + C::S_AUX);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + C::S_BAR);
   unsigned* stm = reinterpret_cast<unsigned*>(sm + C::S_BAR + 8);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -167,6 +239,18 @@ __global__ void __launch_bounds__(512, 1) tet_tc_kernel(Args A) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  const int ntiles = (A.K + TE - 1) / TE;
+  auto tile_elem = [&](int tile, int i) -> int {
+    const int li = tile * TE + i;
+    return tile < ntiles && li < A.K ? (A.elist ? A.elist[li] : li) : -1;
+  };
+  {   // the first tile's copies start before the block's set-up completes
+    TetBuf<N> B0(sm + C::S_BUF);
+    if (tid < TE) B0.e[tid] = tile_elem(blockIdx.x, tid);
+    __syncthreads();
+    if (blockIdx.x < ntiles) tet_issue_tile<N>(A, B0, tid);
+  }
+  int pe = tid < TE ? tile_elem(blockIdx.x + gridDim.x, tid) : -1;   // element ids one tile ahead
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // operator visible to the tensor cores
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -180,85 +264,37 @@ __global__ void __launch_bounds__(512, 1) tet_tc_kernel(Args A) {
   const int q4 = warp & 3, wq = warp >> 2;   // TMEM lane quarter of this warp; column share
   const unsigned lanebase = tb + ((unsigned)(q4 * 32) << 16);
 
-  const int ntiles = (A.K + TE - 1) / TE;
-  for (int tile = blockIdx.x; tile < ntiles && !bail; tile += gridDim.x) {
-    const int li0 = tile * TE;
-    if (tid < TE) se[tid] = li0 + tid < A.K ? (A.elist ? A.elist[li0 + tid] : li0 + tid) : -1;
-    __syncthreads();
-    // ---- every global read of the tile, as asynchronous copies completing together: state,
-    // metrics and c^2, side data, face (n, J^s), inbox lattice values, residual / history.
-    // Rows (element, field) of NP contiguous values, 4 threads per row.
-    constexpr int NAUX = MODE == MODE_STAGE ? 1 : (MODE == MODE_MRC || MODE == MODE_MRF) ? 2 : 0;
-    {
-      const int row = tid >> 2, sub = tid & 3, el = row >> 2, f = row & 3;
-      const int e = se[el];
-      if (e >= 0) {
-        const int64_t g0 = f * A.ndof + A.dof_off + (int64_t)e * NP;
-        for (int n = sub; n < NP; n += 4) {
-          cpa4(sq + row * NP + n, A.q + g0 + n);
-          if (NAUX > 0) cpa4(saux + row * NP + n, (MODE == MODE_STAGE ? A.res : A.h1) + g0 + n);
-          if (NAUX > 1) cpa4(saux + TE * 4 * NP + row * NP + n, A.h2 + g0 + n);
-        }
-      } else {
-        for (int n = sub; n < NP; n += 4) sq[row * NP + n] = 0.f;
-      }
-    }
-    if (tid < TE * 16) {
-      const int el = tid >> 4, i = tid & 15;
-      const int e = se[el];
-      if (i < 13) {
-        if (e >= 0) cpa4(sg + el * 16 + i, i < 12 ? A.geo + (int64_t)e * 12 + i : A.c2 + e);
-        else sg[el * 16 + i] = i == 9 ? 1.f : 0.f;
-      }
-    }
-    if (tid < TE * 4) {
-      const int e = se[tid >> 2];
-      if (e >= 0) {
-        const int64_t gs = A.side_off + (int64_t)e * 4 + (tid & 3);
-        cpa4(scode + tid, A.code + gs);
-        cpa4(snb + tid, A.nbr + gs);
-        cpa4(stau + tid, A.tau + gs);
-        cpa16(sn + tid, A.sgeo2 + ((int64_t)e * 4 + (tid & 3)) * NQ);
-      } else {
-        scode[tid] = 0;
-        snb[tid] = -1;
-        stau[tid] = 1.f;
-        sn[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-    }
-    {   // inbox lattice slots: rows (element, face, plane) of NFN values, 2 threads per row
-      const int row = tid >> 1, sub = tid & 1, el = row >> 3, f = (row >> 1) & 3, pl = row & 1;
-      const int e = se[el];
-      if (e >= 0) {
-        const float* src = A.tin + pl * A.plane + (A.side_off + (int64_t)e * 4 + f) * NQ;
-        for (int c = sub; c < NFN; c += 2) cpa4(sin_ + row * NFN + c, src + c);
-      }
-    }
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+  int it = 0;
+  for (int tile = blockIdx.x; tile < ntiles && !bail; tile += gridDim.x, ++it) {
+    const TetBuf<N> B(sm + C::S_BUF + (it & 1) * C::BUFB);
+    const TetBuf<N> BN(sm + C::S_BUF + ((it & 1) ^ 1) * C::BUFB);
+    const int next = tile + gridDim.x;
+    if (tid < TE) BN.e[tid] = pe;
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     // ---- per element: 16 threads; fluxes at the 4 NFN face-lattice nodes (strong form, scaled
     // by J^s, component planes) and the metric-transformed velocities -w_a (into sr)
     {
       const int el = tid >> 4, t16 = tid & 15;
-      const int e = se[el];
-      const float* qe = sq + el * 4 * NP;
+      const int e = B.e[el];
+      const float* qe = B.q + el * 4 * NP;
       float* fe = sfc + el * 4 * (KL + 1);
       for (int y = t16; y < KL; y += 16) {
         const int f = y / NFN, nl = y - f * NFN;
         float fp = 0.f, fu = 0.f;
-        const float4 sgv = sn[el * 4 + f];   // (n, J^s), constant on the face
+        const float4 sgv = B.n[el * 4 + f];   // (n, J^s), constant on the face
         if (e >= 0) {
           const int node = sfn[y];
           const float pm = qe[node];
           const float unm = sgv.x * qe[NP + node] + sgv.y * qe[2 * NP + node] + sgv.z * qe[3 * NP + node];
-          const int nb = snb[el * 4 + f];
+          const int nb = B.nb[el * 4 + f];
           float P = 0.f, UN = 0.f;
           if (nb >= 0) {
-            const int ci = stp[scode[el * 4 + f] * NFN + nl];
-            P = sin_[(el * 8 + f * 2) * NFN + ci];
-            UN = sin_[(el * 8 + f * 2 + 1) * NFN + ci];
+            const int ci = stp[B.code[el * 4 + f] * NFN + nl];
+            P = B.in[(el * 8 + f * 2) * NFN + ci];
+            UN = B.in[(el * 8 + f * 2 + 1) * NFN + ci];
           }
-          const float ta = stau[el * 4 + f];
+          const float ta = B.tau[el * 4 + f];
           flux(nb < 0, pm, unm, P, UN, A.tau_scale * ta, A.tau_scale / ta, false, fp, fu);
         }
         fe[y] = sgv.w * fp;
@@ -266,7 +302,7 @@ __global__ void __launch_bounds__(512, 1) tet_tc_kernel(Args A) {
         fe[2 * (KL + 1) + y] = sgv.w * fu * sgv.y;
         fe[3 * (KL + 1) + y] = sgv.w * fu * sgv.z;
       }
-      const float* G = sg + el * 16;
+      const float* G = B.g + el * 16;
       float* we = sr + el * KV;
       for (int m = t16; m < NP; m += 16) {
         const float u = qe[NP + m], v = qe[2 * NP + m], w = qe[3 * NP + m];
@@ -275,17 +311,34 @@ __global__ void __launch_bounds__(512, 1) tet_tc_kernel(Args A) {
       }
     }
     __syncthreads();
+    // ---- the next tile's copies run while this tile's products and update proceed; the residual /
+    // history rows of this tile come into registers (used by the update)
+    if (next < ntiles) tet_issue_tile<N>(A, BN, tid);
+    if (tid < TE) pe = tile_elem(next + gridDim.x, tid);
+    const int urow = tid >> 2, usub = tid & 3, uel = urow >> 2, uf = urow & 3;
+    const int ue = B.e[uel];
+    const int64_t ug0 = uf * A.ndof + A.dof_off + (int64_t)(ue >= 0 ? ue : 0) * NP;
+    float ax[NAUX > 0 ? NAUX : 1][NJ];
+    if (NAUX > 0) {
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const int n = usub + 4 * j;
+        const bool ok = ue >= 0 && n < NP;
+        ax[0][j] = ok ? (MODE == MODE_STAGE ? A.res : A.h1)[ug0 + n] : 0.f;
+        if (NAUX > 1) ax[NAUX - 1][j] = ok ? A.h2[ug0 + n] : 0.f;
+      }
+    }
     // ---- X rows (hi, lo) into tensor memory: lane r = 4 el + field, 8-column chunks shared by
     // the four warps of each lane quarter.  p row: [-w_r, -w_s, -w_t, F_p / J];
     // u_d rows: [-c^2 G[a][d] p (a = r,s,t), c^2 F_d / J]
     {
       const int row = q4 * 32 + lane, el = row >> 2, fld = row & 3;
-      const float* G = sg + el * 16;
+      const float* G = B.g + el * 16;
       const float iJ = 1.f / G[9], c2 = G[12];
       const float sl = fld == 0 ? iJ : c2 * iJ;
       const int d = fld == 0 ? 0 : fld - 1;
       const float cf0 = -c2 * G[d], cf1 = -c2 * G[3 + d], cf2 = -c2 * G[6 + d];
-      const float* wsrc = fld == 0 ? sr + el * KV : sq + el * 4 * NP;   // volume source row
+      const float* wsrc = fld == 0 ? sr + el * KV : B.q + el * 4 * NP;   // volume source row
       const float* fsrc = sfc + row * (KL + 1) - KV;                      // lift source row
       for (int ch = wq; ch < KP / 8; ch += 4) {
         unsigned vh[8], vl[8];
@@ -347,34 +400,32 @@ __global__ void __launch_bounds__(512, 1) tet_tc_kernel(Args A) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     // ---- update: rows (element, field), 4 threads per row
-    {
-      const int row = tid >> 2, sub = tid & 3, el = row >> 2, f = row & 3;
-      const int e = se[el];
-      if (e >= 0) {
-        const int64_t g0 = f * A.ndof + A.dof_off + (int64_t)e * NP;
-        for (int n = sub; n < NP; n += 4) {
-          const int x = row * NP + n;
-          const int64_t id = g0 + n;
-          const float rv = sr[x], qo = sq[x];
-          if (MODE == MODE_RHS) {
-            A.rhs[id] = rv;
-          } else if (MODE == MODE_STAGE) {
-            const float rr = A.a * saux[x] + (A.dtE ? A.dtE[e] : A.dt) * rv;
-            const float qn = qo + A.b * rr;
-            A.res[id] = rr;
-            A.qout[id] = qn;
-            sq[x] = qn;
-          } else {   // MRC / MRF: AB3; MRC: prediction -> sq, new state -> sr
-            const float r1 = saux[x], r2 = saux[TE * 4 * NP + x];
-            A.hw[id] = rv;
-            const float qn = qo + A.ab0 * rv + A.ab1 * r1 + A.ab2 * r2;
-            A.qout[id] = qn;
-            if (MODE == MODE_MRC) {
-              sq[x] = qo + A.pr0 * rv + A.pr1 * r1 + A.pr2 * r2;
-              sr[x] = qn;
-            } else {
-              sq[x] = qn;
-            }
+    if (ue >= 0) {
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const int n = usub + 4 * j;
+        if (n >= NP) break;
+        const int x = urow * NP + n;
+        const int64_t id = ug0 + n;
+        const float rv = sr[x], qo = B.q[x];
+        if (MODE == MODE_RHS) {
+          A.rhs[id] = rv;
+        } else if (MODE == MODE_STAGE) {
+          const float rr = A.a * ax[0][j] + (A.dtE ? A.dtE[ue] : A.dt) * rv;
+          const float qn = qo + A.b * rr;
+          A.res[id] = rr;
+          A.qout[id] = qn;
+          B.q[x] = qn;
+        } else {   // MRC / MRF: AB3; MRC: prediction -> B.q, new state -> sr
+          const float r1 = ax[0][j], r2 = ax[NAUX - 1][j];
+          A.hw[id] = rv;
+          const float qn = qo + A.ab0 * rv + A.ab1 * r1 + A.ab2 * r2;
+          A.qout[id] = qn;
+          if (MODE == MODE_MRC) {
+            B.q[x] = qo + A.pr0 * rv + A.pr1 * r1 + A.pr2 * r2;
+            sr[x] = qn;
+          } else {
+            B.q[x] = qn;
           }
         }
       }
@@ -383,18 +434,18 @@ __global__ void __launch_bounds__(512, 1) tet_tc_kernel(Args A) {
     // ---- traces of the new state (MRC: prediction, then new state) into the neighbours' inboxes
     if (MODE != MODE_RHS) {
       const int el = tid >> 4, t16 = tid & 15;
-      const int e = se[el];
+      const int e = B.e[el];
 #pragma unroll 1
       for (int pass = 0; pass < (MODE == MODE_MRC ? 2 : 1); ++pass) {
-        const float* qe = (pass ? sr : sq) + el * 4 * NP;
+        const float* qe = (pass ? sr : B.q) + el * 4 * NP;
         float* tout = pass ? A.tout2 : A.tout;
         for (int y = t16; y < KL && e >= 0; y += 16) {
           const int f = y / NFN, nl = y - f * NFN;
-          const int nb = snb[el * 4 + f];
+          const int nb = B.nb[el * 4 + f];
           if (nb < 0) continue;
           const int node = sfn[y];
-          const float4 sgv = sn[el * 4 + f];
-          const int ci = stp[scode[el * 4 + f] * NFN + nl];
+          const float4 sgv = B.n[el * 4 + f];
+          const int ci = stp[B.code[el * 4 + f] * NFN + nl];
           tout[(int64_t)nb * NQ + ci] = qe[node];
           tout[A.plane + (int64_t)nb * NQ + ci] =
               sgv.x * qe[NP + node] + sgv.y * qe[2 * NP + node] + sgv.z * qe[3 * NP + node];
@@ -403,6 +454,8 @@ __global__ void __launch_bounds__(512, 1) tet_tc_kernel(Args A) {
     }
     __syncthreads();
   }
+  // copies still in flight (a bail-out, or none) complete before the block exits
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   if (bail) {   // report; wait (bounded) for the MMAs in flight before freeing tensor memory
     if (tid == 0) atomicOr(A.err, 1);
     bar_wait(bar, phase);
