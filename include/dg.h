@@ -71,7 +71,7 @@ typedef struct {
                               pyramid base (r,s) lexicographic at t=-1, apex (-1,-1,1);
                               tet (-1,-1,-1),(1,-1,-1),(-1,1,-1),(-1,-1,1) */
   const double *c2[4];     /* host, [nelem] squared wave speed per element (> 0) */
-  int N;                   /* polynomial order, 1..7 */
+  int N;                   /* polynomial order, 1..9 */
   int hex_basis;           /* 0 = GL nodes; 1 = SEM: GLL nodes and GLL points on every quad face */
   int pyr_form;            /* 0 = skew-symmetric, 1 = strong (identical results, Sec. 2.2) */
   double tau_scale;        /* 1 = upwind, 0 = central flux */
@@ -82,8 +82,9 @@ typedef struct {
                               16-bit hi + lo split operands on the tensor cores, FP32 accumulation
                               (about 2^-17 / 2^-22 relative per product); hexahedra, wedges and all
                               face terms stay FP32.  1, 2 apply on meshes with the lattice face
-                              exchange (no wedge triangle face against a tet or pyramid); the
-                              adjoint refuses them (DG_ENOTSUP) */
+                              exchange (no wedge triangle face against a tet or pyramid), to types
+                              with at most 256 nodes (pyramids at N >= 8 stay FP32); the adjoint
+                              refuses them (DG_ENOTSUP) */
   int integrator;          /* nlevels = 2: 0 = multi-rate Adams-Bashforth 3 (default),
                               1 = multi-rate LSRK(5,4) (see dg_step) */
 } dg_mesh_desc;

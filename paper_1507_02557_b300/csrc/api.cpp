@@ -67,7 +67,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* d, void* stream, dg_mesh** out) {
   if (!d || !out) return DG_EINVAL;
   *out = nullptr;
   if (d->N < 1 || d->N > dgk::MAXN) {
-    g_err = "N must be in 1..7";
+    g_err = "N must be in 1..9";
     return DG_ENOTSUP;
   }
   if ((d->hex_basis != 0 && d->hex_basis != 1) || d->nlevels > 2 || d->precision < 0 || d->precision > 2) {

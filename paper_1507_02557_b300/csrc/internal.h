@@ -11,7 +11,7 @@
 
 namespace dgk {
 
-constexpr int MAXN = 7;       // kernels are instantiated for N = 1..MAXN
+constexpr int MAXN = 9;       // kernels are instantiated for N = 1..MAXN
 constexpr int NCODES = 8;     // face orientation codes (6 used for triangles)
 
 // Device data of one element type.

@@ -30,8 +30,8 @@ struct HexCfg {
   static constexpr int EPB = TPE >= 256 ? 1 : 256 / TPE;
   static constexpr int NT = TPE * EPB;
   // resident blocks per SM the register allocation aims at (measured best: N = 5..7: 8, 5, 3; one
-  // more block at N = 7 spills enough to lose)
-  static constexpr int MINB = N >= 7 ? 3 : N == 6 ? 5 : N == 5 ? 8 : 1;
+  // more block at N = 7 spills enough to lose; N = 8, 9: blocks of 736 / 1024 threads, one)
+  static constexpr int MINB = N >= 8 ? 1 : N == 7 ? 3 : N == 6 ? 5 : N == 5 ? 8 : 1;
 };
 
 // a x + y on the four fields as two packed FP32 pair FMAs (round to nearest, the same values as
@@ -87,7 +87,6 @@ __global__ void __launch_bounds__(HexCfg<N>::NT, HexCfg<N>::MINB) hex_kernel(Arg
   for (int i = threadIdx.x; i < 8 * NQ; i += blockDim.x) s_perm[i] = A.perm[i];
   const int64_t base = A.dof_off + e * NP;
   if (valid && tid < NP) {
-#pragma unroll
     s_q4[le][tid] = make_float4(A.q[base + tid], A.q[A.ndof + base + tid], A.q[2 * A.ndof + base + tid],
                                 A.q[3 * A.ndof + base + tid]);
   }
@@ -194,8 +193,8 @@ __global__ void __launch_bounds__(HexCfg<N>::NT, HexCfg<N>::MINB) hex_kernel(Arg
       } else {
         const float4 qo = s_q4[le][tid];
         const float qv[4] = {qo.x, qo.y, qo.z, qo.w};
-#pragma unroll
         const float dte = A.dtE ? A.dtE[e] : A.dt;
+#pragma unroll
         for (int fl = 0; fl < 4; ++fl) {
           const int64_t id = fl * A.ndof + base + tid;
           float r = A.a * A.res[id] + dte * rhs[fl];
@@ -1020,6 +1019,9 @@ struct GenCfg {
   static constexpr int NP = np_of(T, N), NQ = (N + 1) * (N + 1), NF = T == DG_TET ? 4 : 5;
   static constexpr int NC = T == DG_WEDGE ? (N + 1) * (N + 1) * (N + 1) : 1;
   static constexpr int NT = 128;
+  // volume intermediates [7][SW] in dynamic shared memory (the wedge's exceed the static limit at N = 9)
+  static constexpr int SW = T == DG_WEDGE ? NC : (T == DG_PYR ? NP : 3 * NP / 7 + 1);
+  static constexpr int DYN = 7 * SW * 4;
 };
 
 template <int T, int N, int MODE>
@@ -1029,7 +1031,8 @@ __global__ void __launch_bounds__(128) gen_kernel(Args A) {
   __shared__ float s_q[4][NP];
   __shared__ float s_r[4][NP];
   __shared__ float s_F[NF][4][NQ];
-  __shared__ float s_w[7][T == DG_WEDGE ? NC : (T == DG_PYR ? NP : 3 * NP / 7 + 1)];
+  extern __shared__ __align__(16) float gen_dyn[];
+  float(*s_w)[C::SW] = reinterpret_cast<float(*)[C::SW]>(gen_dyn);
   __shared__ float s_e[12];
   __shared__ int s_code[NF];
 
@@ -1200,8 +1203,8 @@ __global__ void __launch_bounds__(128) gen_kernel(Args A) {
 #pragma unroll
         for (int fl = 0; fl < 4; ++fl) A.rhs[fl * A.ndof + base + n] = r[fl];
       } else {
-#pragma unroll
         const float dte = A.dtE ? A.dtE[e] : A.dt;
+#pragma unroll
         for (int fl = 0; fl < 4; ++fl) {
           const int64_t id = fl * A.ndof + base + n;
           float rr = A.a * A.res[id] + dte * r[fl];
@@ -1367,8 +1370,14 @@ static void launch_hex_n(const Args& A, cudaStream_t s) {
 
 template <int T, int N, int MODE>
 static void launch_gen_n(const Args& A, cudaStream_t s) {
+  using C = GenCfg<T, N>;
   if (A.K == 0) return;
-  gen_kernel<T, N, MODE><<<A.K, 128, 0, s>>>(A);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(gen_kernel<T, N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::DYN);
+    attr = true;
+  }
+  gen_kernel<T, N, MODE><<<A.K, C::NT, C::DYN, s>>>(A);
 }
 
 template <int MODE>
@@ -1421,7 +1430,8 @@ static void launch_type(dg_mesh* m, const Args& A0, int t) {
   // precision > 0: the volume products of tets and pyramids on the tensor cores in split 16-bit
   // form, then the type's warp kernel with those products as input (lattice-exchange meshes)
   Args A = A0;
-  const bool tcv = m->precision > 0 && (t == DG_TET || t == DG_PYR) && MODE != MODE_TRACE && m->tri_lat;
+  const bool tcv = m->precision > 0 && (t == DG_TET || t == DG_PYR) && MODE != MODE_TRACE && m->tri_lat &&
+                   m->prec[t == DG_TET ? 0 : 1].y != nullptr;
   if (tcv) launch_prec_volume(m, t, A, s);
   switch (m->N) {
 #define DG_CASE(NN)                                                   \
@@ -1433,7 +1443,7 @@ static void launch_type(dg_mesh* m, const Args& A0, int t) {
     else if (t == DG_PYR) launch_gen_n<DG_PYR, NN, (MODE > 2 ? 1 : MODE)>(A, s);       \
     else launch_gen_n<DG_TET, NN, (MODE > 2 ? 1 : MODE)>(A, s);                        \
     break;
-    DG_CASE(1) DG_CASE(2) DG_CASE(3) DG_CASE(4) DG_CASE(5) DG_CASE(6) DG_CASE(7)
+    DG_CASE(1) DG_CASE(2) DG_CASE(3) DG_CASE(4) DG_CASE(5) DG_CASE(6) DG_CASE(7) DG_CASE(8) DG_CASE(9)
 #undef DG_CASE
     default: break;
   }
@@ -1602,7 +1612,7 @@ cudaError_t launch_energy(dg_mesh* m, const float* q, double* acc) {
     if (A[2].K) energy_kernel<DG_PYR, NN><<<egrid(2), 256, 0, s>>>(A[2], nullptr, acc);              \
     if (A[3].K) energy_kernel<DG_TET, NN><<<egrid(3), 256, 0, s>>>(A[3], m->tet_chol_dev, acc);      \
     break;
-    DG_CASE(1) DG_CASE(2) DG_CASE(3) DG_CASE(4) DG_CASE(5) DG_CASE(6) DG_CASE(7)
+    DG_CASE(1) DG_CASE(2) DG_CASE(3) DG_CASE(4) DG_CASE(5) DG_CASE(6) DG_CASE(7) DG_CASE(8) DG_CASE(9)
 #undef DG_CASE
     default: break;
   }

@@ -82,7 +82,11 @@ struct G2 {
   static constexpr int WXN = WPLANE ? NQ : NC;
   static constexpr int WV0 = 2 * NT * N1 + 2 * WXN, WV1 = 2 * NT + 3 * N1 * N1 + 3 * NQ;
   static constexpr int WV = T == DG_WEDGE ? (WV0 > WV1 ? WV0 : WV1) : NP;
-  static constexpr int WB = NP + WV + NFX + 2 * NTRI * NFN + (T == DG_PYR ? NKL * N1 + NQ : 0);   // F4: NFX
+  static constexpr int WB0 = NP + WV + NFX + 2 * NTRI * NFN + (T == DG_PYR ? NKL * N1 + NQ : 0);   // F4: NFX
+  // pyramid: the volume products' scratch (3 NIT floats from F4 on) may run past the face buffers
+  // (N = 9): extra float4 at the end of the warp's buffer
+  static constexpr int PEX0 = T == DG_PYR ? 3 * NIT - 4 * (WB0 - NP - WV) : 0;
+  static constexpr int WB = WB0 + (PEX0 > 0 ? (PEX0 + 3) / 4 : 0);
   // tet / pyramid: the volume operator transposed, (D^T)[m][n] = D[n][m] as float4, follows the
   // operators in global memory at float offset OPS_T (host layout size NOPS)
   static constexpr int OPS_T = ((OPS + 3) / 4) * 4;
@@ -902,6 +906,9 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
 template <int T, int N, int MODE>
 static bool launch_one(const Args& A, cudaStream_t s) {
   using C = G2<T, N>;
+  if constexpr (N > 4 && (MODE == MODE_MRC || MODE == MODE_MRF)) {
+    return false;   // the fused multi-rate modes exist for N <= 4 only (not instantiated above)
+  } else {
   if (A.nops2 != C::NOPS) return false;   // host operator layout of another (type, N)
   static int blocks = 0;   // persistent grid: resident blocks per SM x SMs (computed once)
   if (blocks == 0) {
@@ -919,6 +926,7 @@ static bool launch_one(const Args& A, cudaStream_t s) {
   const int grid = (int)(need < blocks ? need : blocks);
   gen2_kernel<T, N, MODE><<<grid, C::NW * 32, C::SMEM, s>>>(A);
   return true;
+  }
 }
 
 template <int MODE>
@@ -932,7 +940,7 @@ bool launch_gen2(int t, int N, const Args& A, cudaStream_t s) {
     if (t == DG_PYR) return launch_one<DG_PYR, NN, MODE>(A, s);            \
     if (t == DG_WEDGE) return launch_one<DG_WEDGE, NN, MODE>(A, s);        \
     return false;
-    G2_CASE(1) G2_CASE(2) G2_CASE(3) G2_CASE(4) G2_CASE(5) G2_CASE(6) G2_CASE(7)
+    G2_CASE(1) G2_CASE(2) G2_CASE(3) G2_CASE(4) G2_CASE(5) G2_CASE(6) G2_CASE(7) G2_CASE(8) G2_CASE(9)
 #undef G2_CASE
     default: return false;
   }

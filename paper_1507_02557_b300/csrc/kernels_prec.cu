@@ -309,7 +309,7 @@ cudaError_t launch_prec_volume(dg_mesh* m, int t, Args& A, cudaStream_t s) {
     if (t == DG_TET) bf ? pack_n<DG_TET, NN, true>(A, P, s, sms) : pack_n<DG_TET, NN, false>(A, P, s, sms); \
     else bf ? pack_n<DG_PYR, NN, true>(A, P, s, sms) : pack_n<DG_PYR, NN, false>(A, P, s, sms);             \
     break;
-    PK_CASE(1) PK_CASE(2) PK_CASE(3) PK_CASE(4) PK_CASE(5) PK_CASE(6) PK_CASE(7)
+    PK_CASE(1) PK_CASE(2) PK_CASE(3) PK_CASE(4) PK_CASE(5) PK_CASE(6) PK_CASE(7) PK_CASE(8) PK_CASE(9)
 #undef PK_CASE
     default: return cudaErrorInvalidValue;
   }

@@ -153,8 +153,10 @@ extern "C" dg_status dg_energy_noalloc(dg_mesh* m, const float* q, double* E) {
     case 5: launch_parts<5>(m, q, part); break;
     case 6: launch_parts<6>(m, q, part); break;
     case 7: launch_parts<7>(m, q, part); break;
+    case 8: launch_parts<8>(m, q, part); break;
+    case 9: launch_parts<9>(m, q, part); break;
     default:
-      dg_set_last_error("dg_energy_noalloc: N must be in 1..7");
+      dg_set_last_error("dg_energy_noalloc: N must be in 1..9");
       return DG_ENOTSUP;
   }
   ordered_sum<<<1, 1024, 0, m->stream>>>(part, nel);

@@ -617,7 +617,9 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
       taup[t].assign(K, 0.0);
       tauu[t].assign(K, 0.0);
     }
-    std::vector<double> phi(512), grad(3 * 512);
+    int npmax = 0;   // basis values of the largest element (the hexahedron's (N+1)^3)
+    for (int t = 0; t < 4; ++t) npmax = std::max(npmax, B[t].Np);
+    std::vector<double> phi(npmax);
     m->face_w.assign((size_t)m->nsides * nq, 0.f);
 
     for (int t = 0; t < 4; ++t) {
@@ -1286,8 +1288,9 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
         td.iops2 = upload(i2, owned);
         td.nops2 = (int)o2.size();
         td.niops2 = (int)i2.size();
-        if (d->precision > 0 && (t == TET || t == PYR) && td.K > 0 && !g_host_only) {
-          // tensor-core volume products (kernels_prec.cu): the block operator B [4 npp][4 npk] from
+        if (d->precision > 0 && (t == TET || t == PYR) && td.K > 0 && !g_host_only && Np <= 256) {
+          // tensor-core volume products (kernels_prec.cu), for Np <= 256 (one MMA's N and one TMA
+          // box; pyramids at N >= 8 keep the FP32 path): the block operator B [4 npp][4 npk] from
           // D^a[x][y] = o2[(x Np + y) 4 + a]: block 0 (sum_a D^a W_a; pyramid (D^a)^T), blocks
           // 1..3 (D^a p)
           dgk::PrecDev& P = m->prec[t == TET ? 0 : 1];

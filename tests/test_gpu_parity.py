@@ -51,11 +51,11 @@ MESHES = {
 }
 
 
-@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7, 8, 9])
 @pytest.mark.parametrize("name", ["hybrid", "cjump", "ragged", "inverted"])
 def test_rhs_matches_oracle(lib, name, N):
-    """Every mesh at every order: the c-jump and both-transition meshes reach the N >= 5 kernel
-    instantiations with wave-speed jumps and the inverted transition layer."""
+    """Every mesh at every order N = 1..9: the c-jump and both-transition meshes reach the N >= 5
+    kernel instantiations with wave-speed jumps and the inverted transition layer."""
     m = MESHES[name]()
     for ts in (1.0, 0.0):
         o = DGOracle(m, N, tau_scale=ts)
@@ -75,11 +75,12 @@ def test_rhs_single_type_meshes(lib):
         assert rel(got, o.rhs(q32.astype(np.float64))) < TOL, L
 
 
-@pytest.mark.parametrize("N", [2, 3, 4, 6])
+@pytest.mark.parametrize("N", [2, 3, 4, 6, 8])
 def test_lsrk_steps_match_oracle(lib, N):
     """Ten LSRK(5,4) steps at the paper's dt from the projected standing mode (N = 4: the
     hexahedra run the TMA-staged stage kernel; N = 6: the pyramids read their operators from
-    global memory, the tets and wedges keep them in shared memory with fewer warps)."""
+    global memory, the tets and wedges keep them in shared memory with fewer warps; N = 8: every
+    operator from global memory, hexahedra in blocks of 736 threads)."""
     from oracle.dg import standing_mode
     m = small_hybrid_mesh()
     o = DGOracle(m, N)
@@ -133,7 +134,7 @@ def test_state_roundtrip_and_layout(lib):
     assert np.array_equal(back, q)
 
 
-@pytest.mark.parametrize("N", [2, 3, 4, 5])
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 9])
 def test_multirate_ab3_matches_oracle(lib, N):
     """Two-level MRAB3 (Sec. 2.4 reading): start-up + 5 coarse steps vs the oracle
     (fused kernels for N <= 4, separate rhs / AB3 kernels for N = 5)."""
@@ -171,7 +172,7 @@ def wedge_tet_mesh():
     return HybridMesh(xyz=xyz, conn=conn, c2=c2)
 
 
-@pytest.mark.parametrize("N", [2, 4])
+@pytest.mark.parametrize("N", [2, 4, 8, 9])
 def test_wedge_tet_triangle_face_rhs(lib, N):
     m = wedge_tet_mesh()
     o = DGOracle(m, N)

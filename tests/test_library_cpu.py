@@ -23,7 +23,7 @@ def test_every_declared_symbol_is_exported():
     assert declared == set(dg.EXPORTS)
 
 
-@pytest.mark.parametrize("N", [1, 2, 3, 4])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 9])
 def test_host_setup_time_step_matches_oracle(N):
     """Eq. dtK computed by the library's own host setup vs the oracle."""
     m = small_hybrid_mesh()
@@ -43,7 +43,8 @@ def test_host_setup_wave_speed_jump():
 
 def test_host_trace_constants_against_paper_table():
     """Library C_T(N) vs the printed Table computedTrace (independent of the oracle)."""
-    tab = {1: [9, 9.93, 11.68, 12.22], 4: [45, 42.99, 47.59, 41.65]}
+    tab = {1: [9, 9.93, 11.68, 12.22], 4: [45, 42.99, 47.59, 41.65], 8: [135, 123.76, 135.07, 109.04],
+           9: [165, 150.48, 164.11, 130.67]}
     for N, row in tab.items():
         _, ct = dg.host_check(small_hybrid_mesh(), N)
         assert np.allclose(ct, row, atol=0.006)
@@ -66,7 +67,7 @@ def test_host_setup_sem_matches_oracle_and_table(N):
 def test_host_setup_rejects_bad_meshes():
     m = small_hybrid_mesh()
     with pytest.raises(dg.DGError, match="not supported"):
-        dg.host_check(m, 8)
+        dg.host_check(m, 10)          # orders 1..9 are built
     bad = small_hybrid_mesh()
     c = bad.conn[0].copy()
     c[0] = c[0][[1, 0, 3, 2, 5, 4, 7, 6]]          # mirrored hexahedron: J < 0

@@ -99,7 +99,7 @@ def test_hex_trace_constants_closed_form(N):
 def test_trace_constants_table(name):
     """Table computedTrace: pins the wedge, pyramid (rational B_N) and tet spaces."""
     tab = read_table("trace_constants.txt")[name]
-    for N in range(1, 8):
+    for N in range(1, 10):
         assert abs(trace_constant(TYPES[name], N) - tab[N - 1]) < 0.006, (name, N)
 
 
@@ -194,7 +194,7 @@ def test_tet_nodal_derivatives_exact(N):
 
 def test_hex_face_interpolation_symmetry():
     """GL symmetry used by Alg. hex_upd: ell_k(1) = ell_{N-k}(-1)."""
-    for N in range(1, 8):
+    for N in range(1, 10):
         hx = Hex(N)
         vm = lagrange_1d(hx.r1, -1.0)[0]
         vp = lagrange_1d(hx.r1, 1.0)[0]

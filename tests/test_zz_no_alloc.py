@@ -24,7 +24,7 @@ def lib():
     return dg
 
 
-@pytest.mark.parametrize("N", [1, 3, 4, 7])
+@pytest.mark.parametrize("N", [1, 3, 4, 7, 9])
 def test_noalloc_energy_matches_dg_energy_twice(lib, N):
     """Every element type at low, middle and the highest order (the tet branch forms its
     O(Np^2) FP64 mass product per node)."""
