@@ -670,12 +670,34 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
         }
       }
       // ---------------------------------------------------------------- face fluxes
-      if (T != DG_TET) lattice_values();
+      // In the fused modes (stage, multi-rate) the element's own trace (p, u.n) at a face with a
+      // neighbour sits in the neighbour's inbox slot of the buffer read here: this element wrote it
+      // at the end of its previous launch, from the state it starts from now (and dg_step begins
+      // with a traces-only launch).  Elements without a wall face read it there instead of
+      // evaluating their own face values.
+      constexpr bool OWN_IN = T != DG_TET && (MODE == MODE_STAGE || MODE == MODE_MRC || MODE == MODE_MRF);
+      bool inner = false;
+      if (OWN_IN) {
+        const int nbf = lane < NF ? A.nbr[A.side_off + e * NF + lane] : 0;
+        inner = __all_sync(0xffffffffu, nbf >= 0);
+      }
+      if (T != DG_TET && !inner) lattice_values();
       __syncwarp();
       for (int fq = lane; fq < NFX; fq += 32) {
         int f, ci;
         float4 tr, sg;
-        if (LAT) {
+        if (inner) {   // face, canonical index and face data only
+          if (LAT && fq < NLT) {
+            f = face_of_tri<T>(fq / NFN);
+            ci = tperm[code[f] * NFN + fq % NFN];
+            sg = A.sgeo2[(e * NF + f) * NQ];
+          } else {
+            const int x = LAT ? fq - NLT : fq, idx = x % NQ;
+            f = LAT ? (T == DG_PYR ? 0 : 2 + x / NQ) : x / NQ;
+            ci = (!LAT && tri_of<T>(f) >= 0) ? idx : qperm[code[f] * NQ + idx];
+            sg = A.sgeo2[(e * NF + f) * NQ + idx];
+          }
+        } else if (LAT) {
           lat_point(fq, f, ci, tr, sg);
         } else {
           f = fq / NQ;
@@ -685,8 +707,15 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
           sg = A.sgeo2[(e * NF + f) * NQ + idx];
         }
         const int64_t gs = A.side_off + e * NF + f;
-        const float unm = sg.x * tr.y + sg.y * tr.z + sg.z * tr.w;
         const int nb = A.nbr[gs];
+        float pm, unm;
+        if (inner) {
+          pm = A.tin[(int64_t)nb * NQ + ci];
+          unm = A.tin[A.plane + (int64_t)nb * NQ + ci];
+        } else {
+          pm = tr.x;
+          unm = sg.x * tr.y + sg.y * tr.z + sg.z * tr.w;
+        }
         float P = 0.f, UN = 0.f;
         if (nb >= 0) {
           P = A.tin[gs * NQ + ci];
@@ -694,7 +723,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
         }
         const float ta = A.tau[gs];
         float fp, fu;
-        flux(nb < 0, tr.x, unm, P, UN, A.tau_scale * ta, A.tau_scale / ta, T != DG_TET && A.skew, fp, fu);
+        flux(nb < 0, pm, unm, P, UN, A.tau_scale * ta, A.tau_scale / ta, T != DG_TET && A.skew, fp, fu);
         F4[fq] = f4(sg.w * fp, sg.w * fu * sg.x, sg.w * fu * sg.y, sg.w * fu * sg.z);
       }
       __syncwarp();
