@@ -99,7 +99,14 @@ struct G2 {
   static constexpr int SMEM_CAP = 226 * 1024;
   static constexpr int NW_DEF = T == DG_PYR ? 28 : 16;
   static constexpr int WB_B = WB * 16;
-  static constexpr int NW_SM = (SMEM_CAP - OPS_B - IOPS_B) / WB_B;
+  // pyramid N <= 4: the first pass of the factorised face values as uniform work items, from a
+  // block-shared table built at block start: per item the first node and the node stride (start |
+  // stride << 8) and N1 coefficients, zero past the item's level size (the padded terms read nodes
+  // that exist: the largest index is NP - 1)
+  static constexpr bool PTAB = T == DG_PYR && N <= 4;
+  static constexpr int PL1 = PTAB ? NTRI * NKL + NKL * N1 : 0;
+  static constexpr int PT_B = PTAB ? ((PL1 * (N1 + 1) * 4 + 15) / 16) * 16 : 0;
+  static constexpr int NW_SM = (SMEM_CAP - OPS_B - IOPS_B - PT_B) / WB_B;
   static constexpr bool OPS_SMEM =
       NW_SM >= (N <= 4 ? NW_DEF : T == DG_TET ? DG_G2_MIN_WARPS_TET : DG_G2_MIN_WARPS);
   static constexpr int UNR = 4;   // volume loops (8 measured no faster from L2, slower for pyramids)
@@ -114,9 +121,9 @@ struct G2 {
   static constexpr int CM0 = 49152 / (NP * 16 * NOPV);
   static constexpr int CM = CM0 < 4 ? 4 : (CM0 > NP ? NP : CM0);
   static constexpr int CHUNK_B = CHUNK ? CM * NP * 16 * NOPV : 0;
-  static constexpr int NW_FIT = OPS_SMEM ? NW_SM : (SMEM_CAP - IOPS_B - CHUNK_B) / WB_B;
+  static constexpr int NW_FIT = OPS_SMEM ? NW_SM : (SMEM_CAP - IOPS_B - CHUNK_B - PT_B) / WB_B;
   static constexpr int NW = NW_FIT < NW_DEF ? NW_FIT : NW_DEF;
-  static constexpr int SMEM = (OPS_SMEM ? OPS_B : 0) + IOPS_B + CHUNK_B + NW * WB_B;
+  static constexpr int SMEM = (OPS_SMEM ? OPS_B : 0) + IOPS_B + CHUNK_B + PT_B + NW * WB_B;
   static constexpr int R = (NP + 31) / 32;
   static_assert(N > 4 || (OPS_SMEM && NW == NW_DEF), "N <= 4 keeps its operators and warps in shared memory");
   static_assert(T != DG_PYR || 3 * NIT <= 4 * (WB - NP - WV), "pyramid product scratch exceeds the free warp buffers");
@@ -155,7 +162,9 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
   constexpr int OPS_SB = C::OPS_SMEM ? C::OPS_B : 0;
   int* sio = reinterpret_cast<int*>(smem_raw + OPS_SB);
   float4* sch = reinterpret_cast<float4*>(smem_raw + OPS_SB + C::IOPS_B);   // [NOPV][CM][NP] (CHUNK)
-  float4* swarp = reinterpret_cast<float4*>(smem_raw + OPS_SB + C::IOPS_B + C::CHUNK_B);
+  int* ptd = reinterpret_cast<int*>(smem_raw + OPS_SB + C::IOPS_B + C::CHUNK_B);   // [PL1] (PTAB)
+  const float* ptc = reinterpret_cast<const float*>(ptd + C::PL1);                   // [PL1][N1]
+  float4* swarp = reinterpret_cast<float4*>(smem_raw + OPS_SB + C::IOPS_B + C::CHUNK_B + C::PT_B);
   if constexpr (C::OPS_SMEM) {
     float* sops = reinterpret_cast<float*>(smem_raw);
     for (int x = threadIdx.x; x < C::OPS; x += blockDim.x) sops[x] = A.ops2[x];
@@ -188,6 +197,24 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
   const int* tperm = sio;                                        // [6][NFN] local lattice -> canonical
   const int* qperm = sio + 12 * NFN;                             // [8][NQ] local GL point -> canonical
   const int* fnode = qperm + 8 * NQ;                             // tet [4][NFN]
+  if constexpr (C::PTAB) {   // uniform items of the first face-value pass (see G2::PTAB)
+    constexpr int PN1 = C::N1;
+    float* pc = const_cast<float*>(ptc);
+    for (int x = threadIdx.x; x < C::PL1; x += blockDim.x) {
+      const bool face = x < NTRI * NKL;
+      const int kl = face ? x % NKL : (x - NTRI * NKL) / PN1;
+      int k = 0;
+      while ((k + 1) * (k + 2) / 2 <= kl) ++k;
+      const int l = kl - k * (k + 1) / 2, k1 = k + 1, off = k * (k + 1) * (2 * k + 1) / 6, kb = k * (k + 1) / 2;
+      const int ti = x / NKL;
+      const bool alongi = face && (ti & 1);   // odd triangle faces sum over i, the others over j
+      const float* src = face ? EF + ti * NKL + kb : LA + ((x - NTRI * NKL) % PN1) * NKL + kb;
+      const float g = face ? 1.f : GC[k];
+      ptd[x] = (alongi ? off + l * k1 : off + l) | ((alongi ? 1 : k1) << 8);
+      for (int t = 0; t < PN1; ++t) pc[x * PN1 + t] = t < k1 ? g * src[t] : 0.f;
+    }
+    __syncthreads();
+  }
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ int s_code[NW][NF];
@@ -263,6 +290,17 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
     // Z[k][i][q] = GC_k sum_j LA[q][k][j] q_kji (PZB), traces = sum_kl LA[p][kl] Z[kl][q] (PTQB)
     auto pyr_face_values = [&]() {
       constexpr int PN1 = C::N1;
+      if constexpr (C::PTAB) {
+        for (int x = lane; x < C::PL1; x += 32) {
+          const int d = ptd[x], n0 = d & 255, ns = d >> 8;
+          const float* pc = ptc + x * PN1;
+          float4 v = f4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int t = 0; t < PN1; ++t) f4acc(v, pc[t], q4[n0 + t * ns]);
+          if (x < NTRI * NKL) G4[x] = v;
+          else PZB[x - NTRI * NKL] = v;
+        }
+      } else
       for (int x = lane; x < NTRI * NKL + NKL * PN1; x += 32) {
         const bool face = x < NTRI * NKL;
         const int kl = face ? x % NKL : (x - NTRI * NKL) / PN1;
