@@ -105,7 +105,7 @@ struct G2 {
   // that exist: the largest index is NP - 1)
   static constexpr bool PTAB = T == DG_PYR && N <= 4;
   static constexpr int PL1 = PTAB ? NTRI * NKL + NKL * N1 : 0;
-  static constexpr int PT_B = PTAB ? ((PL1 * (N1 + 1) * 4 + 15) / 16) * 16 : 0;
+  static constexpr int PT_B = PTAB ? (((PL1 * (N1 + 1) + NP) * 4 + 15) / 16) * 16 : 0;   // + node decode [NP]
   static constexpr int NW_SM = (SMEM_CAP - OPS_B - IOPS_B - PT_B) / WB_B;
   static constexpr bool OPS_SMEM =
       NW_SM >= (N <= 4 ? NW_DEF : T == DG_TET ? DG_G2_MIN_WARPS_TET : DG_G2_MIN_WARPS);
@@ -164,6 +164,8 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
   float4* sch = reinterpret_cast<float4*>(smem_raw + OPS_SB + C::IOPS_B);   // [NOPV][CM][NP] (CHUNK)
   int* ptd = reinterpret_cast<int*>(smem_raw + OPS_SB + C::IOPS_B + C::CHUNK_B);   // [PL1] (PTAB)
   const float* ptc = reinterpret_cast<const float*>(ptd + C::PL1);                   // [PL1][N1]
+  // pyramid node n = off_k + row (k + 1) + col: k | row << 4 | col << 8 (PTAB)
+  const int* pnd = reinterpret_cast<const int*>(ptc + C::PL1 * C::N1);
   float4* swarp = reinterpret_cast<float4*>(smem_raw + OPS_SB + C::IOPS_B + C::CHUNK_B + C::PT_B);
   if constexpr (C::OPS_SMEM) {
     float* sops = reinterpret_cast<float*>(smem_raw);
@@ -212,6 +214,13 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
       const float g = face ? 1.f : GC[k];
       ptd[x] = (alongi ? off + l * k1 : off + l) | ((alongi ? 1 : k1) << 8);
       for (int t = 0; t < PN1; ++t) pc[x * PN1 + t] = t < k1 ? g * src[t] : 0.f;
+    }
+    int* nd = const_cast<int*>(pnd);
+    for (int n = threadIdx.x; n < NP; n += blockDim.x) {
+      int k = 0;
+      while ((k + 1) * (k + 2) * (2 * k + 3) / 6 <= n) ++k;
+      const int rem = n - k * (k + 1) * (2 * k + 1) / 6;
+      nd[n] = k | ((rem / (k + 1)) << 4) | ((rem % (k + 1)) << 8);
     }
     __syncthreads();
   }
@@ -547,7 +556,15 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
             const int n = lane + 32 * r;
             yg[r][0] = yg[r][1] = yg[r][2] = 0.f;
             if (n >= NP) continue;
-            const int q = lev(n), rem = n - off(q), b = rem / (q + 1), l = rem - b * (q + 1);
+            int q, b, l;
+            if constexpr (C::PTAB) {
+              const int d = pnd[n];
+              q = d & 15, b = (d >> 4) & 15, l = d >> 8;
+            } else {
+              q = lev(n);
+              const int rem = n - off(q);
+              b = rem / (q + 1), l = rem - b * (q + 1);
+            }
             float yr = 0.f, ys = 0.f, yc = 0.f;
             for (int k = 0; k <= (q + 1 < N ? q + 1 : N); ++k) {
               const int base = PB[q * N1 + k];
@@ -573,7 +590,15 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
           // (C) W_r + (1+a_l)/2 W_t, W_s + (1+a_b)/2 W_t, W_t at each node (in place), then
           // A1[q][k][j][l] = sum_b E[q][k][b][j] (..)_r(l,b,q), A2 with E' and (..)_s, A3 with E and W_t
           for (int m = lane; m < NP; m += 32) {
-            const int q = lev(m), rem = m - off(q), b = rem / (q + 1), l = rem - b * (q + 1);
+            int q, b, l;
+            if constexpr (C::PTAB) {
+              const int d = pnd[m];
+              q = d & 15, b = (d >> 4) & 15, l = d >> 8;
+            } else {
+              q = lev(m);
+              const int rem = m - off(q);
+              b = rem / (q + 1), l = rem - b * (q + 1);
+            }
             const float4 w = W4[m];
             W4[m] = f4(fmaf(AH[q * N1 + l], w.z, w.x), fmaf(AH[q * N1 + b], w.z, w.y), w.z, w.w);
           }
@@ -599,7 +624,15 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
           for (int r = 0; r < R; ++r) {
             const int m = lane + 32 * r;
             if (m >= NP) break;
-            const int k = lev(m), rem = m - off(k), j = rem / (k + 1), i = rem - j * (k + 1);
+            int k, j, i;
+            if constexpr (C::PTAB) {
+              const int d = pnd[m];
+              k = d & 15, j = (d >> 4) & 15, i = d >> 8;
+            } else {
+              k = lev(m);
+              const int rem = m - off(k);
+              j = rem / (k + 1), i = rem - j * (k + 1);
+            }
             float z = 0.f;
             for (int q = (k > 0 ? k - 1 : 0); q <= N; ++q) {
               const int base = PB[q * N1 + k] + j * (q + 1);
@@ -826,9 +859,15 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
         float4 sum = f4(0.f, 0.f, 0.f, 0.f);
         if (T == DG_PYR) {   // node (k, j, i): four triangle faces, then the base
           constexpr int PN1 = C::N1;
-          int k = 0;
-          while ((k + 1) * (k + 2) * (2 * k + 3) / 6 <= n) ++k;
-          const int r0 = n - k * (k + 1) * (2 * k + 1) / 6, j = r0 / (k + 1), i = r0 % (k + 1);
+          int k = 0, j, i;
+          if constexpr (C::PTAB) {
+            const int d = pnd[n];
+            k = d & 15, j = (d >> 4) & 15, i = d >> 8;
+          } else {
+            while ((k + 1) * (k + 2) * (2 * k + 3) / 6 <= n) ++k;
+            const int r0 = n - k * (k + 1) * (2 * k + 1) / 6;
+            j = r0 / (k + 1), i = r0 % (k + 1);
+          }
           const int kb = k * (k + 1) / 2;
           f4acc(sum, EF[0 * NKL + kb + j], G4[0 * NKL + kb + i]);
           f4acc(sum, EF[1 * NKL + kb + i], G4[1 * NKL + kb + j]);
