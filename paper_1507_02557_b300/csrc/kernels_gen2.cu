@@ -154,7 +154,7 @@ __device__ __forceinline__ int face_of_tri(int ti) {
 }
 
 template <int T, int N, int MODE>
-__global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
+__global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
   using C = G2<T, N>;
   constexpr int NP = C::NP, NQ = C::NQ, NFN = C::NFN, NF = C::NF, NTRI = C::NTRI, NQUAD = C::NQUAD;
   constexpr int NC = C::NC, NW = C::NW, R = C::R;
@@ -678,6 +678,9 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
         const int q0 = PL ? lp * NQ : 0, q1 = PL ? q0 + NQ : NC;
         for (int qc = q0 + lane; qc < q1; qc += 32) {
           const int qt = qc % NQ, l = qc / NQ;
+          float g[12];   // lanes read consecutive cubature points: coalesced; in flight during the sums
+#pragma unroll
+          for (int c = 0; c < 12; ++c) g[c] = geo[c * NC + qc];
           float P = 0.f, Pr = 0.f, Ps = 0.f, Pt = 0.f, U0 = 0.f, U1 = 0.f, U2 = 0.f;
           const float4* vrow = DV4 + qt * NT;
 #pragma unroll 5
@@ -691,9 +694,6 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32) gen2_kernel(Args A) {
             U1 = fmaf(v.x, y.z, U1);
             U2 = fmaf(v.x, y.w, U2);
           }
-          float g[12];   // lanes read consecutive cubature points: coalesced
-#pragma unroll
-          for (int c = 0; c < 12; ++c) g[c] = geo[c * NC + qc];
           const float w = wq[qt * N1 + l];
           const float A0 = g[0] * Pr + g[3] * Ps + g[6] * Pt - P * g[9];
           const float A1 = g[1] * Pr + g[4] * Ps + g[7] * Pt - P * g[10];
