@@ -933,6 +933,367 @@ static void launch_hexw_n(const Args& A, const HexMaps& M, cudaStream_t s) {
   hexw_kernel<N, MODE, TMA, SEM><<<grid, 32 * H::WPB, H::SMEM, s>>>(A, M);
 }
 
+// ---------------------------------------------------------------------------- hex, N >= 6, columns
+// Column kernel for N = 6..9 (rhs, LSRK stage, traces; at N = 5 its 36 columns fill 2 warps too
+// sparsely and the thread-per-node kernel is 5 % faster): an element's (N+1)^2 node columns are
+// spread over WPE = ceil((N+1)^2 / 32) warps, thread = column (i, j) with the column's N+1 nodes
+// in registers (t-derivatives, t-face traces and the update from registers; r/s-derivatives and
+// r/s-face traces read the element's node values from shared memory), as in the N <= 4 kernel
+// above.  A block holds G element groups of WPE warps; each group walks its own elements and
+// synchronises on its own named barrier, so the groups stay independent.  While a group computes
+// element g, the cp.async copies of the next element's state and side data (double-buffered), of
+// its inbox planes (after g's flux phase) and of its residual (after g's update) are in flight.
+template <int N, int MODE>
+struct HexC {
+  static constexpr int n1 = N + 1, NP = n1 * n1 * n1, NQ = n1 * n1;
+  static constexpr int WPE = (NQ + 31) / 32, GT = WPE * 32;
+  static constexpr int G = WPE >= 3 ? 1 : 4 / WPE;        // N = 5..7: 2 groups of 2 warps; N = 8, 9: 1
+  static constexpr int NT = G * GT;
+  static constexpr int NAUX = MODE == MODE_STAGE ? 1 : 0;
+  static constexpr int SD = 44;   // geometry [24], nbr [6], code [6], tau [6], c2
+  // per group (bytes): q [2][NP] float4, aux [NAUX][NP] float4, F [4][NQ] float4, Nrm [6][NQ]
+  // float4, in [12 NQ] float, sd [2][SD] float
+  static constexpr int O_AUX = 2 * NP * 16;
+  static constexpr int O_F = O_AUX + NAUX * NP * 16;
+  static constexpr int O_N = O_F + 4 * NQ * 16;
+  static constexpr int O_IN = O_N + 6 * NQ * 16;
+  static constexpr int O_SD = O_IN + 12 * NQ * 4;
+  static constexpr int PG = ((O_SD + 2 * SD * 4 + 15) / 16) * 16;
+  static constexpr int CB = ((n1 * n1 + 5 * n1) * 4 + 15) / 16 * 16;   // D, Vm, Vp, w, r, 1/w
+  static constexpr int PERM_B = 8 * NQ * 4;
+  static constexpr int SMEM = CB + PERM_B + G * PG;
+  static_assert(SMEM <= 227 * 1024, "hex column kernel: shared memory");
+};
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(HexC<N, MODE>::NT, 1) hexc_kernel(Args A) {
+  using H = HexC<N, MODE>;
+  constexpr int n1 = H::n1, NP = H::NP, NQ = H::NQ, GT = H::GT, G = H::G, SD = H::SD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sc = reinterpret_cast<float*>(smem_raw);
+  const float* Dm = sc;
+  const float* Vm = Dm + n1 * n1;
+  const float* Vp = Vm + n1;
+  const float* W1 = Vp + n1;
+  const float* R1 = W1 + n1;
+  const float* iW = R1 + n1;
+  int* s_perm = reinterpret_cast<int*>(smem_raw + H::CB);
+  const int grp = threadIdx.x / GT, col = threadIdx.x % GT;
+  const bool own = col < NQ;            // threads past the last column only copy and synchronise
+  const int cl = own ? col : 0;
+  const int i = cl % n1, j = cl / n1;
+  unsigned char* pg = smem_raw + H::CB + H::PERM_B + grp * H::PG;
+  auto SQ = [&](int b) { return reinterpret_cast<float4*>(pg) + b * NP; };
+  float4* c_aux = reinterpret_cast<float4*>(pg + H::O_AUX);
+  float4* s_F = reinterpret_cast<float4*>(pg + H::O_F);
+  float4* s_N = reinterpret_cast<float4*>(pg + H::O_N);
+  float* c_in = reinterpret_cast<float*>(pg + H::O_IN);
+  auto SDp = [&](int b) { return reinterpret_cast<float*>(pg + H::O_SD) + b * SD; };
+  const unsigned bid = 1 + grp;   // named barrier of the group
+  auto gsync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(bid), "r"(GT) : "memory"); };
+
+  for (int x = threadIdx.x; x < n1 * n1 + 5 * n1; x += blockDim.x) sc[x] = A.hexc[x];
+  for (int x = threadIdx.x; x < 8 * NQ; x += blockDim.x) s_perm[x] = A.perm[x];
+  __syncthreads();
+
+  auto elem = [&](int64_t g) -> int64_t {
+    const int64_t li = g * G + grp;
+    if (li >= A.K) return -1;
+    return A.elist ? (int64_t)A.elist[li] : li;
+  };
+  // copies by every thread of the group: columns col, col + GT, ... of the NQ columns
+  auto stage_main = [&](int b, int64_t e) {
+    if (e >= 0) {
+      float* dq = reinterpret_cast<float*>(SQ(b));
+      for (int c = col; c < NQ; c += GT) {
+        const float* qs = A.q + A.dof_off + e * NP + c;
+#pragma unroll
+        for (int k = 0; k < n1; ++k)
+#pragma unroll
+          for (int f = 0; f < 4; ++f) cp_async4(dq + 4 * (c + NQ * k) + f, qs + f * A.ndof + NQ * k);
+      }
+      const int64_t gs0 = A.side_off + e * 6;
+      float* ds = SDp(b);
+      for (int x = col; x < SD - 1; x += GT) {
+        const void* src = x < 24   ? static_cast<const void*>(A.geo + e * 24 + x)
+                          : x < 30 ? static_cast<const void*>(A.nbr + gs0 + (x - 24))
+                          : x < 36 ? static_cast<const void*>(A.code + gs0 + (x - 30))
+                          : x < 42 ? static_cast<const void*>(A.tau + gs0 + (x - 36))
+                                   : static_cast<const void*>(A.c2 + e);
+        cp_async4(ds + x, src);
+      }
+    }
+    cp_async_commit();
+  };
+  auto stage_in = [&](int64_t e) {
+    if (MODE != MODE_TRACE && e >= 0) {
+      const float* src = A.tin + (A.side_off + e * 6) * NQ;
+      for (int y = col; y < 12 * NQ; y += GT) cp_async4(c_in + y, src + (y >= 6 * NQ ? A.plane - 6 * NQ : 0) + y);
+    }
+    cp_async_commit();
+  };
+  auto stage_aux = [&](int64_t e) {
+    if (H::NAUX > 0 && e >= 0) {
+      float* d = reinterpret_cast<float*>(c_aux);
+      for (int c = col; c < NQ; c += GT) {
+        const float* s0 = A.res + A.dof_off + e * NP + c;
+#pragma unroll
+        for (int k = 0; k < n1; ++k)
+#pragma unroll
+          for (int f = 0; f < 4; ++f) cp_async4(d + 4 * (c + NQ * k) + f, s0 + f * A.ndof + NQ * k);
+      }
+    }
+    cp_async_commit();
+  };
+
+  int64_t g = blockIdx.x;
+  const int64_t gstride = gridDim.x;
+  int64_t e_c = elem(g), e_n = elem(g + gstride);
+  stage_main(0, e_c);
+  stage_in(e_c);
+  stage_aux(e_c);
+  int b = 0;
+  for (; g * G + grp < A.K; g += gstride, b ^= 1) {
+    const int64_t e_nn = elem(g + 2 * gstride);   // consumed one element later
+    stage_main(b ^ 1, e_n);
+    cp_async_wait<2>();                           // main(g) and in(g) have landed
+    gsync();
+    const int64_t e = e_c;
+    const int64_t base = A.dof_off + e * NP;
+    const float* g_ = SDp(b);
+    const int* s_nb = reinterpret_cast<const int*>(g_ + 24);
+    const int* s_code = reinterpret_cast<const int*>(g_ + 30);
+    const float* s_tau = g_ + 36;
+    const float c2 = g_[42];
+    float4* s_q = SQ(b);
+    float q[4][n1];
+#pragma unroll
+    for (int k = 0; k < n1; ++k) {
+      const float4 v = s_q[cl + NQ * k];
+      q[0][k] = v.x;
+      q[1][k] = v.y;
+      q[2][k] = v.z;
+      q[3][k] = v.w;
+    }
+    float rhs[4][n1];
+    float iJn[n1];
+    if (MODE != MODE_TRACE && own) {
+      // ---- volume: collocated strong form (Alg. hex_vol), metrics built along the column
+      const float r = R1[i], s = R1[j];
+      float Ar[3], Br[3], As[3], Bs[3], xt[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        Ar[d] = g_[d] + g_[9 + d] * s;
+        Br[d] = g_[12 + d] + g_[18 + d] * s;
+        As[d] = g_[3 + d] + g_[9 + d] * r;
+        Bs[d] = g_[15 + d] + g_[18 + d] * r;
+        xt[d] = g_[6 + d] + g_[12 + d] * r + g_[15 + d] * s + g_[18 + d] * r * s;
+      }
+      float G0a[3], G0b[3], G1a[3], G1b[3], G2a[3], G2b[3], G2c[3], tmp[3];
+      cross3(As, xt, G0a);
+      cross3(Bs, xt, G0b);
+      cross3(xt, Ar, G1a);
+      cross3(xt, Br, G1b);
+      cross3(Ar, As, G2a);
+      cross3(Ar, Bs, G2b);
+      cross3(Br, As, tmp);
+      G2b[0] += tmp[0];
+      G2b[1] += tmp[1];
+      G2b[2] += tmp[2];
+      cross3(Br, Bs, G2c);
+#pragma unroll
+      for (int k = 0; k < n1; ++k) {
+        const float t = R1[k];
+        float g0[3], g1[3], g2[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          g0[d] = G0a[d] + t * G0b[d];
+          g1[d] = G1a[d] + t * G1b[d];
+          g2[d] = G2a[d] + t * (G2b[d] + t * G2c[d]);
+        }
+        const float J = (Ar[0] + t * Br[0]) * g0[0] + (Ar[1] + t * Br[1]) * g0[1] + (Ar[2] + t * Br[2]) * g0[2];
+        const float iJ = __frcp_rn(J);
+        iJn[k] = iJ;
+        float4 dr = make_float4(0.f, 0.f, 0.f, 0.f), ds = dr, dt4 = dr;
+#pragma unroll
+        for (int m = 0; m < n1; ++m) {
+          dr = f4fma(Dm[i * n1 + m], s_q[m + n1 * j + NQ * k], dr);
+          ds = f4fma(Dm[j * n1 + m], s_q[i + n1 * m + NQ * k], ds);
+          dt4 = f4fma(Dm[k * n1 + m], make_float4(q[0][m], q[1][m], q[2][m], q[3][m]), dt4);
+        }
+        const float dt[4] = {dt4.x, dt4.y, dt4.z, dt4.w};
+        const float drf[4] = {dr.x, dr.y, dr.z, dr.w}, dsf[4] = {ds.x, ds.y, ds.z, ds.w};
+        float div = 0.f;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) div += g0[d] * drf[1 + d] + g1[d] * dsf[1 + d] + g2[d] * dt[1 + d];
+        rhs[0][k] = -div * iJ;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) rhs[1 + d][k] = -c2 * iJ * (g0[d] * drf[0] + g1[d] * dsf[0] + g2[d] * dt[0]);
+      }
+    }
+    float4 F45[2];
+    if (MODE != MODE_TRACE && own) {
+      // ---- fluxes at this thread's point (a,b) = (i,j) of all six faces
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) {
+        float4 tm = make_float4(0.f, 0.f, 0.f, 0.f), tp = tm;
+#pragma unroll
+        for (int m = 0; m < n1; ++m) {
+          const float4 v = ax == 0 ? s_q[m + n1 * i + NQ * j]
+                           : ax == 1 ? s_q[i + n1 * m + NQ * j]
+                                     : make_float4(q[0][m], q[1][m], q[2][m], q[3][m]);
+          tm = f4fma(Vm[m], v, tm);
+          tp = f4fma(Vp[m], v, tp);
+        }
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+          const int f = 2 * ax + sd;
+          const float4 tr = sd ? tp : tm;
+          float nv[3], Js;
+          hexw_face_geom<N>(g_, R1, f, i, j, nv, Js);
+          s_N[f * NQ + cl] = make_float4(nv[0], nv[1], nv[2], Js);
+          const float unm = nv[0] * tr.y + nv[1] * tr.z + nv[2] * tr.w;
+          const int nb = s_nb[f];
+          float P = 0.f, UN = 0.f;
+          if (nb >= 0) {
+            const int cidx = s_perm[s_code[f] * NQ + cl];
+            P = c_in[f * NQ + cidx];
+            UN = c_in[6 * NQ + f * NQ + cidx];
+          }
+          const float ta = s_tau[f];
+          float fp, fu;
+          flux(nb < 0, tr.x, unm, P, UN, A.tau_scale * ta, A.tau_scale * __frcp_rn(ta), false, fp, fu);
+          const float wg = W1[i] * W1[j] * Js;
+          const float4 Fv = make_float4(wg * fp, wg * fu * nv[0], wg * fu * nv[1], wg * fu * nv[2]);
+          if (ax < 2) s_F[f * NQ + cl] = Fv;
+          else F45[sd] = Fv;
+        }
+      }
+    }
+    gsync();
+    stage_in(e_n);   // the inbox buffer is free again
+    if (MODE != MODE_TRACE) {
+      if (own) {
+        // ---- lift (Alg. hex_surf), M^{-1} = 1/(w w w J)
+#pragma unroll
+        for (int k = 0; k < n1; ++k) {
+          float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+          sum = f4fma(Vm[i], s_F[0 * NQ + j + n1 * k], sum);
+          sum = f4fma(Vp[i], s_F[1 * NQ + j + n1 * k], sum);
+          sum = f4fma(Vm[j], s_F[2 * NQ + i + n1 * k], sum);
+          sum = f4fma(Vp[j], s_F[3 * NQ + i + n1 * k], sum);
+          sum = f4fma(Vm[k], F45[0], sum);
+          sum = f4fma(Vp[k], F45[1], sum);
+          const float iM = iW[i] * iW[j] * iW[k] * iJn[k];
+          rhs[0][k] += iM * sum.x;
+          rhs[1][k] += c2 * iM * sum.y;
+          rhs[2][k] += c2 * iM * sum.z;
+          rhs[3][k] += c2 * iM * sum.w;
+        }
+        if (e == A.src_e) {   // point source on p
+#pragma unroll
+          for (int k = 0; k < n1; ++k) rhs[0][k] += A.src_s * A.src_g[cl + NQ * k];
+        }
+      }
+      cp_async_wait<2>();   // aux(g) has landed
+      gsync();
+      if (own) {
+        if (MODE == MODE_RHS) {
+#pragma unroll
+          for (int k = 0; k < n1; ++k)
+#pragma unroll
+            for (int f = 0; f < 4; ++f) A.rhs[f * A.ndof + base + cl + NQ * k] = rhs[f][k];
+        } else {   // LSRK(5,4) 2N-storage update
+          const float dte = A.dtE ? A.dtE[e] : A.dt;
+#pragma unroll
+          for (int k = 0; k < n1; ++k) {
+            const float4 rv = c_aux[cl + NQ * k];
+            const float ro[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+              const int64_t id = f * A.ndof + base + cl + NQ * k;
+              const float rr = A.a * ro[f] + dte * rhs[f][k];
+              q[f][k] += A.b * rr;
+              A.res[id] = rr;
+              A.qout[id] = q[f][k];
+            }
+          }
+        }
+      }
+      gsync();
+    }
+    stage_aux(e_n);   // the aux buffer is free again
+
+    // ---- traces of the state in q[] into the neighbours' inboxes
+    if (MODE != MODE_RHS) {
+      if (MODE == MODE_STAGE) {
+        if (own) {
+#pragma unroll
+          for (int k = 0; k < n1; ++k) s_q[cl + NQ * k] = make_float4(q[0][k], q[1][k], q[2][k], q[3][k]);
+        }
+        gsync();
+      }
+      if (own) {
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+          float4 tm = make_float4(0.f, 0.f, 0.f, 0.f), tp = tm;
+#pragma unroll
+          for (int m = 0; m < n1; ++m) {
+            const float4 v = ax == 0 ? s_q[m + n1 * i + NQ * j]
+                             : ax == 1 ? s_q[i + n1 * m + NQ * j]
+                                       : make_float4(q[0][m], q[1][m], q[2][m], q[3][m]);
+            tm = f4fma(Vm[m], v, tm);
+            tp = f4fma(Vp[m], v, tp);
+          }
+#pragma unroll
+          for (int sd = 0; sd < 2; ++sd) {
+            const int f = 2 * ax + sd;
+            const int nb = s_nb[f];
+            const int64_t dst = nb >= 0 ? (int64_t)nb : ((MODE == MODE_TRACE && A.wall_self) ? A.side_off + e * 6 + f : -1);
+            if (dst < 0) continue;
+            float nv[3];
+            if (MODE != MODE_TRACE) {
+              const float4 nn = s_N[f * NQ + cl];
+              nv[0] = nn.x;
+              nv[1] = nn.y;
+              nv[2] = nn.z;
+            } else {
+              float Js;
+              hexw_face_geom<N>(g_, R1, f, i, j, nv, Js);
+            }
+            const float4 tr = sd ? tp : tm;
+            const int cidx = s_perm[s_code[f] * NQ + cl];
+            A.tout[dst * NQ + cidx] = tr.x;
+            A.tout[A.plane + dst * NQ + cidx] = nv[0] * tr.y + nv[1] * tr.z + nv[2] * tr.w;
+          }
+        }
+      }
+    }
+    gsync();   // the state buffer is refilled two elements later; side data and faces next element
+    e_c = e_n;
+    e_n = e_nn;
+  }
+  cp_async_wait<0>();
+}
+
+template <int N, int MODE>
+static void launch_hexc_n(const Args& A, cudaStream_t s) {
+  using H = HexC<N, MODE>;
+  if (A.K == 0) return;
+  static int blocks = 0;   // persistent grid: resident blocks per SM x SMs (computed once)
+  if (blocks == 0) {
+    cudaFuncSetAttribute(hexc_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, H::SMEM);
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, hexc_kernel<N, MODE>, H::NT, H::SMEM);
+    blocks = (per < 1 ? 1 : per) * sms;
+  }
+  const int64_t need = ((int64_t)A.K + H::G - 1) / H::G;
+  const int grid = (int)(need < blocks ? need : blocks);
+  hexc_kernel<N, MODE><<<grid, H::NT, H::SMEM, s>>>(A);
+}
+
 // ---------------------------------------------------------------------------- TMA descriptors
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -1436,7 +1797,7 @@ static void launch_type(dg_mesh* m, const Args& A0, int t) {
   switch (m->N) {
 #define DG_CASE(NN)                                                   \
   case NN:                                                            \
-    if (t == DG_HEX) { if (NN <= 4) launch_hex_fast<(NN <= 4 ? NN : 4), MODE>(m, A, s); else launch_hex_n<NN, (MODE > 2 ? 1 : MODE)>(A, s); } \
+    if (t == DG_HEX) { if (NN <= 4) launch_hex_fast<(NN <= 4 ? NN : 4), MODE>(m, A, s); else if (NN == 5) launch_hex_n<(NN < 6 ? NN : 5), (MODE > 2 ? 1 : MODE)>(A, s); else launch_hexc_n<(NN > 5 ? NN : 6), (MODE > 2 ? 1 : MODE)>(A, s); } \
     else if (DG_TET_TC && !tcv && t == DG_TET && m->tri_lat && m->use_tet_tc && launch_tet_tc<MODE>(NN, A, s)) {}   \
     else if ((t == DG_WEDGE || m->tri_lat) && launch_gen2<MODE>(t, NN, A, s)) {}   \
     else if (t == DG_WEDGE) launch_gen_n<DG_WEDGE, NN, (MODE > 2 ? 1 : MODE)>(A, s);   \
