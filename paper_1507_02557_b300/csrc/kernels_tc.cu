@@ -84,7 +84,11 @@ struct TetTC {
   static constexpr int NP = (N + 1) * (N + 2) * (N + 3) / 6, NFN = (N + 1) * (N + 2) / 2, NQ = (N + 1) * (N + 1);
   static constexpr int TE = 32, NT = 512;                 // elements per tile (128 TMEM lanes), threads
   static constexpr int KV = 3 * NP, KL = 4 * NFN;         // volume and lift columns of X
-  static constexpr int KP = (KV + KL + 7) / 8 * 8;        // K padded to the MMA's 8
+  // K layout: each of the blocks D^r, D^s, D^t, Lf padded to a multiple of the MMA's 8, so that an
+  // 8-column chunk of X lies in one block
+  static constexpr int NP8 = (NP + 7) / 8 * 8, KL8 = (KL + 7) / 8 * 8;
+  static constexpr int KV8 = 3 * NP8;
+  static constexpr int KP = KV8 + KL8;
   static constexpr int NPP = (NP + 15) / 16 * 16;         // MMA N: multiple of 16 for M = 128
   static constexpr int XHI = 0, XLO = KP, DCOL = 2 * KP;  // tensor-memory columns
   static constexpr int TCOLS = pow2_cols(DCOL + NPP);
@@ -214,12 +218,14 @@ __global__ void __launch_bounds__(512, 1) tet_tc_kernel(Args A) {
       const int n = x / KP, k = x % KP;
       float v = 0.f;
       if (n < NP) {
-        if (k < KV) {
-          const float4 d = DV4[n * NP + k % NP];
-          const int a = k / NP;
-          v = a == 0 ? d.x : a == 1 ? d.y : d.z;
-        } else if (k < KV + KL) {
-          v = Lf[(k - KV) * NP + n];
+        if (k < C::KV8) {
+          const int a = k / C::NP8, m = k - a * C::NP8;
+          if (m < NP) {
+            const float4 d = DV4[n * NP + m];
+            v = a == 0 ? d.x : a == 1 ? d.y : d.z;
+          }
+        } else if (k - C::KV8 < KL) {
+          v = Lf[(k - C::KV8) * NP + n];
         }
       }
       const float h = tf32r(v);
@@ -338,21 +344,19 @@ __global__ void __launch_bounds__(512, 1) tet_tc_kernel(Args A) {
       const float sl = fld == 0 ? iJ : c2 * iJ;
       const int d = fld == 0 ? 0 : fld - 1;
       const float cf0 = -c2 * G[d], cf1 = -c2 * G[3 + d], cf2 = -c2 * G[6 + d];
-      const float* wsrc = fld == 0 ? sr + el * KV : B.q + el * 4 * NP;   // volume source row
-      const float* fsrc = sfc + row * (KL + 1) - KV;                      // lift source row
+      const float* fsrc = sfc + row * (KL + 1);                           // lift source row
       for (int ch = wq; ch < KP / 8; ch += 4) {
+        // the chunk's block: volume a (source, scale, first node) or the lift
+        const bool vol = ch < C::KV8 / 8;
+        const int a = vol ? ch / (C::NP8 / 8) : 0;
+        const int m0 = vol ? (ch - a * (C::NP8 / 8)) * 8 : ch * 8 - C::KV8;
+        const int lim = vol ? NP : KL;
+        const float mul = vol ? (fld == 0 ? 1.f : (a == 0 ? cf0 : a == 1 ? cf1 : cf2)) : sl;
+        const float* src = vol ? (fld == 0 ? sr + el * KV + a * NP : B.q + el * 4 * NP) : fsrc;
         unsigned vh[8], vl[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          const int k = ch * 8 + c;
-          float v = 0.f;
-          if (k < KV) {
-            const int a = (k >= NP) + (k >= 2 * NP);
-            const float mul = fld == 0 ? 1.f : (a == 0 ? cf0 : a == 1 ? cf1 : cf2);
-            v = mul * wsrc[fld == 0 ? k : k - a * NP];
-          } else if (k < KV + KL) {
-            v = sl * fsrc[k];
-          }
+          const float v = m0 + c < lim ? mul * src[m0 + c] : 0.f;
           const float h = tf32r(v);
           vh[c] = __float_as_uint(h);
           vl[c] = __float_as_uint(tf32r(v - h));
