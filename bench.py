@@ -701,6 +701,15 @@ def main():
               "step_roofline": {"bytes_per_step": sum(tb1) / args.steps, "achieved": step1, "peak": hbm,
                                 "unit": "GB/s", "frac": step1 / hbm},
               "gpu_launches": int(sum(l1))}
+    # the same steps with the warp-per-element SIMT tet kernel instead of the tensor-core one
+    g1.set_choices(tet_tensor_cores=False)
+    g1.profile(1)
+    g1.step(args.steps, dt)
+    kms_simt, _ = g1.profile(0)
+    g1.set_choices()
+    single["tet_tensor_cores_vs_simt"] = {"tensor_core_ms": kms1[3], "simt_ms": kms_simt[3],
+                                          "time_ratio": kms1[3] / kms_simt[3] if kms_simt[3] > 0 else None,
+                                          "note": "tet kernel time over the same LSRK steps (per-type timing)"}
     del g1
     torch.cuda.synchronize()
 

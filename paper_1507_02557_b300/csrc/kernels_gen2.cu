@@ -260,36 +260,44 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
     float4* YB = W4 + 2 * WNT;
     float4* TQB = YB + 3 * WN1 * WN1;
     auto wedge_face_values = [&]() {
-      for (int x = lane; x < 2 * WNT + 3 * WN1 * WN1; x += 32) {
-        float4 v = f4(0.f, 0.f, 0.f, 0.f);
-        if (x < 2 * WNT) {
-          const int f = x / WNT, mt = x % WNT;
+      {
+        auto item = [&](int x) {
+          float4 v = f4(0.f, 0.f, 0.f, 0.f);
+          if (x < 2 * WNT) {
+            const int f = x / WNT, mt = x % WNT;
 #pragma unroll
-          for (int j = 0; j < WN1; ++j) f4acc(v, V1e[f * WN1 + j], q4[mt + WNT * j]);
-          ZB[x] = v;
-        } else {
-          const int y = x - 2 * WNT, qf = y / (WN1 * WN1), ia = (y / WN1) % WN1, j = y % WN1;
-          const float* ve = Ve + (qf * WN1 + ia) * WNT;
+            for (int j = 0; j < WN1; ++j) f4acc(v, V1e[f * WN1 + j], q4[mt + WNT * j]);
+            ZB[x] = v;
+          } else {
+            const int y = x - 2 * WNT, qf = y / (WN1 * WN1), ia = (y / WN1) % WN1, j = y % WN1;
+            const float* ve = Ve + (qf * WN1 + ia) * WNT;
 #pragma unroll 5
-          for (int mt = 0; mt < WNT; ++mt) f4acc(v, ve[mt], q4[mt + WNT * j]);
-          YB[y] = v;
-        }
+            for (int mt = 0; mt < WNT; ++mt) f4acc(v, ve[mt], q4[mt + WNT * j]);
+            YB[y] = v;
+          }
+        };
+        for (int x = lane; x < 2 * WNT; x += 32) item(x);   // one kind of item per warp pass
+        for (int x = 2 * WNT + lane; x < 2 * WNT + 3 * WN1 * WN1; x += 32) item(x);
       }
       __syncwarp();
-      for (int x = lane; x < 2 * NFN + 3 * NQ; x += 32) {
-        float4 v = f4(0.f, 0.f, 0.f, 0.f);
-        if (x < 2 * NFN) {
-          const int ti = x / NFN, nl = x % NFN;
-          const float* vt = Vtl + (ti * NFN + nl) * WNT;
+      {
+        auto item = [&](int x) {
+          float4 v = f4(0.f, 0.f, 0.f, 0.f);
+          if (x < 2 * NFN) {
+            const int ti = x / NFN, nl = x % NFN;
+            const float* vt = Vtl + (ti * NFN + nl) * WNT;
 #pragma unroll 5
-          for (int mt = 0; mt < WNT; ++mt) f4acc(v, vt[mt], ZB[ti * WNT + mt]);
-          V4[ti * NFN + tperm[code[ti] * NFN + nl]] = v;
-        } else {
-          const int y = x - 2 * NFN, qf = y / NQ, idx = y % NQ, ia = idx % WN1, ib = idx / WN1;
+            for (int mt = 0; mt < WNT; ++mt) f4acc(v, vt[mt], ZB[ti * WNT + mt]);
+            V4[ti * NFN + tperm[code[ti] * NFN + nl]] = v;
+          } else {
+            const int y = x - 2 * NFN, qf = y / NQ, idx = y % NQ, ia = idx % WN1, ib = idx / WN1;
 #pragma unroll
-          for (int j = 0; j < WN1; ++j) f4acc(v, V1q[ib * WN1 + j], YB[(qf * WN1 + ia) * WN1 + j]);
-          TQB[y] = v;
-        }
+            for (int j = 0; j < WN1; ++j) f4acc(v, V1q[ib * WN1 + j], YB[(qf * WN1 + ia) * WN1 + j]);
+            TQB[y] = v;
+          }
+        };
+        for (int x = lane; x < 2 * NFN; x += 32) item(x);   // one kind of item per warp pass
+        for (int x = 2 * NFN + lane; x < 2 * NFN + 3 * NQ; x += 32) item(x);
       }
     };
     // canonical lattice values of the triangle faces (V4) from q4
@@ -309,46 +317,53 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
           if (x < NTRI * NKL) G4[x] = v;
           else PZB[x - NTRI * NKL] = v;
         }
-      } else
-      for (int x = lane; x < NTRI * NKL + NKL * PN1; x += 32) {
-        const bool face = x < NTRI * NKL;
-        const int kl = face ? x % NKL : (x - NTRI * NKL) / PN1;
-        int k = 0;
-        while ((k + 1) * (k + 2) / 2 <= kl) ++k;
-        const int l = kl - k * (k + 1) / 2, k1 = k + 1, off = k * (k + 1) * (2 * k + 1) / 6, kb = k * (k + 1) / 2;
-        float4 v = f4(0.f, 0.f, 0.f, 0.f);
-        if (face) {
-          const int ti = x / NKL;
-          const float* ef = EF + ti * NKL + kb;
-          if (ti & 1) {
-            for (int i = 0; i < k1; ++i) f4acc(v, ef[i], q4[off + l * k1 + i]);
+      } else {
+        auto item = [&](int x) {
+          const bool face = x < NTRI * NKL;
+          const int kl = face ? x % NKL : (x - NTRI * NKL) / PN1;
+          int k = 0;
+          while ((k + 1) * (k + 2) / 2 <= kl) ++k;
+          const int l = kl - k * (k + 1) / 2, k1 = k + 1, off = k * (k + 1) * (2 * k + 1) / 6, kb = k * (k + 1) / 2;
+          float4 v = f4(0.f, 0.f, 0.f, 0.f);
+          if (face) {
+            const int ti = x / NKL;
+            const float* ef = EF + ti * NKL + kb;
+            if (ti & 1) {
+              for (int i = 0; i < k1; ++i) f4acc(v, ef[i], q4[off + l * k1 + i]);
+            } else {
+              for (int j = 0; j < k1; ++j) f4acc(v, ef[j], q4[off + j * k1 + l]);
+            }
+            G4[x] = v;
           } else {
-            for (int j = 0; j < k1; ++j) f4acc(v, ef[j], q4[off + j * k1 + l]);
+            const float* la = LA + ((x - NTRI * NKL) % PN1) * NKL + kb;
+            for (int j = 0; j < k1; ++j) f4acc(v, la[j], q4[off + j * k1 + l]);
+            const float g = GC[k];
+            PZB[x - NTRI * NKL] = f4(g * v.x, g * v.y, g * v.z, g * v.w);
           }
-          G4[x] = v;
-        } else {
-          const float* la = LA + ((x - NTRI * NKL) % PN1) * NKL + kb;
-          for (int j = 0; j < k1; ++j) f4acc(v, la[j], q4[off + j * k1 + l]);
-          const float g = GC[k];
-          PZB[x - NTRI * NKL] = f4(g * v.x, g * v.y, g * v.z, g * v.w);
-        }
+        };
+        for (int x = lane; x < NTRI * NKL; x += 32) item(x);   // one kind of item per warp pass
+        for (int x = NTRI * NKL + lane; x < NTRI * NKL + NKL * PN1; x += 32) item(x);
       }
       __syncwarp();
-      for (int x = lane; x < NTRI * NFN + NQ; x += 32) {
-        float4 v = f4(0.f, 0.f, 0.f, 0.f);
-        if (x < NTRI * NFN) {
-          const float* pf = PF + x * NKL;
-          const float4* y = G4 + (x / NFN) * NKL;
+      {
+        auto item = [&](int x) {
+          float4 v = f4(0.f, 0.f, 0.f, 0.f);
+          if (x < NTRI * NFN) {
+            const float* pf = PF + x * NKL;
+            const float4* y = G4 + (x / NFN) * NKL;
 #pragma unroll 5
-          for (int kl = 0; kl < NKL; ++kl) f4acc(v, pf[kl], y[kl]);
-          V4[x] = v;
-        } else {
-          const int idx = x - NTRI * NFN, pp = idx % PN1, qq = idx / PN1;
-          const float* la = LA + pp * NKL;
+            for (int kl = 0; kl < NKL; ++kl) f4acc(v, pf[kl], y[kl]);
+            V4[x] = v;
+          } else {
+            const int idx = x - NTRI * NFN, pp = idx % PN1, qq = idx / PN1;
+            const float* la = LA + pp * NKL;
 #pragma unroll 5
-          for (int kl = 0; kl < NKL; ++kl) f4acc(v, la[kl], PZB[kl * PN1 + qq]);
-          PTQB[idx] = v;
-        }
+            for (int kl = 0; kl < NKL; ++kl) f4acc(v, la[kl], PZB[kl * PN1 + qq]);
+            PTQB[idx] = v;
+          }
+        };
+        for (int x = lane; x < NTRI * NFN; x += 32) item(x);   // one kind of item per warp pass
+        for (int x = NTRI * NFN + lane; x < NTRI * NFN + NQ; x += 32) item(x);
       }
     };
     // (tet, pyramid: local order; the wedge also fills the quad-face traces)
@@ -816,39 +831,47 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
       float4* HB = W4;              // wedge: H_f[mt] = sum_nl phi_tri_mt(lattice_nl) G_f[nl]
       float4* PB = W4 + 2 * WNT;    // wedge: P_qf[ia][j] = sum_ib phi_1D_j(x_ib) F_qf[ia, ib]
       if (T == DG_WEDGE) {
-        for (int x = lane; x < 2 * WNT + 3 * WN1 * WN1; x += 32) {
-          float4 v = f4(0.f, 0.f, 0.f, 0.f);
-          if (x < 2 * WNT) {
-            const int f = x / WNT, mt = x % WNT;
+        {
+          auto item = [&](int x) {
+            float4 v = f4(0.f, 0.f, 0.f, 0.f);
+            if (x < 2 * WNT) {
+              const int f = x / WNT, mt = x % WNT;
 #pragma unroll 5
-            for (int nl = 0; nl < NFN; ++nl) f4acc(v, Vtl[(f * NFN + nl) * WNT + mt], G4[f * NFN + nl]);
-            HB[x] = v;
-          } else {
-            const int y = x - 2 * WNT, qf = y / (WN1 * WN1), ia = (y / WN1) % WN1, j = y % WN1;
+              for (int nl = 0; nl < NFN; ++nl) f4acc(v, Vtl[(f * NFN + nl) * WNT + mt], G4[f * NFN + nl]);
+              HB[x] = v;
+            } else {
+              const int y = x - 2 * WNT, qf = y / (WN1 * WN1), ia = (y / WN1) % WN1, j = y % WN1;
 #pragma unroll
-            for (int ib = 0; ib < WN1; ++ib) f4acc(v, V1q[ib * WN1 + j], F4[(2 + qf) * NQ + ia + WN1 * ib]);
-            PB[y] = v;
-          }
+              for (int ib = 0; ib < WN1; ++ib) f4acc(v, V1q[ib * WN1 + j], F4[(2 + qf) * NQ + ia + WN1 * ib]);
+              PB[y] = v;
+            }
+          };
+          for (int x = lane; x < 2 * WNT; x += 32) item(x);   // one kind of item per warp pass
+          for (int x = 2 * WNT + lane; x < 2 * WNT + 3 * WN1 * WN1; x += 32) item(x);
         }
         __syncwarp();
       }
       if (T == DG_PYR) {
         // H_ti[kl] = sum_n PF2[ti][n][kl] F_ti[n] (G4); Wb[(k,j)][p] = sum_q LA[q][(k,j)] F_base[p, q] (PZB)
         constexpr int PN1 = C::N1;
-        for (int x = lane; x < NTRI * NKL + NKL * PN1; x += 32) {
-          float4 v = f4(0.f, 0.f, 0.f, 0.f);
-          if (x < NTRI * NKL) {
-            const int ti = x / NKL, kl = x % NKL;
-            const float* pf2 = PF2 + ti * NFN * NKL + kl;
+        {
+          auto item = [&](int x) {
+            float4 v = f4(0.f, 0.f, 0.f, 0.f);
+            if (x < NTRI * NKL) {
+              const int ti = x / NKL, kl = x % NKL;
+              const float* pf2 = PF2 + ti * NFN * NKL + kl;
 #pragma unroll 5
-            for (int n = 0; n < NFN; ++n) f4acc(v, pf2[n * NKL], F4[ti * NFN + n]);
-            G4[x] = v;
-          } else {
-            const int y = x - NTRI * NKL, kl = y / PN1, pp = y % PN1;
+              for (int n = 0; n < NFN; ++n) f4acc(v, pf2[n * NKL], F4[ti * NFN + n]);
+              G4[x] = v;
+            } else {
+              const int y = x - NTRI * NKL, kl = y / PN1, pp = y % PN1;
 #pragma unroll
-            for (int qq = 0; qq < PN1; ++qq) f4acc(v, LA[qq * NKL + kl], F4[NLT + pp + PN1 * qq]);
-            PZB[y] = v;
-          }
+              for (int qq = 0; qq < PN1; ++qq) f4acc(v, LA[qq * NKL + kl], F4[NLT + pp + PN1 * qq]);
+              PZB[y] = v;
+            }
+          };
+          for (int x = lane; x < NTRI * NKL; x += 32) item(x);   // one kind of item per warp pass
+          for (int x = NTRI * NKL + lane; x < NTRI * NKL + NKL * PN1; x += 32) item(x);
         }
         __syncwarp();
       }
