@@ -769,48 +769,53 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
       }
       if (T != DG_TET && !inner) lattice_values();
       __syncwarp();
-      for (int fq = lane; fq < NFX; fq += 32) {
-        int f, ci;
-        float4 tr, sg;
-        if (inner) {   // face, canonical index and face data only
-          if (LAT && fq < NLT) {
-            f = face_of_tri<T>(fq / NFN);
-            ci = tperm[code[f] * NFN + fq % NFN];
-            sg = A.sgeo2[(e * NF + f) * NQ];
+      {   // triangle-face points, then quad-face points: one kind per warp pass
+        auto point = [&](int fq) {
+          int f, ci;
+          float4 tr, sg;
+          if (inner) {   // face, canonical index and face data only
+            if (LAT && fq < NLT) {
+              f = face_of_tri<T>(fq / NFN);
+              ci = tperm[code[f] * NFN + fq % NFN];
+              sg = A.sgeo2[(e * NF + f) * NQ];
+            } else {
+              const int x = LAT ? fq - NLT : fq, idx = x % NQ;
+              f = LAT ? (T == DG_PYR ? 0 : 2 + x / NQ) : x / NQ;
+              ci = (!LAT && tri_of<T>(f) >= 0) ? idx : qperm[code[f] * NQ + idx];
+              sg = A.sgeo2[(e * NF + f) * NQ + idx];
+            }
+          } else if (LAT) {
+            lat_point(fq, f, ci, tr, sg);
           } else {
-            const int x = LAT ? fq - NLT : fq, idx = x % NQ;
-            f = LAT ? (T == DG_PYR ? 0 : 2 + x / NQ) : x / NQ;
-            ci = (!LAT && tri_of<T>(f) >= 0) ? idx : qperm[code[f] * NQ + idx];
+            f = fq / NQ;
+            const int idx = fq % NQ;
+            tr = trace_at(f, idx);
+            ci = tri_of<T>(f) >= 0 ? idx : qperm[code[f] * NQ + idx];
             sg = A.sgeo2[(e * NF + f) * NQ + idx];
           }
-        } else if (LAT) {
-          lat_point(fq, f, ci, tr, sg);
-        } else {
-          f = fq / NQ;
-          const int idx = fq % NQ;
-          tr = trace_at(f, idx);
-          ci = tri_of<T>(f) >= 0 ? idx : qperm[code[f] * NQ + idx];
-          sg = A.sgeo2[(e * NF + f) * NQ + idx];
-        }
-        const int64_t gs = A.side_off + e * NF + f;
-        const int nb = A.nbr[gs];
-        float pm, unm;
-        if (inner) {
-          pm = A.tin[(int64_t)nb * NQ + ci];
-          unm = A.tin[A.plane + (int64_t)nb * NQ + ci];
-        } else {
-          pm = tr.x;
-          unm = sg.x * tr.y + sg.y * tr.z + sg.z * tr.w;
-        }
-        float P = 0.f, UN = 0.f;
-        if (nb >= 0) {
-          P = A.tin[gs * NQ + ci];
-          UN = A.tin[A.plane + gs * NQ + ci];
-        }
-        const float ta = A.tau[gs];
-        float fp, fu;
-        flux(nb < 0, pm, unm, P, UN, A.tau_scale * ta, A.tau_scale / ta, T != DG_TET && A.skew, fp, fu);
-        F4[fq] = f4(sg.w * fp, sg.w * fu * sg.x, sg.w * fu * sg.y, sg.w * fu * sg.z);
+          const int64_t gs = A.side_off + e * NF + f;
+          const int nb = A.nbr[gs];
+          float pm, unm;
+          if (inner) {
+            pm = A.tin[(int64_t)nb * NQ + ci];
+            unm = A.tin[A.plane + (int64_t)nb * NQ + ci];
+          } else {
+            pm = tr.x;
+            unm = sg.x * tr.y + sg.y * tr.z + sg.z * tr.w;
+          }
+          float P = 0.f, UN = 0.f;
+          if (nb >= 0) {
+            P = A.tin[gs * NQ + ci];
+            UN = A.tin[A.plane + gs * NQ + ci];
+          }
+          const float ta = A.tau[gs];
+          float fp, fu;
+          flux(nb < 0, pm, unm, P, UN, A.tau_scale * ta, A.tau_scale / ta, T != DG_TET && A.skew, fp, fu);
+          F4[fq] = f4(sg.w * fp, sg.w * fu * sg.x, sg.w * fu * sg.y, sg.w * fu * sg.z);
+        };
+        constexpr int NTP = LAT ? NLT : NTRI * NQ;
+        for (int fq = lane; fq < NTP; fq += 32) point(fq);
+        for (int fq = NTP + lane; fq < NFX; fq += 32) point(fq);
       }
       __syncwarp();
       if (!LAT) {
@@ -993,28 +998,33 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
     auto emit = [&](float* tout) {
       if (T != DG_TET) lattice_values();
       __syncwarp();
-      for (int fq = lane; fq < NFX; fq += 32) {
-        int f, ci;
-        float4 tr, sg;
-        if (LAT) {
-          f = fq < NLT ? face_of_tri<T>(fq / NFN) : (T == DG_PYR ? 0 : 2 + (fq - NLT) / NQ);
-        } else {
-          f = fq / NQ;
-        }
-        const int64_t gs = A.side_off + e * NF + f;
-        const int nb = A.nbr[gs];
-        const int64_t dst = nb >= 0 ? (int64_t)nb : ((MODE == MODE_TRACE && A.wall_self) ? gs : -1);
-        if (dst < 0) continue;
-        if (LAT) {
-          lat_point(fq, f, ci, tr, sg);
-        } else {
-          const int idx = fq % NQ;
-          tr = trace_at(f, idx);
-          ci = tri_of<T>(f) >= 0 ? idx : qperm[code[f] * NQ + idx];
-          sg = A.sgeo2[(e * NF + f) * NQ + idx];
-        }
-        tout[dst * NQ + ci] = tr.x;
-        tout[A.plane + dst * NQ + ci] = sg.x * tr.y + sg.y * tr.z + sg.z * tr.w;
+      {   // triangle-face points, then quad-face points: one kind per warp pass
+        auto point = [&](int fq) {
+          int f, ci;
+          float4 tr, sg;
+          if (LAT) {
+            f = fq < NLT ? face_of_tri<T>(fq / NFN) : (T == DG_PYR ? 0 : 2 + (fq - NLT) / NQ);
+          } else {
+            f = fq / NQ;
+          }
+          const int64_t gs = A.side_off + e * NF + f;
+          const int nb = A.nbr[gs];
+          const int64_t dst = nb >= 0 ? (int64_t)nb : ((MODE == MODE_TRACE && A.wall_self) ? gs : -1);
+          if (dst < 0) return;
+          if (LAT) {
+            lat_point(fq, f, ci, tr, sg);
+          } else {
+            const int idx = fq % NQ;
+            tr = trace_at(f, idx);
+            ci = tri_of<T>(f) >= 0 ? idx : qperm[code[f] * NQ + idx];
+            sg = A.sgeo2[(e * NF + f) * NQ + idx];
+          }
+          tout[dst * NQ + ci] = tr.x;
+          tout[A.plane + dst * NQ + ci] = sg.x * tr.y + sg.y * tr.z + sg.z * tr.w;
+        };
+        constexpr int NTP = LAT ? NLT : NTRI * NQ;
+        for (int fq = lane; fq < NTP; fq += 32) point(fq);
+        for (int fq = NTP + lane; fq < NFX; fq += 32) point(fq);
       }
       __syncwarp();
     };
