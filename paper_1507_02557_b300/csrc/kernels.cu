@@ -943,6 +943,9 @@ static void launch_hexw_n(const Args& A, const HexMaps& M, cudaStream_t s) {
 // synchronises on its own named barrier, so the groups stay independent.  While a group computes
 // element g, the cp.async copies of the next element's state and side data (double-buffered), of
 // its inbox planes (after g's flux phase) and of its residual (after g's update) are in flight.
+#ifndef DG_HEXC_MINB
+#define DG_HEXC_MINB 1
+#endif
 template <int N, int MODE>
 struct HexC {
   static constexpr int n1 = N + 1, NP = n1 * n1 * n1, NQ = n1 * n1;
@@ -966,7 +969,7 @@ struct HexC {
 };
 
 template <int N, int MODE>
-__global__ void __launch_bounds__(HexC<N, MODE>::NT, 1) hexc_kernel(Args A) {
+__global__ void __launch_bounds__(HexC<N, MODE>::NT, DG_HEXC_MINB) hexc_kernel(Args A) {
   using H = HexC<N, MODE>;
   constexpr int n1 = H::n1, NP = H::NP, NQ = H::NQ, GT = H::GT, G = H::G, SD = H::SD;
   extern __shared__ __align__(16) unsigned char smem_raw[];

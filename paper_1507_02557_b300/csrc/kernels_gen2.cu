@@ -99,11 +99,11 @@ struct G2 {
   static constexpr int SMEM_CAP = 226 * 1024;
   static constexpr int NW_DEF = T == DG_PYR ? 28 : 16;
   static constexpr int WB_B = WB * 16;
-  // pyramid N <= 4: the first pass of the factorised face values as uniform work items, from a
+  // pyramid N <= 7: the first pass of the factorised face values as uniform work items, from a
   // block-shared table built at block start: per item the first node and the node stride (start |
-  // stride << 8) and N1 coefficients, zero past the item's level size (the padded terms read nodes
+  // stride << 16) and N1 coefficients, zero past the item's level size (the padded terms read nodes
   // that exist: the largest index is NP - 1)
-  static constexpr bool PTAB = T == DG_PYR && N <= 4;
+  static constexpr bool PTAB = T == DG_PYR && N <= 7;   // (N = 8, 9: the table would cost warps)
   static constexpr int PL1 = PTAB ? NTRI * NKL + NKL * N1 : 0;
   static constexpr int PT_B = PTAB ? (((PL1 * (N1 + 1) + NP) * 4 + 15) / 16) * 16 : 0;   // + node decode [NP]
   static constexpr int NW_SM = (SMEM_CAP - OPS_B - IOPS_B - PT_B) / WB_B;
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
       const bool alongi = face && (ti & 1);   // odd triangle faces sum over i, the others over j
       const float* src = face ? EF + ti * NKL + kb : LA + ((x - NTRI * NKL) % PN1) * NKL + kb;
       const float g = face ? 1.f : GC[k];
-      ptd[x] = (alongi ? off + l * k1 : off + l) | ((alongi ? 1 : k1) << 8);
+      ptd[x] = (alongi ? off + l * k1 : off + l) | ((alongi ? 1 : k1) << 16);
       for (int t = 0; t < PN1; ++t) pc[x * PN1 + t] = t < k1 ? g * src[t] : 0.f;
     }
     int* nd = const_cast<int*>(pnd);
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
       constexpr int PN1 = C::N1;
       if constexpr (C::PTAB) {
         for (int x = lane; x < C::PL1; x += 32) {
-          const int d = ptd[x], n0 = d & 255, ns = d >> 8;
+          const int d = ptd[x], n0 = d & 0xFFFF, ns = d >> 16;
           const float* pc = ptc + x * PN1;
           float4 v = f4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
