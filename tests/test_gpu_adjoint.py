@@ -31,8 +31,9 @@ def tiny():
     return layered_mesh(2, 2, 5, "HWHTK", seed=4, c_of_layer=lambda k: [1.0, 1.6, 0.8, 1.3, 1.1][k])
 
 
-@pytest.mark.parametrize("N", [1, 2, 3, 4])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 6])
 def test_adjoint_matches_oracle(lib, N):
+    """N = 6: the hexahedra run the column kernel (several warps per element)."""
     m = tiny()
     o = DGOracle(m, N)
     g = lib.Mesh(m, N)

@@ -54,7 +54,7 @@ def gpu_record(g, q0, dt, n):
     return out.cpu().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("N", [2, 4])
+@pytest.mark.parametrize("N", [2, 4, 6])
 def test_receiver_traces_match_oracle(lib, N):
     m = tiny()
     o = DGOracle(m, N)
