@@ -880,6 +880,28 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
         }
         __syncwarp();
       }
+      // tets whose operators stay in global memory: the lattice lift operator crosses from L2 in
+      // row chunks staged once per block iteration for all its warps (as the volume operator)
+      float4 lsum[R];
+      if constexpr (C::CHUNK && T == DG_TET) {
+        constexpr int CL = 4 * C::CM;   // rows of NP floats per chunk
+        float* schf = reinterpret_cast<float*>(sch);
+#pragma unroll
+        for (int r = 0; r < R; ++r) lsum[r] = f4(0.f, 0.f, 0.f, 0.f);
+        for (int x0 = 0; x0 < NLT; x0 += CL) {
+          const int xc = NLT - x0 < CL ? NLT - x0 : CL;
+          __syncthreads();
+          for (int y = threadIdx.x; y < xc * NP; y += blockDim.x) schf[y] = __ldg(Tn + (size_t)x0 * NP + y);
+          __syncthreads();
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int n = lane + 32 * r;
+            if (n >= NP) break;
+#pragma unroll 4
+            for (int xx = 0; xx < xc; ++xx) f4acc(lsum[r], schf[xx * NP + n], F4[x0 + xx]);
+          }
+        }
+      }
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int n = lane + 32 * r;
@@ -914,6 +936,8 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
 #pragma unroll
             for (int ia = 0; ia < WN1; ++ia)
               f4acc(sum, Ve[(qf * WN1 + ia) * WNT + mt], PB[(qf * WN1 + ia) * WN1 + j]);
+        } else if constexpr (C::CHUNK) {   // tet, lift from the staged chunks above
+          sum = lsum[r];
         } else {   // tet: lattice-point fluxes (Lf holds the face mass)
 #pragma unroll 4
           for (int x = 0; x < NLT; ++x) f4acc(sum, Tn[x * NP + n], F4[x]);
