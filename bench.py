@@ -335,8 +335,8 @@ def alg_bytes(t, N):
     mrf:   fused multi-rate fine substep (as mrc with one trace set written)
 
     Geometry: hex 21 trilinear coefficients (96 B with padding; metric terms and normals are
-    recomputed); wedge G and grad J / (2J) at its (N+1)^3 cubature points, (n, w J^s / sqrt J) and
-    1 / sqrt J at its 5 (N+1)^2 face points; pyramid G, J at its semi-nodal points, (n, J^s) once
+    recomputed); wedge 15 map coefficients (64 B with padding; the metric terms at the cubature
+    points are recomputed), (n, w J^s / sqrt J) and 1 / sqrt J at its 5 (N+1)^2 face points; pyramid G, J at its semi-nodal points, (n, J^s) once
     per triangle face and (n, w J^s) at the base's points; tet G, J (12 floats) and (n, J^s) once
     per face.  Face-flux points: quad faces (N+1)^2 GL points, tet and pyramid triangle faces their
     (N+1)(N+2)/2 lattice nodes, wedge triangle faces (N+1)^2 quadrature points."""
@@ -345,7 +345,7 @@ def alg_bytes(t, N):
     NP = [n1 ** 3, n1 * n1 * (N + 2) // 2, n1 * (N + 2) * (2 * N + 3) // 6, n1 * (N + 2) * (N + 3) // 6][t]
     nf = [6, 5, 5, 4][t]
     nfx = [6 * NQ, 5 * NQ, 4 * NFN + NQ, 4 * NFN][t]
-    geo = [96, n1 ** 3 * 48 + 5 * NQ * 16 + 5 * NQ * 4, NP * 40 + 4 * 16 + NQ * 16, 48 + 4 * 16][t]
+    geo = [96, 64 + 5 * NQ * 16 + 5 * NQ * 4, NP * 40 + 4 * 16 + NQ * 16, 48 + 4 * 16][t]
     side = nf * 12
     st = 16 * NP
     tr = 8 * nfx

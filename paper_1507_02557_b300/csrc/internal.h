@@ -21,9 +21,11 @@ struct TypeDev {
   int64_t side_off = 0;       // first global side index of the type (side = off + e*nf + f)
   float* c2 = nullptr;        // [K]
   float* geo = nullptr;       // hex [K][24] trilinear coefficients; tet [K][12] G,J;
-                              // pyramid [K][10][Np] G,J; wedge [K][12][nc] G, grad J/(2J)
-                              // (component-major within an element: lanes on consecutive
-                              // nodes / points read consecutive words)
+                              // pyramid [K][10][Np] G,J (component-major within an element:
+                              // lanes on consecutive nodes read consecutive words); wedge [K][16]
+                              // map coefficients x_r = a_r + s b_r, x_t = a_t + s b_t,
+                              // x_s = c + r b_r + t b_t (a_r, b_r, a_t, b_t, c, 0)
+  float* wpts = nullptr;      // wedge: cubature points, triangle (r, t) [nc / (N+1)][2], then s [N+1]
   float4* sgeo = nullptr;     // non-hex: [K*nf][nq] (n, w_q J^s [/sqrt J for the wedge])
   float* sisq = nullptr;      // wedge: [K*nf][nq] 1/sqrt(J) at face points
   float* ops = nullptr;       // volume operators (type-specific layout, see setup.cpp)

@@ -62,7 +62,53 @@ struct Args {
   int vol_np;
   // per-element LSRK step (element index of the type), NULL = dt
   const float* dtE;
+  const float* wpts;   // wedge cubature points (TypeDev::wpts)
 };
+
+// Wedge metric terms at reference point (r, s, t) from the element's map coefficients c[15]
+// (TypeDev::geo): g[0..8] = d(r,s,t)/d(x,y,z) row-major, g[9..11] = grad_x J / (2 J) (the LSC-DG
+// term of Sec. 2.3.3), with J the map's Jacobian determinant.
+__device__ __forceinline__ void wedge_metrics(const float* c, float r, float s, float t, float g[12]) {
+  float xr[3], xs[3], xt[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    xr[d] = fmaf(s, c[3 + d], c[d]);
+    xt[d] = fmaf(s, c[9 + d], c[6 + d]);
+    xs[d] = fmaf(t, c[9 + d], fmaf(r, c[3 + d], c[12 + d]));
+  }
+  auto cr = [](const float* a, const float* b, float* o) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+  };
+  float gr[3], gs[3], gt[3];
+  cr(xs, xt, gr);
+  cr(xt, xr, gs);
+  cr(xr, xs, gt);
+  const float J = xr[0] * gr[0] + xr[1] * gr[1] + xr[2] * gr[2];
+  const float iJ = 1.f / J;
+  // dJ/dr = det(x_rs, x_s, x_t) + det(x_r, x_ss, x_t) + ... with x_rr = x_ss = x_tt = x_rt = 0:
+  // dJ/dr = det(x_r, x_rs, x_t), dJ/ds = det(x_rs, x_s, x_t) + det(x_r, x_s, x_ts),
+  // dJ/dt = det(x_r, x_ts, x_t); x_rs = b_r, x_ts = b_t
+  const float* brs = c + 3;
+  const float* bts = c + 9;
+  float u[3];
+  cr(brs, xt, u);
+  const float Jr = xr[0] * u[0] + xr[1] * u[1] + xr[2] * u[2];
+  const float Js = brs[0] * gr[0] + brs[1] * gr[1] + brs[2] * gr[2] + bts[0] * gt[0] + bts[1] * gt[1] +
+                   bts[2] * gt[2];
+  cr(bts, xt, u);
+  const float Jt = xr[0] * u[0] + xr[1] * u[1] + xr[2] * u[2];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    g[d] = gr[d] * iJ;
+    g[3 + d] = gs[d] * iJ;
+    g[6 + d] = gt[d] * iJ;
+  }
+  const float h = 0.5f * iJ;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) g[9 + d] = h * (g[d] * Jr + g[3 + d] * Js + g[6 + d] * Jt);
+}
 
 __device__ __forceinline__ void flux(bool wall, float pm, float unm, float P, float UN, float tp,
                                      float tu, bool skew, float& fp, float& fu) {

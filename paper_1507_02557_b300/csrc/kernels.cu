@@ -1470,7 +1470,8 @@ __global__ void __launch_bounds__(128) gen_kernel(Args A) {
       const float* V = A.ops;                              // [NC][NP]
       const float* VT = A.ops + 4 * NC * NP;               // [NP][NC]
       const float* wq = A.ops + 8 * NC * NP;
-      const float* geo = A.geo + e * NC * 12;   // [12][NC]: component c of point q at c * NC + q
+      constexpr int NQT = NC / (N + 1);   // triangle points; point q = (q % NQT, q / NQT)
+      const float* wc = A.geo + e * 16;
       for (int q = tid; q < NC; q += NT) {
         float P = 0.f, Pa[3] = {0.f, 0.f, 0.f}, U[3] = {0.f, 0.f, 0.f};
         for (int m = 0; m < NP; ++m) {
@@ -1482,18 +1483,19 @@ __global__ void __launch_bounds__(128) gen_kernel(Args A) {
 #pragma unroll
           for (int a = 0; a < 3; ++a) Pa[a] += VT[(1 + a) * NC * NP + m * NC + q] * s_q[0][m];
         }
-        const float* g = geo + q;
+        float g[12];
+        wedge_metrics(wc, A.wpts[2 * (q % NQT)], A.wpts[2 * NQT + q / NQT], A.wpts[2 * (q % NQT) + 1], g);
         const float w = wq[q];
         float UJ = 0.f;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          float Ad = g[d * NC] * Pa[0] + g[(3 + d) * NC] * Pa[1] + g[(6 + d) * NC] * Pa[2] - P * g[(9 + d) * NC];
+          float Ad = g[d] * Pa[0] + g[3 + d] * Pa[1] + g[6 + d] * Pa[2] - P * g[9 + d];
           s_w[d][q] = w * Ad;
-          UJ += U[d] * g[(9 + d) * NC];
+          UJ += U[d] * g[9 + d];
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-          s_w[3 + a][q] = w * (g[3 * a * NC] * U[0] + g[(3 * a + 1) * NC] * U[1] + g[(3 * a + 2) * NC] * U[2]);
+          s_w[3 + a][q] = w * (g[3 * a] * U[0] + g[3 * a + 1] * U[1] + g[3 * a + 2] * U[2]);
         s_w[6][q] = w * UJ;
       }
       __syncthreads();
@@ -1692,6 +1694,7 @@ static Args make_args(dg_mesh* m, int t) {
   Args A{};
   A.plane = m->nsides * (int64_t)m->nq;
   A.geo = td.geo;
+  A.wpts = td.wpts;
   A.sgeo = td.sgeo;
   A.sisq = td.sisq;
   A.c2 = td.c2;

@@ -670,7 +670,9 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
         float4* Ys4 = W4 + NT * N1;       // phase 1: [NT][N1] sum_j D1 p (x); phase 2: ZB
         float4* X1 = W4 + 2 * NT * N1;    // [WXN] w (A0, A1, A2, UJ)
         float4* X2 = X1 + C::WXN;         // [WXN] w (GU0, GU1, GU2, 0)
-        const float* geo = A.geo + e * NC * 12;   // [12][NC]: component c of point q at c * NC + q
+        float wc[15];   // the element's map coefficients; metric terms rebuilt at each point
+#pragma unroll
+        for (int c = 0; c < 15; ++c) wc[c] = A.geo[e * 16 + c];
         for (int x = lane; x < NT * N1; x += 32) {
           const int mt = x / N1, l = x % N1;
           float4 y = f4(0.f, 0.f, 0.f, 0.f);
@@ -693,9 +695,8 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
         const int q0 = PL ? lp * NQ : 0, q1 = PL ? q0 + NQ : NC;
         for (int qc = q0 + lane; qc < q1; qc += 32) {
           const int qt = qc % NQ, l = qc / NQ;
-          float g[12];   // lanes read consecutive cubature points: coalesced; in flight during the sums
-#pragma unroll
-          for (int c = 0; c < 12; ++c) g[c] = geo[c * NC + qc];
+          float g[12];
+          wedge_metrics(wc, __ldg(A.wpts + 2 * qt), __ldg(A.wpts + 2 * NQ + l), __ldg(A.wpts + 2 * qt + 1), g);
           float P = 0.f, Pr = 0.f, Ps = 0.f, Pt = 0.f, U0 = 0.f, U1 = 0.f, U2 = 0.f;
           const float4* vrow = DV4 + qt * NT;
 #pragma unroll 5

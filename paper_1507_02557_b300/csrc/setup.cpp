@@ -652,8 +652,12 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
             wedge_w.push_back(tww[q] * sw[l]);
           }
         td.nc = (int)wedge_w.size();
+        std::vector<float> wp;   // triangle points (r, t), then the 1D points s
+        for (double v : tp) wp.push_back((float)v);
+        for (double v : sx) wp.push_back((float)v);
+        td.wpts = upload(wp, owned);
       }
-      const int gstride = t == HEX ? 24 : t == TET ? 12 : t == PYR ? 10 * Np : 12 * td.nc;
+      const int gstride = t == HEX ? 24 : t == TET ? 12 : t == PYR ? 10 * Np : 16;
       std::vector<float> geo((size_t)K * gstride, 0.f);
 #pragma omp parallel for schedule(dynamic, 256)
       for (int64_t e = 0; e < K; ++e) {
@@ -702,18 +706,31 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
             ge[9 * Np + n] = (float)J;
             jinvmax[t][e] = std::max(jinvmax[t][e], 1.0 / J);
           }
-        } else {  // wedge
+        } else {  // wedge: J > 0 at every cubature point; the kernels rebuild the metric terms
           for (int q = 0; q < td.nc; ++q) {
             map_jacobian(WEDGE, xv, &wedge_pts[3 * q], F);
             double J = inverse_metric(F, G);
             if (!(J > 0)) flag("wedge with J <= 0");
-            double gJ[3];
-            wedge_grad_J(xv, &wedge_pts[3 * q], gJ);
-            for (int i = 0; i < 9; ++i) ge[i * td.nc + q] = (float)G[i];   // [12][nc]: component-major
-            for (int dd = 0; dd < 3; ++dd) {
-              double gx = G[0 + dd] * gJ[0] + G[3 + dd] * gJ[1] + G[6 + dd] * gJ[2];
-              ge[(9 + dd) * td.nc + q] = (float)(gx / (2.0 * J));
+          }
+          // map coefficients: with lo / hi the bottom / top vertex of each triangle corner v,
+          // x_r = sum_v lr_v (lo + hi) / 2 + s sum_v lr_v (hi - lo) / 2 (likewise x_t with lt) and
+          // x_s = sum_v lam_v(r, t) (hi - lo) / 2, lam = (0, 1/2, 1/2) + r lr + t lt
+          const double lr[3] = {-0.5, 0.5, 0.0}, lt[3] = {-0.5, 0.0, 0.5}, l0[3] = {0.0, 0.5, 0.5};
+          for (int d = 0; d < 3; ++d) {
+            double ar = 0, br = 0, at = 0, bt = 0, cs = 0;
+            for (int v = 0; v < 3; ++v) {
+              const double lo = xv[3 * v + d], hi = xv[3 * (v + 3) + d];
+              ar += lr[v] * 0.5 * (lo + hi);
+              br += lr[v] * 0.5 * (hi - lo);
+              at += lt[v] * 0.5 * (lo + hi);
+              bt += lt[v] * 0.5 * (hi - lo);
+              cs += l0[v] * 0.5 * (hi - lo);
             }
+            ge[d] = (float)ar;
+            ge[3 + d] = (float)br;
+            ge[6 + d] = (float)at;
+            ge[9 + d] = (float)bt;
+            ge[12 + d] = (float)cs;
           }
         }
       }
