@@ -86,7 +86,12 @@ struct G2 {
   // pyramid: the volume products' scratch (3 NIT floats from F4 on) may run past the face buffers
   // (N = 9): extra float4 at the end of the warp's buffer
   static constexpr int PEX0 = T == DG_PYR ? 3 * NIT - 4 * (WB0 - NP - WV) : 0;
-  static constexpr int WB = WB0 + (PEX0 > 0 ? (PEX0 + 3) / 4 : 0);
+  // wedge N <= 4: the element's face-point data (sgeo2 [NF][NQ] float4, sisq2 [NF][NQ] float)
+  // copied into the end of the warp's buffer once per element (cp.async, during the volume
+  // terms) and read there by the flux pass and the trace passes
+  static constexpr bool WSG = T == DG_WEDGE && N <= 4;
+  static constexpr int WSGB = WSG ? NF * NQ + (NF * NQ + 3) / 4 : 0;
+  static constexpr int WB = WB0 + (PEX0 > 0 ? (PEX0 + 3) / 4 : 0) + WSGB;
   // tet / pyramid: the volume operator transposed, (D^T)[m][n] = D[n][m] as float4, follows the
   // operators in global memory at float offset OPS_T (host layout size NOPS)
   static constexpr int OPS_T = ((OPS + 3) / 4) * 4;
@@ -235,6 +240,8 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
   float4* V4 = G4 + NTRI * NFN;
   float4* PZB = V4 + NTRI * NFN;                                 // pyramid [NKL][N1]
   float4* PTQB = PZB + NKL * C::N1;                              // pyramid [NQ] base traces
+  float4* SGw = q4 + (C::WB - C::WSGB);                          // wedge (WSG): face data [NF][NQ]
+  float* SIw = reinterpret_cast<float*>(SGw + NF * NQ);          // wedge (WSG): 1/sqrt J [NF][NQ]
 
   // CHUNK: the block's warps walk their elements in step (lb is the block's first) and every warp
   // takes part in every operator chunk (block barriers); a warp past the end redoes the last
@@ -249,7 +256,33 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
     if (lane < NF) code[lane] = A.code[A.side_off + e * NF + lane];
     for (int n = lane; n < NP; n += 32)
       q4[n] = f4(A.q[base + n], A.q[A.ndof + base + n], A.q[2 * A.ndof + base + n], A.q[3 * A.ndof + base + n]);
+    if constexpr (C::WSG) {
+      const float4* sgs = A.sgeo2 + e * NF * NQ;
+      const float* sis = A.sisq2 + e * NF * NQ;
+      for (int x = lane; x < NF * NQ; x += 32) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(SGw + x)),
+                     "l"(sgs + x) : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(SIw + x)),
+                     "l"(sis + x) : "memory");
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
     __syncwarp();
+    // the element's face data: staged copies (wedge N <= 4) or global memory
+    auto face_ready = [&]() {
+      if constexpr (C::WSG) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncwarp();
+      }
+    };
+    auto sg_at = [&](int f, int idx) -> float4 {
+      if constexpr (C::WSG) return SGw[f * NQ + idx];
+      else return A.sgeo2[(e * NF + f) * NQ + idx];
+    };
+    auto is_at = [&](int f, int idx) -> float {
+      if constexpr (C::WSG) return SIw[f * NQ + idx];
+      else return A.sisq2[(e * NF + f) * NQ + idx];
+    };
 
     // wedge, factorised over triangle x 1D: lattice values of the two triangle faces (V4,
     // canonical order) and traces at the local GL points of the three quad faces (TQ), with
@@ -406,7 +439,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
         for (int m = 0; m < NP; ++m) f4acc(tr, row[m], q4[m]);
       }
       if (T == DG_WEDGE) {
-        const float is = A.sisq2[(e * NF + f) * NQ + idx];
+        const float is = is_at(f, idx);
         tr.x *= is; tr.y *= is; tr.z *= is; tr.w *= is;
       }
       return tr;
@@ -419,13 +452,13 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
         f = face_of_tri<T>(ti);
         tr = T == DG_TET ? q4[fnode[x]] : V4[x];
         ci = tperm[code[f] * NFN + nl];
-        sg = A.sgeo2[(e * NF + f) * NQ];
+        sg = sg_at(f, 0);
       } else {
         const int idx = (x - NLT) % NQ;
         f = T == DG_PYR ? 0 : 2 + (x - NLT) / NQ;
         tr = trace_at(f, idx);
         ci = qperm[code[f] * NQ + idx];
-        sg = A.sgeo2[(e * NF + f) * NQ + idx];
+        sg = sg_at(f, idx);
       }
     };
 
@@ -768,6 +801,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
         const int nbf = lane < NF ? A.nbr[A.side_off + e * NF + lane] : 0;
         inner = __all_sync(0xffffffffu, nbf >= 0);
       }
+      face_ready();
       if (T != DG_TET && !inner) lattice_values();
       __syncwarp();
       {   // triangle-face points, then quad-face points: one kind per warp pass
@@ -778,12 +812,12 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
             if (LAT && fq < NLT) {
               f = face_of_tri<T>(fq / NFN);
               ci = tperm[code[f] * NFN + fq % NFN];
-              sg = A.sgeo2[(e * NF + f) * NQ];
+              sg = sg_at(f, 0);
             } else {
               const int x = LAT ? fq - NLT : fq, idx = x % NQ;
               f = LAT ? (T == DG_PYR ? 0 : 2 + x / NQ) : x / NQ;
               ci = (!LAT && tri_of<T>(f) >= 0) ? idx : qperm[code[f] * NQ + idx];
-              sg = A.sgeo2[(e * NF + f) * NQ + idx];
+              sg = sg_at(f, idx);
             }
           } else if (LAT) {
             lat_point(fq, f, ci, tr, sg);
@@ -792,7 +826,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
             const int idx = fq % NQ;
             tr = trace_at(f, idx);
             ci = tri_of<T>(f) >= 0 ? idx : qperm[code[f] * NQ + idx];
-            sg = A.sgeo2[(e * NF + f) * NQ + idx];
+            sg = sg_at(f, idx);
           }
           const int64_t gs = A.side_off + e * NF + f;
           const int nb = A.nbr[gs];
@@ -1021,6 +1055,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
     }
     // traces of the state in q4 into the neighbours' inboxes
     auto emit = [&](float* tout) {
+      face_ready();
       if (T != DG_TET) lattice_values();
       __syncwarp();
       {   // triangle-face points, then quad-face points: one kind per warp pass
@@ -1042,7 +1077,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
             const int idx = fq % NQ;
             tr = trace_at(f, idx);
             ci = tri_of<T>(f) >= 0 ? idx : qperm[code[f] * NQ + idx];
-            sg = A.sgeo2[(e * NF + f) * NQ + idx];
+            sg = sg_at(f, idx);
           }
           tout[dst * NQ + ci] = tr.x;
           tout[A.plane + dst * NQ + ci] = sg.x * tr.y + sg.y * tr.z + sg.z * tr.w;
