@@ -318,7 +318,7 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-HEX_MRC_DRAM_BYTES_PER_ELEMENT = 969227776 / 73728   # 550,391,040 read + 418,836,736 written
+HEX_MRC_DRAM_BYTES_PER_ELEMENT = 879598336 / 73728   # 545,932,032 read + 333,666,304 written
 
 
 def alg_bytes(t, N):
@@ -331,7 +331,8 @@ def alg_bytes(t, N):
     stage: fused LSRK stage (q, res read and written; traces read and written)
     trace: trace-only launch (q read, traces written)
     mrc:   fused multi-rate coarse step (q, two history slots read; rhs, q written; traces read,
-           half-step and full-step traces written)
+           half-step and full-step traces written; the half-step set only by the coarse elements
+           with a fine face neighbour, the others' total is less by one trace set, `trace_set`)
     mrf:   fused multi-rate fine substep (as mrc with one trace set written)
 
     Geometry: hex 21 trilinear coefficients (96 B with padding; metric terms and normals are
@@ -351,7 +352,8 @@ def alg_bytes(t, N):
     tr = 8 * nfx
     trace_geo = [96, 5 * NQ * 4, 0, 0][t]
     return {"stage": 4 * st + 2 * tr + geo + side + 4, "trace": st + tr + trace_geo + side,
-            "mrc": 5 * st + 3 * tr + geo + side + 4, "mrf": 5 * st + 2 * tr + geo + side + 4}
+            "mrc": 5 * st + 3 * tr + geo + side + 4, "mrf": 5 * st + 2 * tr + geo + side + 4,
+            "trace_set": tr}
 
 
 def timed_run(g, torch, stream, steps, dt, barrier):
@@ -730,7 +732,9 @@ def main():
     value = stage_units / (ms / 1e3) / 1e9
     # hex kernels: one trace launch per dg_step call, then per coarse step the fused coarse
     # step of the coarse hexes and two fused substeps of the fine hexes
+    iface = g.level_type_counts(-1)   # coarse elements with a fine neighbour: they alone write half-step traces
     tb = [mesh.nelem[t] * ab[t]["trace"] + args.steps * ((mesh.nelem[t] - fine[t]) * ab[t]["mrc"]
+                                                         - (mesh.nelem[t] - fine[t] - iface[t]) * ab[t]["trace_set"]
                                                          + 2 * fine[t] * ab[t]["mrf"]) for t in range(4)]
     hex_bytes = tb[0]
     achieved = hex_bytes / (kms[0] / 1e3) / 1e9
@@ -827,7 +831,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(args.cells, ORDER, {
                     "integrator": "two-level multi-rate AB3 (step = one coarse step of 2h)",
-                    "ndof": ndof, "ndof_fine": ndof_fine, "elements": mesh.nelem, "fine_elements": fine,
+                    "ndof": ndof, "ndof_fine": ndof_fine, "elements": mesh.nelem, "fine_elements": fine, "coarse_elements_with_fine_neighbour": iface,
                     "h_fine": h, "parallelism": "replicas" if world > 1 else "single GPU"}),
                 "roofline": {"bound": "hbm", "kernel": "hexw_kernel<4,MRC> (fused multi-rate coarse step)",
                              "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,

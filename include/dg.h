@@ -112,7 +112,9 @@ dg_status dg_ndof(const dg_mesh *mesh, int64_t *ndof);
 /* Elements of each type (counts[4]: hex, wedge, pyramid, tet) in time-step
  * level `level` (1 = coarsest .. nlevels = finest, Sec. 2.4).  level = 0 on a
  * multi-rate LSRK mesh (integrator 1): the elements of S, the fine elements and
- * the coarse elements sharing a face with one. */
+ * the coarse elements sharing a face with one.  level = -1 on a two-level mesh: the
+ * coarse elements sharing a face with a fine element (the only ones whose half-step
+ * traces the fine substeps read, so the only ones that write them). */
 dg_status dg_level_counts(const dg_mesh *mesh, int level, int64_t *counts);
 
 /* Copy a state [4][ndof] into the mesh's state (and zero the LSRK residual).

@@ -170,6 +170,10 @@ dg_status dg_level_counts(const dg_mesh* m, int level, int64_t* counts) {
     for (int t = 0; t < 4; ++t) counts[t] = m->mr_s.count[t];
     return DG_OK;
   }
+  if (m && counts && level == -1 && m->nlevels == 2) {   // coarse elements next to fine ones
+    for (int t = 0; t < 4; ++t) counts[t] = m->mr_pred_count[t];
+    return DG_OK;
+  }
   if (!m || !counts || level < 1 || level > m->nlevels) return DG_EINVAL;
   for (int t = 0; t < 4; ++t) counts[t] = m->nlevels == 1 ? m->td[t].K : m->lev[level - 1].count[t];
   return DG_OK;

@@ -112,6 +112,10 @@ struct dg_mesh {
   int integrator = 0;
   dgk::Sel mr_s, mr_t, mr_tc;     // mr_tc: the coarse elements of T
   unsigned char* mr_in_s[4] = {nullptr, nullptr, nullptr, nullptr};
+  // two levels: 1 for a coarse element with a fine face neighbour (only those elements' half-step
+  // traces are read, by the fine substeps); counts per type
+  unsigned char* mr_pred[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t mr_pred_count[4] = {0, 0, 0, 0};
   float* mrl = nullptr;
   bool hex_sem = false;           // SEM hexahedra (GLL nodes)
   bool tri_lat = true;            // tet / pyramid triangle faces exchange lattice values (gen2)

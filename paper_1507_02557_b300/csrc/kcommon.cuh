@@ -63,6 +63,9 @@ struct Args {
   // per-element LSRK step (element index of the type), NULL = dt
   const float* dtE;
   const float* wpts;   // wedge cubature points (TypeDev::wpts)
+  // MRC: per element of the type, 1 if it has a fine face neighbour; the others skip the half-step
+  // traces, which no launch reads (NULL: every element writes them)
+  const unsigned char* pred;
 };
 
 // Wedge metric terms at reference point (r, s, t) from the element's map coefficients c[15]

@@ -845,12 +845,14 @@ __global__ void __launch_bounds__(128, DG_HEXP_MINB) hexw_kernel(Args A, const _
 #pragma unroll 1
     for (int pass = 0; pass < NPASS; ++pass) {
       float* tout = pass ? A.tout2 : A.tout;
-      if (act) {
+      // the half-step traces only where a fine neighbour reads them
+      const bool em = act && (MODE != MODE_MRC || pass == 1 || !A.pred || A.pred[e]);
+      if (em) {
 #pragma unroll
         for (int k = 0; k < n1; ++k) s_q[col + NQ * k] = make_float4(q[0][k], q[1][k], q[2][k], q[3][k]);
       }
       __syncwarp();
-      if (act) {
+      if (em) {
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
           float4 tm = make_float4(0.f, 0.f, 0.f, 0.f), tp = tm;
@@ -1724,6 +1726,7 @@ static Args make_args(dg_mesh* m, int t) {
   A.tau_scale = (float)m->tau_scale;
   A.skew = 1;
   A.dtE = m->dte[t];
+  A.pred = m->mr_pred[t];
   return A;
 }
 

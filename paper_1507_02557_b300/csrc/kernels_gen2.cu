@@ -1088,7 +1088,8 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
       }
       __syncwarp();
     };
-    if (MODE != MODE_RHS && act) emit(A.tout);
+    // (multi-rate coarse step: the half-step traces only where a fine neighbour reads them)
+    if (MODE != MODE_RHS && act && (MODE != MODE_MRC || !A.pred || A.pred[e])) emit(A.tout);
     if (MODE == MODE_MRC && act) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {

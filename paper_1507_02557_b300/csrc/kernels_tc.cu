@@ -443,7 +443,9 @@ __global__ void __launch_bounds__(512, 1) tet_tc_kernel(Args A) {
       for (int pass = 0; pass < (MODE == MODE_MRC ? 2 : 1); ++pass) {
         const float* qe = (pass ? sr : B.q) + el * 4 * NP;
         float* tout = pass ? A.tout2 : A.tout;
-        for (int y = t16; y < KL && e >= 0; y += 16) {
+        // (multi-rate coarse step: the half-step traces only where a fine neighbour reads them)
+        const bool em = e >= 0 && (MODE != MODE_MRC || pass == 1 || !A.pred || A.pred[e]);
+        for (int y = t16; y < KL && em; y += 16) {
           const int f = y / NFN, nl = y - f * NFN;
           const int nb = B.nb[el * 4 + f];
           if (nb < 0) continue;

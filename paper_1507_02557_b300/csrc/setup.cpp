@@ -1401,6 +1401,23 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
       }
       m->hist = alloc_zero<float>(3 * 4 * (size_t)m->ndof, owned);
       m->trace3 = alloc_zero<float>(2 * (size_t)side * nq, owned);
+      {   // coarse elements with a fine face neighbour: the readers of the half-step traces
+        std::vector<std::vector<unsigned char>> pred(4);
+        for (int t = 0; t < 4; ++t) pred[t].assign(m->td[t].K, 0);
+        for (int64_t s2 = 0; s2 < side; ++s2) {
+          if (nbr[s2] < 0) continue;
+          int t, f, t2, f2;
+          int64_t e, e2;
+          side_elem(s2, t, e, f);
+          side_elem(nbr[s2], t2, e2, f2);
+          if (level[t][e] == 1 && level[t2][e2] == 2) pred[t][e] = 1;
+        }
+        for (int t = 0; t < 4; ++t) {
+          m->mr_pred_count[t] = 0;
+          for (unsigned char v : pred[t]) m->mr_pred_count[t] += v;
+          m->mr_pred[t] = upload(pred[t], owned);
+        }
+      }
       if (d->integrator == 1) {
         // multi-rate LSRK element sets: S = fine + coarse next to fine, T = S + face neighbours of S
         std::vector<std::vector<unsigned char>> inS(4), inT(4);
