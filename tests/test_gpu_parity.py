@@ -147,6 +147,14 @@ def test_multirate_ab3_matches_oracle(lib, N):
     assert g.level_counts() == [sum(int(np.sum(l == L)) for l in lev) for L in (1, 2)]
     for L in (1, 2):
         assert g.level_type_counts(L) == [int(np.sum(l == L)) for l in lev]
+    # coarse elements with a fine face neighbour (the writers of the half-step traces)
+    iface = [set() for _ in range(4)]
+    for sd in o.geo.sides:
+        if sd.nbr >= 0:
+            nb = o.geo.sides[sd.nbr]
+            if lev[sd.t][sd.e] == 1 and lev[nb.t][nb.e] == 2:
+                iface[sd.t].add(sd.e)
+    assert g.level_type_counts(-1) == [len(x) for x in iface]
     h = g.timestep()
     assert abs(h - dmin) < 1e-12 * dmin
     q0 = o.project(standing_mode, 0.0).astype(np.float32)
