@@ -30,7 +30,8 @@ struct HexCfg {
   static constexpr int EPB = TPE >= 256 ? 1 : 256 / TPE;
   static constexpr int NT = TPE * EPB;
   // resident blocks per SM the register allocation aims at (measured best: N = 5..7: 8, 5, 3; one
-  // more block at N = 7 spills enough to lose; N = 8, 9: blocks of 736 / 1024 threads, one)
+  // more block at N = 7 spills enough to lose).  The launchers run this kernel at N = 5 only; N = 6..9
+  // run the column kernel hexc_kernel below.
   static constexpr int MINB = N >= 8 ? 1 : N == 7 ? 3 : N == 6 ? 5 : N == 5 ? 8 : 1;
 };
 
@@ -952,7 +953,7 @@ template <int N, int MODE>
 struct HexC {
   static constexpr int n1 = N + 1, NP = n1 * n1 * n1, NQ = n1 * n1;
   static constexpr int WPE = (NQ + 31) / 32, GT = WPE * 32;
-  static constexpr int G = WPE >= 3 ? 1 : 4 / WPE;        // N = 5..7: 2 groups of 2 warps; N = 8, 9: 1
+  static constexpr int G = WPE >= 3 ? 1 : 4 / WPE;        // N = 6, 7: 2 groups of 2 warps; N = 8, 9: 1
   static constexpr int NT = G * GT;
   static constexpr int NAUX = MODE == MODE_STAGE ? 1 : 0;
   static constexpr int SD = 44;   // geometry [24], nbr [6], code [6], tau [6], c2
