@@ -80,11 +80,13 @@ typedef struct {
   int precision;           /* volume products of tets and pyramids: 0 = FP32 (CUDA cores; tets at
                               N <= 4 on the tensor cores in TF32 x 3); 1 = BF16 x 3, 2 = FP16 x 3:
                               16-bit hi + lo split operands on the tensor cores, FP32 accumulation
-                              (about 2^-17 / 2^-22 relative per product); hexahedra, wedges and all
-                              face terms stay FP32.  1, 2 apply on meshes with the lattice face
-                              exchange (no wedge triangle face against a tet or pyramid), to types
-                              with at most 256 nodes (pyramids at N >= 8 stay FP32); the adjoint
-                              refuses them (DG_ENOTSUP) */
+                              (about 2^-17 / 2^-22 relative per product); hexahedra, the wedges'
+                              second contraction and metric terms, and all face terms stay FP32.
+                              Tets and pyramids: on meshes with the lattice face exchange (no wedge
+                              triangle face against a tet or pyramid), at most 256 nodes (pyramids
+                              at N >= 8 stay FP32).  Wedges: the triangle-mode to cubature-point
+                              contraction at N >= 7, single-rate and rhs calls.  The adjoint
+                              refuses 1, 2 (DG_ENOTSUP) */
   int integrator;          /* nlevels = 2: 0 = multi-rate Adams-Bashforth 3 (default),
                               1 = multi-rate LSRK(5,4) (see dg_step) */
 } dg_mesh_desc;

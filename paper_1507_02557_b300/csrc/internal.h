@@ -49,10 +49,13 @@ struct TmaArr {
 };
 bool tma_map_1d(TmaArr& t, const float* base, int64_t n, int box);   // kernels.cu
 
-// Tensor-core volume terms (precision 1 = BF16 x 3, 2 = FP16 x 3) of tets ([0]) and pyramids ([1]):
-// per element X = [W_r | W_s | W_t | p] (4 blocks of npk 16-bit values, hi and lo parts, scaled by
-// a power of two per row; xis = 1 / scale), Y = B X in FP32 (4 blocks of npp), B = the fixed block
-// operator (FP32 copy and its scaled hi / lo parts; bis = 1 / its scale).  Layout in kernels_prec.cu.
+// Tensor-core volume terms (precision 1 = BF16 x 3, 2 = FP16 x 3) of tets ([0]), pyramids ([1]) and
+// wedges ([2]): rows of X (kx 16-bit values, hi and lo parts, scaled by a power of two per row; xis =
+// 1 / scale), Y = B X in FP32 (nblk blocks of npp per row), B = the fixed block operator (FP32 copy
+// and its scaled hi / lo parts; bis = 1 / its scale).  Output block b reads X columns
+// [kb0[b], kb0[b] + kbn[b]) against B's rows [b npp, (b + 1) npp).  Tets and pyramids: a row per
+// element, X = [W_r | W_s | W_t | p] (4 blocks of npk); wedges: a row per element and 1D level l,
+// X = [y_p | y_s | y_u | y_v | y_w] (triangle-mode vectors).  Layouts in kernels_prec.cu.
 struct PrecDev {
   unsigned short *xh = nullptr, *xl = nullptr, *bh = nullptr, *bl = nullptr;
   float* xis = nullptr;
@@ -60,7 +63,10 @@ struct PrecDev {
   float* b32 = nullptr;
   int npk = 0, npp = 0;
   float bis = 1.f;
+  int nblk = 4, kx = 0;
+  int kb0[8] = {0, 0, 0, 0, 0, 0, 0, 0}, kbn[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
+__host__ __device__ inline int prec_slot(int t) { return t == DG_TET ? 0 : t == DG_PYR ? 1 : 2; }
 // 2D TMA descriptors of X (hi, lo: boxes of 8 values x 128 rows) and B (hi, lo: 8 x npp)
 struct PrecMaps {
   CUtensorMap xh, xl, bh, bl;
@@ -128,8 +134,8 @@ struct dg_mesh {
   // precision of the tet and pyramid volume products: 0 = FP32 (SIMT, or TF32 x 3 tensor-core tets
   // for N <= 4), 1 = BF16 x 3, 2 = FP16 x 3 on the tensor cores (kernels_prec.cu)
   int precision = 0;
-  dgk::PrecDev prec[2];
-  dgk::PrecMaps prec_maps[2];
+  dgk::PrecDev prec[3];
+  dgk::PrecMaps prec_maps[3];
   cudaStream_t tstream[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t tev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   // adjoint (adjoint.cu): host data kept by the setup, device copies made on first use
@@ -199,8 +205,8 @@ cudaError_t launch_seg_copy(const Seg* segs_dev, int nseg, cudaStream_t s);
 // Hex constants (1D D, V^f, GL weights and nodes) of order N <= 4 into constant memory.
 cudaError_t upload_hex_constants(int N, bool sem, const float* hc, int count);
 struct Args;
-// Tensor-core volume terms of type t (DG_TET / DG_PYR) for the elements of A (precision > 0): pack
-// X, Y = B X; sets A.vol, A.vol_np for the type's warp kernel (kernels_prec.cu).
+// Tensor-core volume terms of type t (DG_TET / DG_PYR / DG_WEDGE) for the elements of A (precision
+// > 0): pack X, Y = B X; sets A.vol, A.vol_np for the type's warp kernel (kernels_prec.cu).
 cudaError_t launch_prec_volume(dg_mesh* m, int t, Args& A, cudaStream_t s);
 // Scaled 16-bit hi / lo parts of the FP32 operator b into P.bh, P.bl (kernels_prec.cu).
 cudaError_t prec_split_operator(PrecDev& P, const float* b, bool bf, cudaStream_t s);

@@ -975,7 +975,7 @@ template <int N, int MODE>
 __global__ void __launch_bounds__(HexC<N, MODE>::NT, DG_HEXC_MINB) hexc_kernel(Args A) {
   using H = HexC<N, MODE>;
   constexpr int n1 = H::n1, NP = H::NP, NQ = H::NQ, GT = H::GT, G = H::G, SD = H::SD;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   float* sc = reinterpret_cast<float*>(smem_raw);
   const float* Dm = sc;
   const float* Vm = Dm + n1 * n1;
@@ -1341,16 +1341,16 @@ bool prec_maps(PrecMaps& M, const PrecDev& P, int64_t rows) {
   EncodeTiledFn enc = encode_fn();
   if (!enc || rows <= 0 || rows >= (1LL << 31)) return false;
   auto map2 = [&](CUtensorMap* m, const void* base, int64_t nrow, int box_rows) {
-    const cuuint64_t dim[2] = {static_cast<cuuint64_t>(4 * P.npk), static_cast<cuuint64_t>(nrow)};
-    const cuuint64_t stride[1] = {static_cast<cuuint64_t>(4 * P.npk * 2)};
+    const cuuint64_t dim[2] = {static_cast<cuuint64_t>(P.kx), static_cast<cuuint64_t>(nrow)};
+    const cuuint64_t stride[1] = {static_cast<cuuint64_t>(P.kx * 2)};
     const cuuint32_t boxd[2] = {8, static_cast<cuuint32_t>(box_rows)};
     const cuuint32_t es[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(base), dim, stride, boxd, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   };
-  return map2(&M.xh, P.xh, rows, 128) && map2(&M.xl, P.xl, rows, 128) && map2(&M.bh, P.bh, 4 * P.npp, P.npp) &&
-         map2(&M.bl, P.bl, 4 * P.npp, P.npp);
+  return map2(&M.xh, P.xh, rows, 128) && map2(&M.xl, P.xl, rows, 128) &&
+         map2(&M.bh, P.bh, (int64_t)P.nblk * P.npp, P.npp) && map2(&M.bl, P.bl, (int64_t)P.nblk * P.npp, P.npp);
 }
 
 // the registered array holding p (with p's offset in floats), or null
@@ -1473,7 +1473,7 @@ __global__ void __launch_bounds__(128) gen_kernel(Args A) {
       const float* V = A.ops;                              // [NC][NP]
       const float* VT = A.ops + 4 * NC * NP;               // [NP][NC]
       const float* wq = A.ops + 8 * NC * NP;
-      constexpr int NQT = NC / (N + 1);   // triangle points; point q = (q % NQT, q / NQT)
+      constexpr int NQT = NC / (N + 1) > 0 ? NC / (N + 1) : 1;   // triangle points; point q = (q % NQT, q / NQT)
       const float* wc = A.geo + e * 16;
       for (int q = tid; q < NC; q += NT) {
         float P = 0.f, Pa[3] = {0.f, 0.f, 0.f}, U[3] = {0.f, 0.f, 0.f};
@@ -1798,11 +1798,15 @@ static void launch_type(dg_mesh* m, const Args& A0, int t) {
     e0 = ev_take(m);
     cudaEventRecord(m->ev_pool[e0], s);
   }
-  // precision > 0: the volume products of tets and pyramids on the tensor cores in split 16-bit
-  // form, then the type's warp kernel with those products as input (lattice-exchange meshes)
+  // precision > 0: the volume products of tets and pyramids (lattice-exchange meshes) and the
+  // first contraction of the wedges' on the tensor cores in split 16-bit form, then the type's
+  // warp kernel with those products as input
   Args A = A0;
-  const bool tcv = m->precision > 0 && (t == DG_TET || t == DG_PYR) && MODE != MODE_TRACE && m->tri_lat &&
-                   m->prec[t == DG_TET ? 0 : 1].y != nullptr;
+  // (wedges: the warp kernel's fused multi-rate modes, which take the products, exist for N <= 4)
+  const bool tcv = m->precision > 0 && MODE != MODE_TRACE &&
+                   (((t == DG_TET || t == DG_PYR) && m->tri_lat) ||
+                    (t == DG_WEDGE && (MODE <= MODE_STAGE || m->N <= 4))) &&
+                   m->prec[prec_slot(t)].y != nullptr;
   if (tcv) launch_prec_volume(m, t, A, s);
   switch (m->N) {
 #define DG_CASE(NN)                                                   \

@@ -706,7 +706,7 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
         float wc[15];   // the element's map coefficients; metric terms rebuilt at each point
 #pragma unroll
         for (int c = 0; c < 15; ++c) wc[c] = A.geo[e * 16 + c];
-        for (int x = lane; x < NT * N1; x += 32) {
+        for (int x = lane; x < NT * N1 && !A.vol; x += 32) {
           const int mt = x / N1, l = x % N1;
           float4 y = f4(0.f, 0.f, 0.f, 0.f);
           float ys = 0.f;
@@ -731,17 +731,28 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
           float g[12];
           wedge_metrics(wc, __ldg(A.wpts + 2 * qt), __ldg(A.wpts + 2 * NQ + l), __ldg(A.wpts + 2 * qt + 1), g);
           float P = 0.f, Pr = 0.f, Ps = 0.f, Pt = 0.f, U0 = 0.f, U1 = 0.f, U2 = 0.f;
-          const float4* vrow = DV4 + qt * NT;
+          if (A.vol) {   // the tensor-core pass: row (li, l) holds the seven products at point qt
+            const float* yr = A.vol + ((int64_t)li * N1 + l) * 7 * A.vol_np + qt;
+            P = yr[0];
+            Pr = yr[A.vol_np];
+            Pt = yr[2 * A.vol_np];
+            Ps = yr[3 * A.vol_np];
+            U0 = yr[4 * A.vol_np];
+            U1 = yr[5 * A.vol_np];
+            U2 = yr[6 * A.vol_np];
+          } else {
+            const float4* vrow = DV4 + qt * NT;
 #pragma unroll 5
-          for (int mt = 0; mt < NT; ++mt) {
-            const float4 v = vrow[mt], y = Y4[mt * N1 + l];
-            P = fmaf(v.x, y.x, P);
-            Pr = fmaf(v.y, y.x, Pr);
-            Pt = fmaf(v.z, y.x, Pt);
-            Ps = fmaf(v.x, Ys4[mt * N1 + l].x, Ps);
-            U0 = fmaf(v.x, y.y, U0);
-            U1 = fmaf(v.x, y.z, U1);
-            U2 = fmaf(v.x, y.w, U2);
+            for (int mt = 0; mt < NT; ++mt) {
+              const float4 v = vrow[mt], y = Y4[mt * N1 + l];
+              P = fmaf(v.x, y.x, P);
+              Pr = fmaf(v.y, y.x, Pr);
+              Pt = fmaf(v.z, y.x, Pt);
+              Ps = fmaf(v.x, Ys4[mt * N1 + l].x, Ps);
+              U0 = fmaf(v.x, y.y, U0);
+              U1 = fmaf(v.x, y.z, U1);
+              U2 = fmaf(v.x, y.w, U2);
+            }
           }
           const float w = wq[qt * N1 + l];
           const float A0 = g[0] * Pr + g[3] * Ps + g[6] * Pt - P * g[9];

@@ -1,6 +1,6 @@
-// Tensor-core volume terms of tetrahedra and pyramids in split 16-bit precision (sm_103a).
+// Tensor-core volume terms of tetrahedra, pyramids and wedges in split 16-bit precision (sm_103a).
 //
-// The volume terms of both types are products of fixed reference operators with per-element
+// The volume terms of tets and pyramids are products of fixed reference operators with per-element
 // vectors (Alg. tet_vol, Sec. 2.3.2; Alg. pyr_vol, Sec. 2.3.4).  Per element, with the metric
 // terms G = d(rst)/d(xyz) (tet: constant; pyramid: at the semi-nodal points, with J):
 //   X = [ W_r | W_s | W_t | p ],   W_a = (G u)_a (tet),  W_a = J (G u)_a (pyramid)
@@ -27,6 +27,11 @@
 //   gen2_kernel   (kernels_gen2.cu) with Args.vol = Y
 // The output blocks of B are the four column blocks of Y: block 0 reads the W part of X (K =
 // 3 NPK), blocks 1..3 the p part (K = NPK), so the zero blocks of B are never multiplied.
+// Wedges at N >= 7 (Alg. wedge_vol1/2, Sec. 2.3.3, sum-factorised over triangle x 1D): the first
+// of their two contractions, triangle modes -> triangle cubature points, runs here on rows
+// (element, 1D level): wpack_kernel forms the level's triangle-mode vectors, vgemm_kernel the seven products
+// (seven output blocks of B, each reading one vector); the wedge warp kernel takes them as its
+// cubature-point values and does the metric terms and the second contraction as before.
 // Every mbarrier wait is bounded (~1 s of SM clock); on a timeout the CTA sets bit 0 of the
 // device error word, waits (bounded) for its copies and MMAs in flight and frees its tensor memory.
 #include <cuda.h>
@@ -145,6 +150,62 @@ __global__ void __launch_bounds__(256) pack_kernel(Args A, PrecDev P) {
   }
 }
 
+// ---------------------------------------------------------------------------- wedges
+// Rows (element li, 1D level l): the triangle-mode vectors of the first factor of the wedge's
+// sum-factorised volume terms (Alg. wedge_vol1/2): y_f[mt] = sum_j V1[l][j] q_f[mt + NT j] for the
+// four fields and y_s[mt] = sum_j D1[l][j] p[mt + NT j], laid out [y_p | y_s | y_u | y_v | y_w]
+// (blocks of NPK); Y = B X then holds, per row, the seven cubature-point products of level l
+// (V y_p, V_r y_p, V_t y_p, V y_s, V y_u, V y_v, V y_w at the NQ triangle points).
+template <int N, bool BF>
+__global__ void __launch_bounds__(256) wpack_kernel(Args A, PrecDev P) {
+  constexpr int N1 = N + 1, NT = N1 * (N + 2) / 2, NP = NT * N1, NQ = N1 * N1;
+  constexpr int NPK = (NT + 15) / 16 * 16, KX = 5 * NPK, NV = (KX + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float* V1 = A.ops2 + NQ * NT * 4;   // [N1 (l)][N1 (j)]
+  const float* D1 = V1 + N1 * N1;
+  for (int64_t li = w0; li < A.K; li += nw) {
+    const int64_t e = A.elist ? (int64_t)A.elist[li] : li;
+    const int64_t base = A.dof_off + e * NP;
+    for (int l = 0; l < N1; ++l) {
+      float v[NV];
+      float mx = 0.f;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        const int k = lane + 32 * i;
+        const int blk = k / NPK, mt = k - blk * NPK;
+        float s = 0.f;
+        if (k < KX && mt < NT) {
+          const int f = blk == 0 || blk == 1 ? 0 : blk - 1;   // field: p, p (D1), u, v, w
+          const float* c = blk == 1 ? D1 + l * N1 : V1 + l * N1;
+          const float* q = A.q + f * A.ndof + base + mt;
+#pragma unroll
+          for (int j = 0; j < N1; ++j) s = fmaf(c[j], q[NT * j], s);
+        }
+        v[i] = s;
+        mx = fmaxf(mx, fabsf(s));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      const float sc = mx > 0.f ? ldexpf(1.f, 14 - ilogbf(mx)) : 1.f;
+      const int64_t row = li * N1 + l;
+      unsigned short* xh = P.xh + row * KX;
+      unsigned short* xl = P.xl + row * KX;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        const int k = lane + 32 * i;
+        if (k >= KX) break;
+        const float x = sc * v[i];
+        const unsigned short h = rn16<BF>(x);
+        xh[k] = h;
+        xl[k] = rn16<BF>(x - f16f<BF>(h));
+      }
+      if (lane == 0) P.xis[row] = 1.f / sc;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------- Y = B X (tcgen05)
 constexpr int VG_BM = 128, VG_BK = 64, VG_ST = 2;
 
@@ -155,7 +216,7 @@ template <bool BF>
 __global__ void __launch_bounds__(128) vgemm_kernel(const __grid_constant__ PrecMaps G, PrecDev P, int M, int* err) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
-  const int npp = P.npp, npk = P.npk;
+  const int npp = P.npp;
   const int SA = VG_BM * VG_BK * 2, SB = npp * VG_BK * 2, SST = 2 * SA + 2 * SB;
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + VG_ST * SST);
   uint64_t* done = full + VG_ST;
@@ -163,8 +224,8 @@ __global__ void __launch_bounds__(128) vgemm_kernel(const __grid_constant__ Prec
   unsigned* tslot = reinterpret_cast<unsigned*>(fin + 1);
   volatile int* sbail = reinterpret_cast<volatile int*>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int mt = blockIdx.x >> 2, blk = blockIdx.x & 3;
-  const int k0 = blk == 0 ? 0 : 3 * npk, kn = blk == 0 ? 3 * npk : npk;
+  const int mt = blockIdx.x / P.nblk, blk = blockIdx.x % P.nblk;
+  const int k0 = P.kb0[blk], kn = P.kbn[blk];
   const int nch = (kn + VG_BK - 1) / VG_BK;
   const unsigned ncols = npp <= 32 ? 32 : npp <= 64 ? 64 : npp <= 128 ? 128 : 256;
   if (tid == 0) {
@@ -243,7 +304,7 @@ __global__ void __launch_bounds__(128) vgemm_kernel(const __grid_constant__ Prec
     const int row = mt * VG_BM + tid;
     const unsigned lb = tb + ((unsigned)(warp * 32) << 16);
     const float sc = row < M ? P.xis[row] * P.bis : 0.f;
-    float* yr = P.y + (int64_t)row * 4 * npp + blk * npp;
+    float* yr = P.y + (int64_t)row * P.nblk * npp + blk * npp;
     for (int ch = 0; ch < npp / 8; ++ch) {
       unsigned v[8];
       tld8(lb + ch * 8, v);
@@ -267,7 +328,7 @@ __global__ void __launch_bounds__(128) vgemm_kernel(const __grid_constant__ Prec
 }
 
 // ---------------------------------------------------------------------------- operator split
-// B (FP32, [4 NPP][4 NPK]) scaled by P.bs into its 16-bit hi and lo parts
+// B (FP32, [nblk NPP][kx]) scaled by 1 / P.bis into its 16-bit hi and lo parts
 template <bool BF>
 __global__ void split_op_kernel(const float* b, unsigned short* bh, unsigned short* bl, int64_t n, float s) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -279,10 +340,17 @@ __global__ void split_op_kernel(const float* b, unsigned short* bh, unsigned sho
 }
 
 cudaError_t prec_split_operator(PrecDev& P, const float* b, bool bf, cudaStream_t s) {
-  const int64_t n = 4LL * P.npp * 4 * P.npk;
+  const int64_t n = (int64_t)P.nblk * P.npp * P.kx;
   if (bf) split_op_kernel<true><<<256, 256, 0, s>>>(b, P.bh, P.bl, n, 1.f / P.bis);
   else split_op_kernel<false><<<256, 256, 0, s>>>(b, P.bh, P.bl, n, 1.f / P.bis);
   return cudaGetLastError();
+}
+
+template <int N, bool BF>
+static void wpack_n(const Args& A, const PrecDev& P, cudaStream_t s, int sms) {
+  const int64_t blocks = ((int64_t)A.K * 32 + 255) / 256;
+  const int grid = (int)(blocks < 16 * sms ? blocks : 16 * sms);
+  wpack_kernel<N, BF><<<grid, 256, 0, s>>>(A, P);
 }
 
 template <int T, int N, bool BF>
@@ -294,8 +362,8 @@ static void pack_n(const Args& A, const PrecDev& P, cudaStream_t s, int sms) {
 
 // pack, multiply; afterwards Args.vol / vol_np point at Y for the type's warp kernel
 cudaError_t launch_prec_volume(dg_mesh* m, int t, Args& A, cudaStream_t s) {
-  PrecDev& P = m->prec[t == DG_TET ? 0 : 1];
-  const PrecMaps& G = m->prec_maps[t == DG_TET ? 0 : 1];
+  PrecDev& P = m->prec[prec_slot(t)];
+  const PrecMaps& G = m->prec_maps[prec_slot(t)];
   const bool bf = m->precision == 1;
   static int sms = 0;
   if (sms == 0) {
@@ -307,7 +375,8 @@ cudaError_t launch_prec_volume(dg_mesh* m, int t, Args& A, cudaStream_t s) {
 #define PK_CASE(NN)                                                             \
   case NN:                                                                      \
     if (t == DG_TET) bf ? pack_n<DG_TET, NN, true>(A, P, s, sms) : pack_n<DG_TET, NN, false>(A, P, s, sms); \
-    else bf ? pack_n<DG_PYR, NN, true>(A, P, s, sms) : pack_n<DG_PYR, NN, false>(A, P, s, sms);             \
+    else if (t == DG_PYR) bf ? pack_n<DG_PYR, NN, true>(A, P, s, sms) : pack_n<DG_PYR, NN, false>(A, P, s, sms); \
+    else bf ? wpack_n<NN, true>(A, P, s, sms) : wpack_n<NN, false>(A, P, s, sms);                          \
     break;
     PK_CASE(1) PK_CASE(2) PK_CASE(3) PK_CASE(4) PK_CASE(5) PK_CASE(6) PK_CASE(7) PK_CASE(8) PK_CASE(9)
 #undef PK_CASE
@@ -321,9 +390,10 @@ cudaError_t launch_prec_volume(dg_mesh* m, int t, Args& A, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr[bf] = true;
   }
-  const int mtiles = (A.K + VG_BM - 1) / VG_BM;
-  if (bf) vgemm_kernel<true><<<mtiles * 4, 128, smem, s>>>(G, P, A.K, m->derr);
-  else vgemm_kernel<false><<<mtiles * 4, 128, smem, s>>>(G, P, A.K, m->derr);
+  const int rows = t == DG_WEDGE ? A.K * (m->N + 1) : A.K;   // wedges: a row per element and 1D level
+  const int mtiles = (rows + VG_BM - 1) / VG_BM;
+  if (bf) vgemm_kernel<true><<<mtiles * P.nblk, 128, smem, s>>>(G, P, rows, m->derr);
+  else vgemm_kernel<false><<<mtiles * P.nblk, 128, smem, s>>>(G, P, rows, m->derr);
   A.vol = P.y;
   A.vol_np = P.npp;
   return cudaGetLastError();

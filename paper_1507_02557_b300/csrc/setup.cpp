@@ -1305,15 +1305,35 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
         td.iops2 = upload(i2, owned);
         td.nops2 = (int)o2.size();
         td.niops2 = (int)i2.size();
+        // the operands of Y = B X in split 16-bit form, Y, and the TMA descriptors of X and B
+        auto prec_buffers = [&](dgk::PrecDev& P, const std::vector<float>& b, int64_t rows) {
+          P.b32 = upload(b, owned);
+          P.bh = alloc_zero<unsigned short>(b.size(), owned);
+          P.bl = alloc_zero<unsigned short>(b.size(), owned);
+          P.xh = alloc_zero<unsigned short>((size_t)rows * P.kx, owned);
+          P.xl = alloc_zero<unsigned short>((size_t)rows * P.kx, owned);
+          P.xis = alloc_zero<float>((size_t)rows, owned);
+          P.y = alloc_zero<float>((size_t)rows * P.nblk * P.npp, owned);
+          if (dgk::prec_split_operator(P, P.b32, d->precision == 1, nullptr) != cudaSuccess ||
+              !dgk::prec_maps(m->prec_maps[dgk::prec_slot(t)], P, rows))
+            throw SetupError(DG_ECUDA, "tensor-core operands: operator split or TMA descriptors failed");
+        };
         if (d->precision > 0 && (t == TET || t == PYR) && td.K > 0 && !g_host_only && Np <= 256) {
           // tensor-core volume products (kernels_prec.cu), for Np <= 256 (one MMA's N and one TMA
           // box; pyramids at N >= 8 keep the FP32 path): the block operator B [4 npp][4 npk] from
-          // D^a[x][y] = o2[(x Np + y) 4 + a]: block 0 (sum_a D^a W_a; pyramid (D^a)^T), blocks
-          // 1..3 (D^a p)
-          dgk::PrecDev& P = m->prec[t == TET ? 0 : 1];
+          // D^a[x][y] = o2[(x Np + y) 4 + a]: block 0 (sum_a D^a W_a; pyramid (D^a)^T) reads the
+          // three field columns of X, blocks 1..3 (D^a p) its p columns
+          dgk::PrecDev& P = m->prec[dgk::prec_slot(t)];
           P.npk = (Np + 15) / 16 * 16;
           P.npp = P.npk;
           const int npk = P.npk, npp = P.npp;
+          P.nblk = 4;
+          P.kx = 4 * npk;
+          const int kb0[4] = {0, 3 * npk, 3 * npk, 3 * npk}, kbn[4] = {3 * npk, npk, npk, npk};
+          for (int bb = 0; bb < 4; ++bb) {
+            P.kb0[bb] = kb0[bb];
+            P.kbn[bb] = kbn[bb];
+          }
           std::vector<float> b((size_t)4 * npp * 4 * npk, 0.f);
           float bmax = 0.f;
           // D^a[x][y]: tets from DV4 (o2), pyramids from the dense host operators (ops: D[a][x][y])
@@ -1330,16 +1350,38 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
               }
           P.bis = bmax > 0.f ? std::ldexp(1.f, std::ilogb(bmax) - 14) : 1.f;   // operator scaled into [2^14, 2^15)
           const int64_t rows = (td.K + 127) / 128 * 128;
-          P.b32 = upload(b, owned);
-          P.bh = alloc_zero<unsigned short>(b.size(), owned);
-          P.bl = alloc_zero<unsigned short>(b.size(), owned);
-          P.xh = alloc_zero<unsigned short>((size_t)rows * 4 * npk, owned);
-          P.xl = alloc_zero<unsigned short>((size_t)rows * 4 * npk, owned);
-          P.xis = alloc_zero<float>((size_t)rows, owned);
-          P.y = alloc_zero<float>((size_t)rows * 4 * npp, owned);
-          if (dgk::prec_split_operator(P, P.b32, d->precision == 1, nullptr) != cudaSuccess ||
-              !dgk::prec_maps(m->prec_maps[t == TET ? 0 : 1], P, rows))
-            throw SetupError(DG_ECUDA, "tensor-core operands: operator split or TMA descriptors failed");
+          prec_buffers(P, b, rows);
+        } else if (d->precision > 0 && t == WEDGE && td.K > 0 && !g_host_only && N >= 7) {
+          // wedges, N >= 7: the first contraction of the sum-factorised volume term (triangle
+          // modes -> triangle cubature points) on the tensor cores (at N = 5 the X / Y round trip
+          // through memory costs more than the FP32 contraction it replaces).  A row of X per
+          // (element, 1D level l) holds five triangle-mode vectors [V1 p | D1 p | V1 u | V1 v | V1 w]
+          // (npk columns each);
+          // B has seven blocks of npp cubature points: V, V_r, V_t against V1 p; V against D1 p,
+          // V1 u, V1 v, V1 w, with V/V_r/V_t[qt][mt] = o2[(qt NT + mt) 4 + {0, 1, 2}]
+          const int ntri = Np / n1, nqt = n1 * n1;
+          dgk::PrecDev& P = m->prec[dgk::prec_slot(t)];
+          P.npk = (ntri + 15) / 16 * 16;
+          P.npp = (nqt + 15) / 16 * 16;
+          const int npk = P.npk, npp = P.npp;
+          P.nblk = 7;
+          P.kx = 5 * npk;
+          const int xblk[7] = {0, 0, 0, 1, 2, 3, 4}, comp[7] = {0, 1, 2, 0, 0, 0, 0};
+          std::vector<float> b((size_t)7 * npp * 5 * npk, 0.f);
+          float bmax = 0.f;
+          for (int bb = 0; bb < 7; ++bb) {
+            P.kb0[bb] = xblk[bb] * npk;
+            P.kbn[bb] = npk;
+            for (int qt = 0; qt < nqt; ++qt)
+              for (int mt = 0; mt < ntri; ++mt) {
+                const float v = o2[((size_t)qt * ntri + mt) * 4 + comp[bb]];
+                b[(size_t)(bb * npp + qt) * 5 * npk + xblk[bb] * npk + mt] = v;
+                bmax = std::max(bmax, std::fabs(v));
+              }
+          }
+          P.bis = bmax > 0.f ? std::ldexp(1.f, std::ilogb(bmax) - 14) : 1.f;
+          const int64_t rows = (td.K * n1 + 127) / 128 * 128;
+          prec_buffers(P, b, rows);
         }
       }
     }

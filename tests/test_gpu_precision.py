@@ -1,5 +1,5 @@
-"""Tensor-core volume products of tets and pyramids in split 16-bit precision (precision 1 = BF16 x 3,
-2 = FP16 x 3) against the FP64 oracle.
+"""Tensor-core volume products of tets and pyramids, and the first volume contraction of the wedges,
+in split 16-bit precision (precision 1 = BF16 x 3, 2 = FP16 x 3) against the FP64 oracle.
 
 Tolerances from the arithmetic of the split (x = x_hi + x_lo, product x_hi b_hi + x_hi b_lo +
 x_lo b_hi accumulated in FP32):
