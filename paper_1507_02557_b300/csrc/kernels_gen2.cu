@@ -764,21 +764,50 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
                            w * (g[6] * U0 + g[7] * U1 + g[8] * U2), 0.f);
         }
         __syncwarp();
-        // Z of plane l overwrites Y of plane l, whose last reads precede the warp barrier above
-        for (int x = lane; x < NT * (PL ? 1 : N1); x += 32) {
+        // Z of plane l overwrites Y of plane l, whose last reads precede the warp barrier above.
+        // Items (mt, l) one per lane in full warp passes; plane by plane (N >= 5), the ZR items
+        // left over share the warp, ZS lanes each (strided over the points, then a butterfly sum
+        // over those lanes): N = 7, 36 items, takes 32 + 4 x 8 lanes instead of 32 + 4
+        constexpr int ZI = NT * (PL ? 1 : N1), ZF = ZI / 32 * 32, ZR = ZI - ZF;
+        constexpr int ZS = !PL || ZR == 0 ? 1 : ZR <= 2 ? 16 : ZR <= 4 ? 8 : ZR <= 8 ? 4 : ZR <= 16 ? 2 : 1;
+        constexpr int ZL = ZS > 1 ? ZF : ZI;   // items taken one per lane
+        auto zitem = [&](int x, int part, int step, float4& za, float& zr, float& zs) {
           const int mt = PL ? x : x / N1, l = PL ? lp : x % N1;
           const int xo = PL ? 0 : NQ * l;
-          float4 za = f4(0.f, 0.f, 0.f, 0.f);
-          float zr = 0.f, zs = 0.f;
 #pragma unroll 5
-          for (int qt = 0; qt < NQ; ++qt) {
+          for (int qt = part; qt < NQ; qt += step) {
             const float4 v = DV4[qt * NT + mt], x1 = X1[qt + xo], x2 = X2[qt + xo];
             f4acc(za, v.x, x1);
             zr = fmaf(v.y, x2.x, fmaf(v.z, x2.z, zr));
             zs = fmaf(v.x, x2.y, zs);
           }
+        };
+        auto zstore = [&](int x, const float4& za, float zr, float zs) {
+          const int mt = PL ? x : x / N1, l = PL ? lp : x % N1;
           ZA[mt * N1 + l] = za;
           ZB[mt * N1 + l] = f4(zr, zs, 0.f, 0.f);
+        };
+        for (int x = lane; x < ZL; x += 32) {
+          float4 za = f4(0.f, 0.f, 0.f, 0.f);
+          float zr = 0.f, zs = 0.f;
+          zitem(x, 0, 1, za, zr, zs);
+          zstore(x, za, zr, zs);
+        }
+        if constexpr (ZS > 1) {
+          const int x = ZF + lane / ZS, part = lane % ZS;
+          float4 za = f4(0.f, 0.f, 0.f, 0.f);
+          float zr = 0.f, zs = 0.f;
+          if (x < ZI) zitem(x, part, ZS, za, zr, zs);
+#pragma unroll
+          for (int o = ZS / 2; o > 0; o >>= 1) {
+            za.x += __shfl_xor_sync(0xffffffffu, za.x, o);
+            za.y += __shfl_xor_sync(0xffffffffu, za.y, o);
+            za.z += __shfl_xor_sync(0xffffffffu, za.z, o);
+            za.w += __shfl_xor_sync(0xffffffffu, za.w, o);
+            zr += __shfl_xor_sync(0xffffffffu, zr, o);
+            zs += __shfl_xor_sync(0xffffffffu, zs, o);
+          }
+          if (x < ZI && part == 0) zstore(x, za, zr, zs);
         }
         __syncwarp();
         }
