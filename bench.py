@@ -448,8 +448,9 @@ PREC_NAMES = {0: "fp32", 1: "bf16x3", 2: "fp16x3"}
 
 def high_order_run(dg, torch, stream, barrier, world, mesh, max_ms, steps=5):
     """The throughput mesh at N = 5 and N = 7 (75.9M / 177.8M DOFs), single-rate LSRK(5,4), with
-    the tet and pyramid volume products in FP32 on the CUDA cores (precision 0) and on the tensor
-    cores in split BF16 / FP16 (precision 1, 2): GDOF-stage/s and the kernel time per element type."""
+    the tet and pyramid volume products (and at N = 7 the wedges' first contraction) in FP32 on
+    the CUDA cores (precision 0) and on the tensor cores in split BF16 / FP16 (precision 1, 2):
+    GDOF-stage/s and the kernel time per element type."""
     from paper_1507_02557_b300.inputs import random_state
     out = {}
     for N in (5, 7):

@@ -55,9 +55,13 @@ struct Args {
   const float* h2;
   float ab0, ab1, ab2, pr0, pr1, pr2;
   float* tout2;
-  // tensor-core volume terms (precision > 0, tets and pyramids): row li of vol holds, for the
-  // element of list index li, [sum_a D^a w_a | D^r p | D^s p | D^t p] (pyramid: the first block
-  // with the transposes (D^a)^T), each block vol_np floats wide; NULL = computed in the kernel
+  // tensor-core volume terms (precision > 0), each block vol_np floats wide; NULL = computed in
+  // the kernel.  Tets and pyramids: row li (element of list index li) holds
+  // [sum_a D^a w_a | D^r p | D^s p | D^t p] (pyramid: the first block with the transposes
+  // (D^a)^T).  Wedges: row li (N + 1) + l (1D level l) holds the seven products at the triangle
+  // cubature points [V y_p | V_r y_p | V_t y_p | V y_s | V y_u | V y_v | V y_w], y_f the
+  // triangle-mode vector of field f at level l (the 1D factor V1 applied; y_s: its derivative D1
+  // applied to p)
   const float* vol;
   int vol_np;
   // per-element LSRK step (element index of the type), NULL = dt
