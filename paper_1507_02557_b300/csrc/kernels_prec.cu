@@ -360,8 +360,11 @@ static void pack_n(const Args& A, const PrecDev& P, cudaStream_t s, int sms) {
   pack_kernel<T, N, BF><<<grid, 256, 0, s>>>(A, P);
 }
 
-// pack, multiply; afterwards Args.vol / vol_np point at Y for the type's warp kernel
+// pack, multiply; afterwards Args.vol / vol_np point at Y for the type's warp kernel.  An empty
+// selection launches nothing.  A launch error is left pending (not cleared) for the launch group's
+// check, and Args.vol stays NULL then (the warp kernel forms its products itself).
 cudaError_t launch_prec_volume(dg_mesh* m, int t, Args& A, cudaStream_t s) {
+  if (A.K == 0) return cudaSuccess;
   PrecDev& P = m->prec[prec_slot(t)];
   const PrecMaps& G = m->prec_maps[prec_slot(t)];
   const bool bf = m->precision == 1;
@@ -394,9 +397,12 @@ cudaError_t launch_prec_volume(dg_mesh* m, int t, Args& A, cudaStream_t s) {
   const int mtiles = (rows + VG_BM - 1) / VG_BM;
   if (bf) vgemm_kernel<true><<<mtiles * P.nblk, 128, smem, s>>>(G, P, rows, m->derr);
   else vgemm_kernel<false><<<mtiles * P.nblk, 128, smem, s>>>(G, P, rows, m->derr);
-  A.vol = P.y;
-  A.vol_np = P.npp;
-  return cudaGetLastError();
+  const cudaError_t e = cudaPeekAtLastError();
+  if (e == cudaSuccess) {
+    A.vol = P.y;
+    A.vol_np = P.npp;
+  }
+  return e;
 }
 
 }  // namespace dgk
