@@ -726,34 +726,36 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
 #pragma unroll 1
         for (int lp = 0; lp < (PL ? N1 : 1); ++lp) {
         const int q0 = PL ? lp * NQ : 0, q1 = PL ? q0 + NQ : NC;
-        for (int qc = q0 + lane; qc < q1; qc += 32) {
+        // the seven first-contraction products at point qc (modes mt = part, part + step, ...)
+        auto wprod = [&](int qc, int part, int step, float (&pr)[7]) {
           const int qt = qc % NQ, l = qc / NQ;
-          float g[12];
-          wedge_metrics(wc, __ldg(A.wpts + 2 * qt), __ldg(A.wpts + 2 * NQ + l), __ldg(A.wpts + 2 * qt + 1), g);
-          float P = 0.f, Pr = 0.f, Ps = 0.f, Pt = 0.f, U0 = 0.f, U1 = 0.f, U2 = 0.f;
+#pragma unroll
+          for (int c = 0; c < 7; ++c) pr[c] = 0.f;
           if (A.vol) {   // the tensor-core pass: row (li, l) holds the seven products at point qt
             const float* yr = A.vol + ((int64_t)li * N1 + l) * 7 * A.vol_np + qt;
-            P = yr[0];
-            Pr = yr[A.vol_np];
-            Pt = yr[2 * A.vol_np];
-            Ps = yr[3 * A.vol_np];
-            U0 = yr[4 * A.vol_np];
-            U1 = yr[5 * A.vol_np];
-            U2 = yr[6 * A.vol_np];
+#pragma unroll
+            for (int c = 0; c < 7; ++c) pr[c] = yr[c * A.vol_np];
           } else {
             const float4* vrow = DV4 + qt * NT;
 #pragma unroll 5
-            for (int mt = 0; mt < NT; ++mt) {
+            for (int mt = part; mt < NT; mt += step) {
               const float4 v = vrow[mt], y = Y4[mt * N1 + l];
-              P = fmaf(v.x, y.x, P);
-              Pr = fmaf(v.y, y.x, Pr);
-              Pt = fmaf(v.z, y.x, Pt);
-              Ps = fmaf(v.x, Ys4[mt * N1 + l].x, Ps);
-              U0 = fmaf(v.x, y.y, U0);
-              U1 = fmaf(v.x, y.z, U1);
-              U2 = fmaf(v.x, y.w, U2);
+              pr[0] = fmaf(v.x, y.x, pr[0]);              // V y_p
+              pr[1] = fmaf(v.y, y.x, pr[1]);              // V_r y_p
+              pr[2] = fmaf(v.z, y.x, pr[2]);              // V_t y_p
+              pr[3] = fmaf(v.x, Ys4[mt * N1 + l].x, pr[3]);   // V y_s
+              pr[4] = fmaf(v.x, y.y, pr[4]);              // V y_u, V y_v, V y_w
+              pr[5] = fmaf(v.x, y.z, pr[5]);
+              pr[6] = fmaf(v.x, y.w, pr[6]);
             }
           }
+        };
+        // metric terms at point qc and the weighted intermediates X1, X2
+        auto wout = [&](int qc, const float (&pr)[7]) {
+          const int qt = qc % NQ, l = qc / NQ;
+          float g[12];
+          wedge_metrics(wc, __ldg(A.wpts + 2 * qt), __ldg(A.wpts + 2 * NQ + l), __ldg(A.wpts + 2 * qt + 1), g);
+          const float P = pr[0], Pr = pr[1], Pt = pr[2], Ps = pr[3], U0 = pr[4], U1 = pr[5], U2 = pr[6];
           const float w = wq[qt * N1 + l];
           const float A0 = g[0] * Pr + g[3] * Ps + g[6] * Pt - P * g[9];
           const float A1 = g[1] * Pr + g[4] * Ps + g[7] * Pt - P * g[10];
@@ -762,6 +764,27 @@ __global__ void __launch_bounds__(G2<T, N>::NW * 32, 1) gen2_kernel(Args A) {
           X1[qc - q0] = f4(w * A0, w * A1, w * A2, w * UJ);
           X2[qc - q0] = f4(w * (g[0] * U0 + g[1] * U1 + g[2] * U2), w * (g[3] * U0 + g[4] * U1 + g[5] * U2),
                            w * (g[6] * U0 + g[7] * U1 + g[8] * U2), 0.f);
+        };
+        // points one per lane in full warp passes; plane by plane (N >= 5) and without the
+        // tensor-core products, the QR points left over share the warp, QS lanes each (strided
+        // over the modes, then a butterfly sum): N = 5, 36 points, take 32 + 4 x 8 lanes
+        constexpr int QI = PL ? NQ : NC, QF = QI / 32 * 32, QR = QI - QF;
+        constexpr int QS = !PL || QR == 0 ? 1 : QR <= 2 ? 16 : QR <= 4 ? 8 : QR <= 8 ? 4 : QR <= 16 ? 2 : 1;
+        const bool qsplit = QS > 1 && !A.vol;
+        for (int qc = q0 + lane; qc < (qsplit ? q0 + QF : q1); qc += 32) {
+          float pr[7];
+          wprod(qc, 0, 1, pr);
+          wout(qc, pr);
+        }
+        if (QS > 1 && qsplit) {
+          const int qc = q0 + QF + lane / QS, part = lane % QS;
+          float pr[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          if (qc < q1) wprod(qc, part, QS, pr);
+#pragma unroll
+          for (int o = QS / 2; o > 0; o >>= 1)
+#pragma unroll
+            for (int c = 0; c < 7; ++c) pr[c] += __shfl_xor_sync(0xffffffffu, pr[c], o);
+          if (qc < q1 && part == 0) wout(qc, pr);
         }
         __syncwarp();
         // Z of plane l overwrites Y of plane l, whose last reads precede the warp barrier above.
