@@ -45,8 +45,22 @@ def trace_constant(t, N, measure="euclid", lobatto=False):
     return float(scipy.linalg.eigh(Ms, M, eigvals_only=True)[-1])
 
 
-def markov_constant(t, N):
-    """C_M(N) of Table markovConsts: largest eigenvalue of K v = lambda M v."""
+def markov_constant(t, N, lobatto=False):
+    """C_M(N) of Table markovConsts: largest eigenvalue of K v = lambda M v.
+
+    lobatto (hexahedron only): the SEM hexahedron of Sec. 2.1.1, whose inner product is the GLL
+    quadrature at its (N+1)^3 nodes, for the mass and the stiffness alike (M = diag(w),
+    K = D^T diag(w) D with D the nodal gradients at the nodes).  The table's hexahedron row is
+    this constant (it is not the one of Q_N in the exact L2 inner product)."""
+    if lobatto:
+        if t != 0:
+            raise ValueError("lobatto applies to the hexahedron only")
+        el = make_element(t, N, True)
+        G = el.grad(el.nodes)                     # (3, Np, Np): d l_j / d r_a at node q
+        W = el.wnodes
+        M = np.diag(W)
+        K = np.einsum("q,aqi,aqj->ij", W, G, G)
+        return float(scipy.linalg.eigh(K, M, eigvals_only=True)[-1])
     el = make_element(t, N)
     P, W = el.exact_rule(N + 2)
     B = el.basis(P)

@@ -120,6 +120,16 @@ def test_markov_constants_table(name):
         assert abs(markov_constant(TYPES[name], N) - tab[N - 1]) < 0.006 * max(1, tab[N - 1] / 100), (name, N)
 
 
+def test_markov_constants_table_hex_sem():
+    """Table markovConsts, hexahedron row (N = 1..9): the SEM hexahedron's constant, its mass and
+    stiffness both in the GLL quadrature of its nodes.  The same Q_N space in the exact L2 inner
+    product gives other values (9, 45, 127.6 at N = 1..3), so the row pins that reading."""
+    tab = read_table("markov_constants.txt")["hex"]
+    for N in range(1, 10):
+        assert abs(markov_constant(0, N, lobatto=True) - tab[N - 1]) < 0.006 * max(1, tab[N - 1] / 100), N
+    assert abs(markov_constant(0, 1) - 9.0) < 1e-9 and abs(markov_constant(0, 2) - 45.0) < 1e-9
+
+
 def test_trace_constant_needs_euclidean_face_measure():
     """With unit-area faces the tet value would differ from the table (documents the reading)."""
     assert abs(trace_constant(3, 1, measure="unit") - 12.22) > 1.0
