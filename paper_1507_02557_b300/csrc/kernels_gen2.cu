@@ -21,6 +21,12 @@
 // Volume terms: Alg. tet_vol (strong form, constant metrics), Alg. pyr_vol (skew
 // form with transposed operators), Alg. wedge_vol1/2 (LSC-DG skew form at the
 // wedge cubature points).  Flux, walls and M^{-1} as in kernels.cu.
+// The wedge's volume term is sum-factorised over triangle x 1D: the triangle modes of each 1D
+// level are contracted to the triangle cubature points (or taken from the tensor-core pass,
+// Args.vol), the metric terms are applied point by point, and a second contraction takes the
+// points back to the modes; at N >= 5 one 1D plane of points at a time.  Where a plane's points
+// or modes leave a partial warp pass, the leftover items share the warp (several lanes each,
+// then a butterfly sum).
 #include <cuda_runtime.h>
 
 #include "kcommon.cuh"
