@@ -97,6 +97,29 @@ def test_multirate_matches_oracle(lib, precision):
     assert rel(got, q) < TOL[precision], per_type(o, got, q)
 
 
+@pytest.mark.parametrize("N", [5, 7])
+def test_multirate_unfused_matches_oracle(lib, N):
+    """Start-up + 3 coarse MRAB3 steps at N = 5, 7 (FP16 x 3): the unfused schedule evaluates the
+    rhs on each level's element lists, so the tensor-core pass packs and multiplies only the
+    listed elements (at N = 7 the wedges' too; this mesh has no fine wedges, an empty list)."""
+    from oracle.constants import trace_constant
+    from oracle.dg import MRAB3, mr_levels, standing_mode
+    m = layered_mesh(3, 3, 5, "HWHTK", seed=3, c_of_layer=lambda k: 1.0 if k % 2 == 0 else 1.5)
+    o = DGOracle(m, N)
+    lev, _ = mr_levels(o, [trace_constant(t, N) for t in range(4)], 2)
+    g = lib.Mesh(m, N, nlevels=2, precision=2)
+    h = g.timestep()
+    q0 = o.project(standing_mode, 0.0).astype(np.float32)
+    g.set_state(q0, on_device=False)
+    g.step(3, h)
+    got = g.get_state(np.zeros_like(q0), on_device=False).astype(np.float64)
+    mr = MRAB3(o, lev)
+    q, hist = mr.start(q0.astype(np.float64), h)
+    for _ in range(3):
+        q, hist = mr.step(q, hist, h)
+    assert rel(got, q) < TOL[2], per_type(o, got, q)
+
+
 @pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("N", [3, 5])
 def test_error_against_exact_mode(lib, N, precision):
