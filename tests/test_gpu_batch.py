@@ -2,8 +2,8 @@
 
 * Bit-for-bit equality with the same meshes stepped one by one through dg_step in the
   chunking the batch documents (nsteps mod 3 steps, then chunks of 3), for a mix of N,
-  element types, time-step levels and hex node sets (GL and SEM hexahedra of the same N
-  in one batch).
+  element types, time-step levels, hex node sets (GL and SEM hexahedra of the same N
+  in one batch) and precision modes (two N = 7 FP16 x 3 meshes packed together).
 * The batched result of one small mesh against the FP64 oracle (relative L2 <= 1e-5).
 * Graph reuse: a second call with the same step sizes and history phases replays the
   cached graph; a call that shifts the multi-rate phase causes one new capture.
@@ -27,22 +27,25 @@ def lib():
     return dg
 
 
-# (mesh factory, N, nlevels, hex_basis): N = 2..5, LSRK and multi-rate, fused and unfused
-# multi-rate schedules, GL and SEM hexahedra at N = 4 side by side
+# (mesh factory, N, nlevels, hex_basis, precision): N = 2..5, LSRK and multi-rate, fused and
+# unfused multi-rate schedules, GL and SEM hexahedra at N = 4 side by side; two N = 7 meshes
+# with FP16 x 3 tensor-core products (tets, pyramids, wedges) that the batch packs together
 CASES = [
-    (lambda: small_hybrid_mesh(), 3, 1, 0),
-    (lambda: layered_mesh(3, 3, 5, "HWHTK", seed=3, c_of_layer=lambda k: 1.0 if k % 2 == 0 else 1.5), 4, 2, 0),
-    (lambda: layered_mesh(3, 3, 5, "HWHTK", seed=3, c_of_layer=lambda k: 1.0 if k % 2 == 0 else 1.5), 4, 2, 1),
-    (lambda: layered_mesh(5, 3, 6, "HHWHTK", seed=5), 2, 1, 0),
-    (lambda: layered_mesh(3, 2, 6, "HTKKUH", seed=2), 4, 1, 1),
-    (lambda: layered_mesh(3, 3, 5, "HWHTK", seed=3, c_of_layer=lambda k: 1.0 if k % 2 == 0 else 1.5), 5, 2, 0),
+    (lambda: small_hybrid_mesh(), 3, 1, 0, 0),
+    (lambda: layered_mesh(3, 3, 5, "HWHTK", seed=3, c_of_layer=lambda k: 1.0 if k % 2 == 0 else 1.5), 4, 2, 0, 0),
+    (lambda: layered_mesh(3, 3, 5, "HWHTK", seed=3, c_of_layer=lambda k: 1.0 if k % 2 == 0 else 1.5), 4, 2, 1, 0),
+    (lambda: layered_mesh(5, 3, 6, "HHWHTK", seed=5), 2, 1, 0, 0),
+    (lambda: layered_mesh(3, 2, 6, "HTKKUH", seed=2), 4, 1, 1, 0),
+    (lambda: layered_mesh(3, 3, 5, "HWHTK", seed=3, c_of_layer=lambda k: 1.0 if k % 2 == 0 else 1.5), 5, 2, 0, 0),
+    (lambda: small_hybrid_mesh(), 7, 1, 0, 2),
+    (lambda: layered_mesh(3, 3, 5, "HWHTK", seed=4), 7, 1, 0, 2),
 ]
 
 
 def make(lib, i):
-    fac, N, nl, hb = CASES[i]
+    fac, N, nl, hb, prec = CASES[i]
     m = fac()
-    g = lib.Mesh(m, N, nlevels=nl, hex_basis=hb)
+    g = lib.Mesh(m, N, nlevels=nl, hex_basis=hb, precision=prec)
     q0 = random_state(g.ndof, 40 + i).astype(np.float32)
     g.set_state(q0, on_device=False)
     return g, m, q0
