@@ -97,6 +97,24 @@ def test_multirate_matches_oracle(lib, precision):
     assert rel(got, q) < TOL[precision], per_type(o, got, q)
 
 
+@pytest.mark.parametrize("N", [6, 7])
+def test_sem_rhs_matches_oracle(lib, N):
+    """SEM hexahedra (GLL nodes; GLL points on the quadrilateral faces of wedges and pyramids too)
+    with FP16 x 3 products at N = 6, 7 (the column hex kernel; at N = 7 the wedges' tensor-core
+    pass with the SEM face rules around it)."""
+    m = small_hybrid_mesh()
+    o = DGOracle(m, N, hex_basis="gll")
+    q32 = random_state(o.ndof, 19).astype(np.float32)
+    want = o.rhs(q32.astype(np.float64))
+    g = lib.Mesh(m, N, hex_basis=1, precision=2)
+    qd = torch.from_numpy(q32).cuda()
+    rd = torch.zeros_like(qd)
+    g.rhs(qd, rd)
+    got = rd.cpu().numpy().astype(np.float64)
+    errs = per_type(o, got, want)
+    assert rel(got, want) < TOL[2] and max(errs) < TOL[2], errs
+
+
 @pytest.mark.parametrize("N", [5, 7])
 def test_multirate_unfused_matches_oracle(lib, N):
     """Start-up + 3 coarse MRAB3 steps at N = 5, 7 (FP16 x 3): the unfused schedule evaluates the
