@@ -97,6 +97,27 @@ def test_multirate_matches_oracle(lib, precision):
     assert rel(got, q) < TOL[precision], per_type(o, got, q)
 
 
+@pytest.mark.parametrize("N", [7, 9])
+def test_single_wedge_against_a_tet(lib, N):
+    """One wedge and one tet sharing a triangle face (the quadrature-point face exchange; the tet
+    keeps its FP32 kernel there): the wedge's tensor-core pass on a single element, 8 or 10 rows
+    of one 128-row tile."""
+    from paper_1507_02557_b300.inputs import HybridMesh
+    xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 0, 1], [0, 1, 0], [1, 1, 0], [0, 1, 1], [0, -1, 0]], float)
+    conn = [np.zeros((0, 8), np.int32), np.array([[0, 1, 2, 3, 4, 5]], np.int32),
+            np.zeros((0, 5), np.int32), np.array([[0, 1, 2, 6]], np.int32)]
+    m = HybridMesh(xyz=xyz, conn=conn, c2=[np.zeros(0), np.array([1.0]), np.zeros(0), np.array([2.25])])
+    o = DGOracle(m, N)
+    q32 = random_state(o.ndof, 23).astype(np.float32)
+    want = o.rhs(q32.astype(np.float64))
+    g = lib.Mesh(m, N, precision=2)
+    qd = torch.from_numpy(q32).cuda()
+    rd = torch.zeros_like(qd)
+    g.rhs(qd, rd)
+    got = rd.cpu().numpy().astype(np.float64)
+    assert rel(got, want) < TOL[2], per_type(o, got, want)
+
+
 @pytest.mark.parametrize("N", [6, 7])
 def test_sem_rhs_matches_oracle(lib, N):
     """SEM hexahedra (GLL nodes; GLL points on the quadrilateral faces of wedges and pyramids too)
