@@ -85,6 +85,15 @@ def test_host_setup_rejects_bad_meshes():
         dg.host_check(neg, 2)
 
 
+@pytest.mark.parametrize("kw", [dict(precision=3), dict(precision=-1), dict(hex_basis=2), dict(nlevels=3),
+                                dict(integrator=2)])
+def test_mesh_create_rejects_unbuilt_options_before_touching_a_device(kw):
+    """dg_mesh_create checks the descriptor's options first: an option value that is not built
+    returns DG_ENOTSUP with a message naming the built ones, also on a machine without a GPU."""
+    with pytest.raises(dg.DGError, match="not supported"):
+        dg.Mesh(small_hybrid_mesh(), 2, **kw)
+
+
 def test_host_setup_multirate_levels_match_oracle():
     """Sec. 2.4 level binning and neighbour smoothing: library vs oracle element counts."""
     from oracle.dg import mr_levels
