@@ -131,8 +131,9 @@ struct dg_mesh {
   bool type_streams = false;
   // kernel choices (dg_autotune): TMA staging of the fused N = 4 hex kernels, tensor-core tets
   bool use_hex_tma = true, use_tet_tc = true;
-  // precision of the tet and pyramid volume products: 0 = FP32 (SIMT, or TF32 x 3 tensor-core tets
-  // for N <= 4), 1 = BF16 x 3, 2 = FP16 x 3 on the tensor cores (kernels_prec.cu)
+  // precision of the tet and pyramid volume products and the wedges' first contraction: 0 = FP32
+  // (SIMT, or TF32 x 3 tensor-core tets for N <= 4), 1 = BF16 x 3, 2 = FP16 x 3 on the tensor cores
+  // (kernels_prec.cu)
   int precision = 0;
   dgk::PrecDev prec[3];
   dgk::PrecMaps prec_maps[3];

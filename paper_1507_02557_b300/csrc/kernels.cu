@@ -1799,10 +1799,10 @@ static void launch_type(dg_mesh* m, const Args& A0, int t) {
     cudaEventRecord(m->ev_pool[e0], s);
   }
   // precision > 0: the volume products of tets and pyramids (lattice-exchange meshes) and the
-  // first contraction of the wedges' on the tensor cores in split 16-bit form, then the type's
-  // warp kernel with those products as input
+  // wedges' first contraction on the tensor cores in split 16-bit form, then the type's warp
+  // kernel with those products as input.  (The wedge warp kernel's fused multi-rate modes exist
+  // for N <= 4 only; at higher N those modes run a kernel that forms its own products.)
   Args A = A0;
-  // (wedges: the warp kernel's fused multi-rate modes, which take the products, exist for N <= 4)
   const bool tcv = m->precision > 0 && MODE != MODE_TRACE &&
                    (((t == DG_TET || t == DG_PYR) && m->tri_lat) ||
                     (t == DG_WEDGE && (MODE <= MODE_STAGE || m->N <= 4))) &&
