@@ -29,9 +29,9 @@
 // 3 NPK), blocks 1..3 the p part (K = NPK), so the zero blocks of B are never multiplied.
 // Wedges at N >= 7 (Alg. wedge_vol1/2, Sec. 2.3.3, sum-factorised over triangle x 1D): the first
 // of their two contractions, triangle modes -> triangle cubature points, runs here on rows
-// (element, 1D level): wpack_kernel forms the level's triangle-mode vectors, vgemm_kernel the seven products
-// (seven output blocks of B, each reading one vector); the wedge warp kernel takes them as its
-// cubature-point values and does the metric terms and the second contraction as before.
+// (element, 1D level): wpack_kernel forms the level's triangle-mode vectors, vgemm_kernel the
+// seven products (seven output blocks of B, each reading one vector); the wedge warp kernel takes
+// them as its cubature-point values and does the metric terms and the second contraction.
 // Every mbarrier wait is bounded (~1 s of SM clock); on a timeout the CTA sets bit 0 of the
 // device error word, waits (bounded) for its copies and MMAs in flight and frees its tensor memory.
 #include <cuda.h>

@@ -1356,9 +1356,8 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
           // modes -> triangle cubature points) on the tensor cores (at N = 5 the X / Y round trip
           // through memory costs more than the FP32 contraction it replaces).  A row of X per
           // (element, 1D level l) holds five triangle-mode vectors [V1 p | D1 p | V1 u | V1 v | V1 w]
-          // (npk columns each);
-          // B has seven blocks of npp cubature points: V, V_r, V_t against V1 p; V against D1 p,
-          // V1 u, V1 v, V1 w, with V/V_r/V_t[qt][mt] = o2[(qt NT + mt) 4 + {0, 1, 2}]
+          // (npk columns each); B has seven blocks of npp cubature points: V, V_r, V_t against V1 p;
+          // V against D1 p, V1 u, V1 v, V1 w, with V/V_r/V_t[qt][mt] = o2[(qt NT + mt) 4 + {0, 1, 2}]
           const int ntri = Np / n1, nqt = n1 * n1;
           dgk::PrecDev& P = m->prec[dgk::prec_slot(t)];
           P.npk = (ntri + 15) / 16 * 16;
