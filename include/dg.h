@@ -83,9 +83,8 @@ typedef struct {
                               (about 2^-17 / 2^-22 relative per product); hexahedra, the wedges'
                               second contraction and metric terms, and all face terms stay FP32.
                               Tets and pyramids: on meshes with the lattice face exchange (no wedge
-                              triangle face against a tet or pyramid), at most 256 nodes (pyramids
-                              at N >= 8 stay FP32).  Wedges: the triangle-mode to cubature-point
-                              contraction at N >= 7, single-rate and rhs calls.  The adjoint
+                              triangle face against a tet or pyramid), any N.  Wedges: the
+                              triangle-mode to cubature-point contraction at N >= 7.  The adjoint
                               refuses 1, 2 (DG_ENOTSUP) */
   int integrator;          /* nlevels = 2: 0 = multi-rate Adams-Bashforth 3 (default),
                               1 = multi-rate LSRK(5,4) (see dg_step) */

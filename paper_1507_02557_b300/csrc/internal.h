@@ -65,6 +65,8 @@ struct PrecDev {
   float bis = 1.f;
   int nblk = 4, kx = 0;
   int kb0[8] = {0, 0, 0, 0, 0, 0, 0, 0}, kbn[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int vnp = 0;   // width of a block of Y as the warp kernel reads it (npp, or 2 npp when each of
+                 // the four tet / pyramid blocks is computed in two halves: pyramids above 256 nodes)
 };
 __host__ __device__ inline int prec_slot(int t) { return t == DG_TET ? 0 : t == DG_PYR ? 1 : 2; }
 // 2D TMA descriptors of X (hi, lo: boxes of 8 values x 128 rows) and B (hi, lo: 8 x npp)

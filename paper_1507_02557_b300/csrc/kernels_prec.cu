@@ -400,7 +400,7 @@ cudaError_t launch_prec_volume(dg_mesh* m, int t, Args& A, cudaStream_t s) {
   const cudaError_t e = cudaPeekAtLastError();
   if (e == cudaSuccess) {
     A.vol = P.y;
-    A.vol_np = P.npp;
+    A.vol_np = P.vnp;
   }
   return e;
 }

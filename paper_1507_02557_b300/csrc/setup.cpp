@@ -1318,23 +1318,26 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
               !dgk::prec_maps(m->prec_maps[dgk::prec_slot(t)], P, rows))
             throw SetupError(DG_ECUDA, "tensor-core operands: operator split or TMA descriptors failed");
         };
-        if (d->precision > 0 && (t == TET || t == PYR) && td.K > 0 && !g_host_only && Np <= 256) {
-          // tensor-core volume products (kernels_prec.cu), for Np <= 256 (one MMA's N and one TMA
-          // box; pyramids at N >= 8 keep the FP32 path): the block operator B [4 npp][4 npk] from
+        if (d->precision > 0 && (t == TET || t == PYR) && td.K > 0 && !g_host_only && Np <= 512) {
+          // tensor-core volume products (kernels_prec.cu): the block operator B [4 npl][4 npk] from
           // D^a[x][y] = o2[(x Np + y) 4 + a]: block 0 (sum_a D^a W_a; pyramid (D^a)^T) reads the
-          // three field columns of X, blocks 1..3 (D^a p) its p columns
+          // three field columns of X, blocks 1..3 (D^a p) its p columns.  One MMA's N and one TMA
+          // box hold at most 256 rows of B: above 256 nodes (pyramids at N = 8, 9) each block is
+          // computed in two halves of npp rows (eight GEMM blocks, the same X columns per pair)
           dgk::PrecDev& P = m->prec[dgk::prec_slot(t)];
+          const int halves = Np <= 256 ? 1 : 2;
           P.npk = (Np + 15) / 16 * 16;
-          P.npp = P.npk;
-          const int npk = P.npk, npp = P.npp;
-          P.nblk = 4;
+          P.npp = halves == 1 ? P.npk : ((Np + 1) / 2 + 15) / 16 * 16;
+          const int npk = P.npk, npl = halves * P.npp;   // npl: a block's width in Y
+          P.vnp = npl;
+          P.nblk = 4 * halves;
           P.kx = 4 * npk;
-          const int kb0[4] = {0, 3 * npk, 3 * npk, 3 * npk}, kbn[4] = {3 * npk, npk, npk, npk};
-          for (int bb = 0; bb < 4; ++bb) {
-            P.kb0[bb] = kb0[bb];
-            P.kbn[bb] = kbn[bb];
-          }
-          std::vector<float> b((size_t)4 * npp * 4 * npk, 0.f);
+          for (int lb = 0; lb < 4; ++lb)
+            for (int h = 0; h < halves; ++h) {
+              P.kb0[lb * halves + h] = lb == 0 ? 0 : 3 * npk;
+              P.kbn[lb * halves + h] = lb == 0 ? 3 * npk : npk;
+            }
+          std::vector<float> b((size_t)4 * npl * 4 * npk, 0.f);
           float bmax = 0.f;
           // D^a[x][y]: tets from DV4 (o2), pyramids from the dense host operators (ops: D[a][x][y])
           auto dop = [&](int a, int x, int y) -> float {
@@ -1345,7 +1348,7 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
               for (int a = 0; a < 3; ++a) {
                 const float dnm = dop(a, n, mm), dmn = dop(a, mm, n);
                 b[(size_t)n * 4 * npk + a * npk + mm] = t == TET ? dnm : dmn;
-                b[(size_t)((1 + a) * npp + n) * 4 * npk + 3 * npk + mm] = dnm;
+                b[(size_t)((1 + a) * npl + n) * 4 * npk + 3 * npk + mm] = dnm;
                 bmax = std::max(bmax, std::fabs(dnm));
               }
           P.bis = bmax > 0.f ? std::ldexp(1.f, std::ilogb(bmax) - 14) : 1.f;   // operator scaled into [2^14, 2^15)
@@ -1363,6 +1366,7 @@ dg_status dg_setup(dg_mesh* m, const dg_mesh_desc* d, std::string& err) {
           P.npk = (ntri + 15) / 16 * 16;
           P.npp = (nqt + 15) / 16 * 16;
           const int npk = P.npk, npp = P.npp;
+          P.vnp = npp;
           P.nblk = 7;
           P.kx = 5 * npk;
           const int xblk[7] = {0, 0, 0, 1, 2, 3, 4}, comp[7] = {0, 1, 2, 0, 0, 0, 0};

@@ -40,7 +40,8 @@ def per_type(o, a, b):
 @pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7, 8, 9])
 def test_rhs_matches_oracle(lib, N, precision):
-    """N = 8, 9: the tets on the tensor cores, the pyramids (more than 256 nodes) in FP32."""
+    """N = 8, 9: the pyramids (285 and 385 nodes, more than one MMA's N of 256) compute each
+    output block of the GEMM in two halves."""
     meshes = [small_hybrid_mesh()]
     if N in (2, 5):   # wave-speed jumps and both transition layers
         meshes.append(layered_mesh(3, 2, 6, "HTKKUH", seed=2, c_of_layer=lambda k: 1.0 + 0.4 * (k % 2)))
