@@ -285,3 +285,43 @@ def test_mrlsrk_energy_nonincreasing_under_upwind():
         q = mr.step(q, dmin)
         E.append(o.energy(q))
     assert all(b <= a * (1 + 1e-12) for a, b in zip(E, E[1:])), E
+
+
+@pytest.mark.parametrize("N", [3, 4])
+def test_tet_results_do_not_depend_on_the_node_set(monkeypatch, N):
+    """Reading of Sec. 2.1.2 (the paper's optimised tet nodes are not tabulated): the tet volume
+    term is the exact derivative of the nodal interpolant and the faces are integrated exactly, so
+    the rhs as a polynomial does not depend on where the nodes sit.  Moving every non-vertex node
+    of the equispaced lattice (a different unisolvent set) and interpolating the same state gives
+    the same rhs polynomial to rounding; the other element types are untouched.  (The oracle takes
+    tet traces by evaluating the basis at the face points, so face nodes may move off the face.)"""
+    import oracle.elements as E
+    m = small_hybrid_mesh()
+    oa = DGOracle(m, N)
+    tet_a = oa.els[3]
+    orig_init = E.Tet.__init__
+
+    def moved_init(self, n):
+        orig_init(self, n)
+        rng = np.random.default_rng(n)
+        vert = np.array([any(np.allclose(x, v) for v in self.verts) for x in self.nodes])
+        shift = 0.1 * rng.uniform(-1, 1, self.nodes.shape) / n
+        self.nodes = np.where(vert[:, None], self.nodes, self.nodes + shift)
+        self.Vinv = np.linalg.inv(self._modal(self.nodes))
+
+    monkeypatch.setattr(E.Tet, "__init__", moved_init)
+    ob = DGOracle(m, N)
+    tet_b = ob.els[3]
+    assert np.abs(tet_b.nodes - tet_a.nodes).max() > 1e-3
+    T = tet_a.basis(tet_b.nodes)                     # nodal values in set A -> values at set B's nodes
+    qa = random_state(oa.ndof, 4)
+    qb = qa.copy()
+    lo, K, npn = oa.off[3], oa.K[3], oa.Np[3]
+    sl = slice(lo, lo + K * npn)
+    qb[:, sl] = np.einsum("bn,fkn->fkb", T, qa[:, sl].reshape(4, K, npn)).reshape(4, -1)
+    ra, rb = oa.rhs(qa), ob.rhs(qb)
+    ra_at_b = ra.copy()
+    ra_at_b[:, sl] = np.einsum("bn,fkn->fkb", T, ra[:, sl].reshape(4, K, npn)).reshape(4, -1)
+    assert np.abs(rb - ra_at_b).max() < 1e-11 * np.abs(ra).max()   # measured 3e-15, 3e-14
+    # control: the moved set read as if it were the lattice gives another rhs
+    assert np.abs(ob.rhs(qa) - ra).max() > 1e-3 * np.abs(ra).max()
