@@ -95,9 +95,10 @@ def test_hex_trace_constants_closed_form(N):
     assert abs(trace_constant(0, N, lobatto=True) - 3 * N * (N + 1) / 2) < 1e-9
 
 
-@pytest.mark.parametrize("name", ["wedge", "pyramid", "tet"])
+@pytest.mark.parametrize("name", ["hex", "wedge", "pyramid", "tet"])
 def test_trace_constants_table(name):
-    """Table computedTrace: pins the wedge, pyramid (rational B_N) and tet spaces."""
+    """Table computedTrace: pins the hex (its printed row is 3(N+1)(N+2)/2), wedge, pyramid
+    (rational B_N) and tet spaces."""
     tab = read_table("trace_constants.txt")[name]
     for N in range(1, 10):
         assert abs(trace_constant(TYPES[name], N) - tab[N - 1]) < 0.006, (name, N)
